@@ -1,0 +1,270 @@
+"""Two-level BDDC preconditioner, Section 3.2 of the paper, applied to the
+whole tangent system through the exact interior/interface block
+factorization (first display of Section 3.2).
+
+Setup, per subdomain i (the unassembled local matrix A^(i), A = sum A^(i)):
+* interior DoFs I (nodes in one subdomain only) and interface DoFs Gamma;
+* interface nodes grouped by the set of subdomains sharing them, split into
+  connected pieces: faces (shared by 2), edges (shared by 3 or more),
+  vertices (single-node edges, and edge nodes lying on the outer boundary,
+  which is where the subdomain corners sit when the coordinates are known);
+* primal constraints: vertex values ("V"), and edge ("E") or face ("F")
+  arithmetic averages per displacement component (Sections 3.2 and 6.2);
+* counting scaling delta_i^dagger = 1 / #subdomains sharing the DoF;
+* coarse basis Phi_i: the minimum-energy extension of each primal
+  constraint (the local saddle-point problem with unit constraint values),
+  and the coarse matrix S_PiPi = sum_i R_Pi^T Phi_i^T A^(i) Phi_i R_Pi.
+
+Apply z = M^-1 r:
+  1. u0 = A_II^-1 r_I                           (block diagonal)
+  2. g  = r_Gamma - A_GammaI u0                 (assembled on Gamma)
+  3. g_i = D_i R_i g
+  4. w_i: local Neumann solve with all primal constraints set to zero
+     (vertices eliminated, averages through Lagrange multipliers)
+  5. u_c = S_PiPi^-1 sum_i R_Pi^T Phi_i^T g_i;   w_i += Phi_i R_Pi u_c
+  6. z_Gamma = sum_i R_i^T D_i w_i
+  7. z_I = A_II^-1 (r_I - A_IGamma z_Gamma)
+Steps 2-6 are M_BDDC^-1 = R_D^T S~^-1 R_D applied to the Schur complement
+system; steps 1 and 7 are the exact outer block factors.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.csgraph as csg
+import scipy.sparse.linalg as spla
+
+
+def hex_corner_faces(k):
+    """Corner-node local indices of the 6 faces of a hexahedron of order k
+    (used only to find the outer boundary)."""
+    m = k + 1
+
+    def idx(a, b, c):
+        return a + m * (b + m * c)
+    K = k
+    return [
+        [idx(0, 0, 0), idx(0, K, 0), idx(0, K, K), idx(0, 0, K)],
+        [idx(K, 0, 0), idx(K, K, 0), idx(K, K, K), idx(K, 0, K)],
+        [idx(0, 0, 0), idx(K, 0, 0), idx(K, 0, K), idx(0, 0, K)],
+        [idx(0, K, 0), idx(K, K, 0), idx(K, K, K), idx(0, K, K)],
+        [idx(0, 0, 0), idx(K, 0, 0), idx(K, K, 0), idx(0, K, 0)],
+        [idx(0, 0, K), idx(K, 0, K), idx(K, K, K), idx(0, K, K)],
+    ]
+
+
+def outer_boundary_nodes(fe):
+    """Nodes lying on element faces that belong to one element only."""
+    from .elements import hex_face_nodes
+    k = fe.k
+    corners = hex_corner_faces(k)
+    keys = {}
+    for f, cn in enumerate(corners):
+        fk = np.sort(fe.elems[:, cn], axis=1)
+        for e in range(fe.n_el):
+            t = tuple(fk[e])
+            keys.setdefault(t, []).append((e, f))
+    on = np.zeros(fe.n_nodes, dtype=bool)
+    for lst in keys.values():
+        if len(lst) == 1:
+            e, f = lst[0]
+            on[fe.elems[e, hex_face_nodes(k, f)]] = True
+    return on
+
+
+class Classification:
+    """Interface classes (faces, edges, vertices) of an element partition."""
+
+    def __init__(self, fe, elem_part, n_parts):
+        self.n_parts = n_parts
+        part = np.asarray(elem_part, dtype=np.int64)
+        n = fe.n_nodes
+        # subdomain membership of each node (free nodes only)
+        memb = [set() for _ in range(n)]
+        for e in range(fe.n_el):
+            p = int(part[e])
+            for a in fe.elems[e]:
+                memb[a].add(p)
+        self.members = [tuple(sorted(s)) if not fe.is_dirichlet[a] else ()
+                        for a, s in enumerate(memb)]
+        self.count = np.array([len(s) for s in self.members])
+        iface = self.count >= 2
+        self.interface = iface
+        # group interface nodes by sharing set; connect through elements
+        key_of = {}
+        key = -np.ones(n, dtype=np.int64)
+        for a in np.nonzero(iface)[0]:
+            key[a] = key_of.setdefault(self.members[a], len(key_of))
+        nen = fe.n_en
+        ii = np.repeat(fe.elems, nen, axis=1).reshape(-1)
+        jj = np.tile(fe.elems, (1, nen)).reshape(-1)
+        same = (key[ii] >= 0) & (key[ii] == key[jj])
+        G = sp.coo_matrix((np.ones(same.sum()), (ii[same], jj[same])),
+                          shape=(n, n))
+        ncomp, comp = csg.connected_components(G, directed=False)
+        on_bnd = outer_boundary_nodes(fe)
+        classes = {}
+        for a in np.nonzero(iface)[0]:
+            classes.setdefault(int(comp[a]), []).append(int(a))
+        vertices, edges, faces = [], [], []
+        for nodes in classes.values():
+            s = self.members[nodes[0]]
+            if len(s) == 2:
+                faces.append(sorted(nodes))
+            elif len(nodes) == 1:
+                vertices.append(nodes[0])
+            else:
+                ends = [a for a in nodes if on_bnd[a]]
+                vertices.extend(ends)
+                rest = sorted(a for a in nodes if not on_bnd[a])
+                if rest:
+                    edges.append(rest)
+        self.vertices = sorted(vertices)
+        self.edges = sorted(edges)
+        self.faces = sorted(faces)
+
+
+class BDDC:
+    """BDDC setup for one tangent (element and face matrices Ke, Kf)."""
+
+    def __init__(self, fe, Ke, Kf, primal="V", classification=None):
+        prob = fe.prob
+        self.fe = fe
+        part = np.asarray(prob["elem_part"], dtype=np.int64)
+        n_parts = int(prob["n_parts"])
+        cl = classification or Classification(fe, part, n_parts)
+        self.cl = cl
+        use_v = "V" in primal
+        avg_classes = []
+        if "E" in primal:
+            avg_classes += cl.edges
+        if "F" in primal:
+            avg_classes += cl.faces
+        # global primal numbering: vertex DoFs, then 3 averages per class
+        vert = cl.vertices if use_v else []
+        self.n_pi = 3 * len(vert) + 3 * len(avg_classes)
+        vpos = {a: 3 * j for j, a in enumerate(vert)}
+        apos = [3 * len(vert) + 3 * j for j in range(len(avg_classes))]
+        node_class = {}
+        for j, c in enumerate(avg_classes):
+            for a in c:
+                node_class[a] = j
+        self.subs = []
+        S = np.zeros((self.n_pi, self.n_pi))
+        n2f = fe.node_to_free
+        for i in range(n_parts):
+            nodes = np.unique(fe.elems[part == i])
+            nodes = nodes[~fe.is_dirichlet[nodes]]
+            nloc = nodes.size
+            dof_map = -np.ones(3 * fe.n_nodes, dtype=np.int64)
+            for c in range(3):
+                dof_map[3 * nodes + c] = 3 * np.arange(nloc) + c
+            A = fe.assemble(Ke, Kf, part == i, dof_map, 3 * nloc).tocsr()
+            gdof = (3 * n2f[nodes][:, None] + np.arange(3)).reshape(-1)
+            iface = cl.count[nodes] >= 2
+            ldofI = (3 * np.nonzero(~iface)[0][:, None] + np.arange(3)).ravel()
+            ldofG = (3 * np.nonzero(iface)[0][:, None] + np.arange(3)).ravel()
+            Dg = np.repeat(1.0 / cl.count[nodes[iface]], 3)
+            # primal vertex DoFs (local) and remaining DoFs r
+            is_v = np.array([use_v and a in vpos for a in nodes])
+            ldofV = (3 * np.nonzero(is_v)[0][:, None] + np.arange(3)).ravel()
+            gV = np.array([vpos[a] + c for a in nodes[is_v] for c in range(3)],
+                          dtype=np.int64)
+            keep = np.ones(3 * nloc, dtype=bool)
+            keep[ldofV] = False
+            ldofR = np.nonzero(keep)[0]
+            rpos = -np.ones(3 * nloc, dtype=np.int64)
+            rpos[ldofR] = np.arange(ldofR.size)
+            # averages touching this subdomain
+            loc_cls = sorted({node_class[a] for a in nodes if a in node_class})
+            rows, cols, vals, gA = [], [], [], []
+            for q, j in enumerate(loc_cls):
+                cnodes = avg_classes[j]
+                lidx = np.searchsorted(nodes, cnodes)
+                for c in range(3):
+                    r = 3 * q + c
+                    for li in lidx:
+                        rows.append(r)
+                        cols.append(rpos[3 * li + c])
+                        vals.append(1.0 / len(cnodes))
+                    gA.append(apos[j] + c)
+            na = 3 * len(loc_cls)
+            Cr = sp.coo_matrix((vals, (rows, cols)),
+                               shape=(na, ldofR.size)).tocsr()
+            Krr = A[ldofR][:, ldofR]
+            sad = sp.bmat([[Krr, Cr.T], [Cr, None]], format="csc") if na else \
+                Krr.tocsc()
+            lu_sad = spla.splu(sad)
+            # coarse basis: vertex columns then average columns
+            nv = ldofV.size
+            nc = nv + na
+            Phi = np.zeros((3 * nloc, nc))
+            if nc:
+                rhs = np.zeros((ldofR.size + na, nc))
+                if nv:
+                    rhs[:ldofR.size, :nv] = -A[ldofR][:, ldofV].toarray()
+                    Phi[ldofV, np.arange(nv)] = 1.0
+                if na:
+                    rhs[ldofR.size:, nv:] = np.eye(na)
+                sol = lu_sad.solve(rhs)
+                Phi[ldofR, :] = sol[:ldofR.size]
+                gP = np.concatenate([gV, np.array(gA, dtype=np.int64)])
+                Sc = Phi.T @ (A @ Phi)
+                S[np.ix_(gP, gP)] += Sc
+            else:
+                gP = np.zeros(0, dtype=np.int64)
+            AII = A[ldofI][:, ldofI].tocsc()
+            sub = dict(nodes=nodes, A=A, gdof=gdof, ldofI=ldofI, ldofG=ldofG,
+                       ldofR=ldofR, Dg=Dg, lu_sad=lu_sad, na=na, Phi=Phi,
+                       gP=gP,
+                       luII=spla.splu(AII) if ldofI.size else None,
+                       AGI=A[ldofG][:, ldofI], AIG=A[ldofI][:, ldofG])
+            self.subs.append(sub)
+        self.S_pipi = S
+        self.n_free = fe.n_free
+
+    def _local_solve(self, sub, f_loc):
+        """Constrained Neumann solve with zero primal values: w_v = 0,
+        C_r w_r = 0, [A_rr C_r^T; C_r 0][w_r; mu] = [f_r; 0]."""
+        rhs = np.concatenate([f_loc[sub["ldofR"]], np.zeros(sub["na"])])
+        sol = sub["lu_sad"].solve(rhs)
+        w = np.zeros(f_loc.size)
+        w[sub["ldofR"]] = sol[:sub["ldofR"].size]
+        return w
+
+    def apply(self, r):
+        r = np.asarray(r, dtype=float)
+        z = np.zeros_like(r)
+        g = r.copy()
+        u0 = []
+        for sub in self.subs:
+            gd = sub["gdof"]
+            if sub["luII"] is not None:
+                u = sub["luII"].solve(r[gd[sub["ldofI"]]])
+                g[gd[sub["ldofG"]]] -= sub["AGI"] @ u
+            else:
+                u = np.zeros(0)
+            u0.append(u)
+        c = np.zeros(self.S_pipi.shape[0])
+        ws = []
+        for sub in self.subs:
+            gd = sub["gdof"]
+            f = np.zeros(gd.size)
+            f[sub["ldofG"]] = sub["Dg"] * g[gd[sub["ldofG"]]]
+            w = self._local_solve(sub, f)
+            if sub["gP"].size:
+                np.add.at(c, sub["gP"], sub["Phi"].T @ f)
+            ws.append(w)
+        uc = np.linalg.solve(self.S_pipi, c) if c.size else c
+        zG = np.zeros_like(r)
+        for sub, w in zip(self.subs, ws):
+            gd = sub["gdof"]
+            if sub["gP"].size:
+                w = w + sub["Phi"] @ uc[sub["gP"]]
+            np.add.at(zG, gd[sub["ldofG"]], sub["Dg"] * w[sub["ldofG"]])
+        z[:] = zG
+        for sub, u in zip(self.subs, u0):
+            gd = sub["gdof"]
+            if sub["luII"] is not None:
+                zI = sub["luII"].solve(r[gd[sub["ldofI"]]]
+                                       - sub["AIG"] @ zG[gd[sub["ldofG"]]])
+                z[gd[sub["ldofI"]]] = zI
+        return z
