@@ -1,0 +1,297 @@
+/*
+ * cardiac_bddc.h -- C ABI of the GB300 Newton-GMRES-BDDC tangent solver.
+ *
+ * The library solves the quasi-static cardiac mechanics problem of
+ * Barnafi, Pavarino & Scacchi, "A comparative study of scalable multilevel
+ * preconditioners for cardiac mechanics" (arXiv 2208.06191):
+ *   - Section 2: Guccione passive law, active stress gamma (Ff)(x)f/|Ff|,
+ *     follower endocardial pressure -p J F^{-T} N (Eq. bc endo), weak form
+ *     (Eq. mechanics time discrete, without the inertia term), Newton on
+ *     the tangent problem (Eq. tangent problem);
+ *   - Section 3.2: two-level BDDC with vertex / edge-average / face-average
+ *     primal constraints and counting scaling, as preconditioner of GMRES.
+ *
+ * Conventions shared by every call:
+ *   - Return value: 0 (CBDDC_OK) or one of the CBDDC_E* codes below; the
+ *     message of the last failure on the calling thread is returned by
+ *     cbddc_last_error().  No call aborts or throws across this boundary.
+ *   - "dev" pointers are CUDA device memory of the current device and are
+ *     borrowed (the caller keeps ownership); "host" pointers are ordinary
+ *     host memory, copied during the call unless stated otherwise.
+ *   - Vectors cover the free degrees of freedom only: nodes in increasing
+ *     id with Dirichlet nodes removed, three interleaved components
+ *     (x, y, z) per node (block size 3, Section 4).  n_free = 3 * number
+ *     of free nodes.
+ *   - Calls are ordered on the given stream and asynchronous unless stated
+ *     otherwise.  A handle must not be used from two streams at once.
+ *   - All floating point arguments are FP64.
+ */
+#ifndef CARDIAC_BDDC_H
+#define CARDIAC_BDDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CBDDC_API __attribute__((visibility("default")))
+#else
+#define CBDDC_API
+#endif
+
+/* cudaStream_t without including the CUDA headers (same type). */
+typedef struct CUstream_st* cbddc_stream_t;
+
+enum {
+  CBDDC_OK = 0,
+  CBDDC_EINVAL = 1,    /* bad argument or unsupported input               */
+  CBDDC_ECUDA = 2,     /* a CUDA runtime call failed                      */
+  CBDDC_EPIVOT = 3,    /* zero (tiny) pivot in a local factorisation      */
+  CBDDC_EINVERTED = 4, /* J = det F <= 0 at a quadrature point            */
+  CBDDC_ENOCONV = 5,   /* GMRES or Newton did not converge                */
+  CBDDC_ETIMEOUT = 6,  /* a device wait exceeded its iteration budget     */
+  CBDDC_ENOMEM = 7     /* device or host allocation failed               */
+};
+
+/* Element types (Section 2, "Space discretization"). */
+enum {
+  CBDDC_HEX_Q1 = 1, /* 8-node trilinear hexahedron, 2x2x2 Gauss points  */
+  CBDDC_HEX_Q2 = 2  /* 27-node triquadratic hexahedron, 3x3x3 points   */
+};
+
+/* Analytic fibre fields, evaluated at quadrature points. */
+enum {
+  /* f = (cos a, sin a, 0), s = (-sin a, cos a, 0), n = e_z, with
+     a = p[2] + (p[3] - p[2]) (Z - p[0]) / (p[1] - p[0]) and Z the
+     reference height; p = fiber_params. */
+  CBDDC_FIBER_SLAB_HELIX = 1
+};
+
+/*
+ * Problem description (all arrays host memory, copied by
+ * fem_problem_create).
+ *
+ * Hexahedron local numbering is lexicographic: local node a+(k+1)(b+(k+1)c)
+ * sits at reference point (-1+2a/k, -1+2b/k, -1+2c/k), k = element order.
+ * Local faces: 0 = xi-, 1 = xi+, 2 = eta-, 3 = eta+, 4 = zeta-, 5 = zeta+.
+ */
+typedef struct {
+  int elem_type;               /* CBDDC_HEX_Q1 or CBDDC_HEX_Q2              */
+  int n_nodes;
+  const double* coords;        /* [n_nodes][3] reference coordinates        */
+  int n_elems;
+  const int32_t* elems;        /* [n_elems][nodes per element]              */
+  const int32_t* elem_part;    /* [n_elems] subdomain id in [0, n_parts)    */
+  int n_parts;
+  int n_dirichlet;
+  const int32_t* dirichlet_nodes; /* clamped nodes (all 3 components)        */
+  int n_pressure_faces;
+  const int32_t* pressure_faces;  /* [n][2] (element, local face) pairs on
+                                     which the follower pressure acts      */
+  int fiber_kind;              /* CBDDC_FIBER_*                             */
+  double fiber_params[8];
+  /* Guccione constants C, b_ff, b_ss, b_nn, b_fs, b_fn, b_sn and the
+     volumetric coefficient B of B/2 (J-1) log J (Section 2). */
+  double material[8];
+  double pressure;             /* p at load factor 1 (Pa)                   */
+  double gamma;                /* activation gamma at load factor 1 (Pa)    */
+} fem_problem_desc;
+
+typedef struct fem_problem fem_problem;
+
+typedef struct {
+  int64_t n_free;              /* free DoFs                                 */
+  int64_t n_block_rows;        /* free nodes                                */
+  int64_t nnzb;                /* 3x3 blocks of the tangent                 */
+  int n_parts;
+  int n_vertices, n_edges, n_faces; /* interface classes (Section 3.2)      */
+  int64_t max_local_dofs;      /* largest subdomain (interior + interface)  */
+  int64_t sum_local_dofs;
+  int64_t device_bytes;        /* device memory held by the problem         */
+} fem_problem_info;
+
+/* Builds DoF numbering, the BSR pattern, element-to-slot maps, the
+   subdomain maps and the interface classification on the host, then
+   uploads everything to the current device.  Interface classes: nodes are
+   grouped by the set of subdomains sharing them and split into connected
+   pieces; a piece shared by two subdomains is a face, by three or more an
+   edge, and single-node edges plus edge nodes on the outer boundary are
+   vertices.  *out receives a handle owned by the caller (destroy it with
+   fem_problem_destroy).  Synchronous. */
+CBDDC_API int fem_problem_create(const fem_problem_desc* desc, fem_problem** out);
+CBDDC_API void fem_problem_destroy(fem_problem* P);
+CBDDC_API int fem_problem_get_info(const fem_problem* P, fem_problem_info* info);
+
+/* View of the assembled global tangent in block-CSR form (3x3 blocks,
+   row-major inside a block).  All pointers are device memory owned by the
+   problem; they stay valid until the next fem_assemble_tangent on the
+   same problem or its destruction. */
+typedef struct {
+  const double* vals;          /* [nnzb][3][3]                              */
+  const int32_t* row_ptr;      /* [n_block_rows + 1]                        */
+  const int32_t* col_idx;      /* [nnzb]                                    */
+  int64_t n_block_rows;
+  int64_t nnzb;
+} fem_tangent;
+
+/* Residual F(d) of the weak form at load factor lambda (pressure and
+   activation scaled by lambda), Section 2:
+     F(d) = int P(F) : grad d*  +  int_{pressure faces} p J F^{-T} N . d*.
+   d, residual: dev, [n_free].  Returns CBDDC_EINVERTED (after writing the
+   residual) if J <= 0 at any quadrature point; that status is only known
+   once the stream reaches the call, so this call synchronises. */
+CBDDC_API int fem_residual(fem_problem* P, const double* d, double load_factor,
+                 double* residual, cbddc_stream_t stream);
+
+/* Residual (if residual != NULL) and the exact tangent DF(d) of
+   Eq. (tangent problem): material tangent dP/dF plus the follower-pressure
+   linearisation (non-symmetric).  Fills *K with a view of the global BSR
+   matrix and keeps the element and face matrices for bddc_setup.
+   Synchronises (reports CBDDC_EINVERTED like fem_residual). */
+CBDDC_API int fem_assemble_tangent(fem_problem* P, const double* d, double load_factor,
+                         double* residual, fem_tangent* K,
+                         cbddc_stream_t stream);
+
+/* Copies the last assembled tangent into caller-owned device buffers:
+   vals [nnzb*9], row_ptr [n_block_rows+1], col_idx [nnzb] (any may be
+   NULL to skip it).  Asynchronous. */
+CBDDC_API int fem_tangent_copy(const fem_problem* P, double* vals, int32_t* row_ptr,
+                               int32_t* col_idx, cbddc_stream_t stream);
+
+/* y = K x with the last assembled tangent.  x, y: dev [n_free]. */
+CBDDC_API int fem_spmv(fem_problem* P, const double* x, double* y, cbddc_stream_t stream);
+
+/* ---------------------------------------------------------------- BDDC */
+
+enum { CBDDC_FP64 = 0, CBDDC_FP32 = 1 };      /* local operator precision */
+enum { CBDDC_PRIMAL_V = 1, CBDDC_PRIMAL_E = 2, CBDDC_PRIMAL_F = 4 };
+
+typedef struct {
+  int precision;     /* CBDDC_FP64: all local operators in FP64;
+                        CBDDC_FP32: local Schur complements, inverses and
+                        triangular-solve equivalents in FP32 (inputs and
+                        outputs of bddc_apply stay FP64, coarse solve FP64) */
+  int primal;        /* OR of CBDDC_PRIMAL_* (Section 6.2: V, VE, VEF ...) */
+  double pivot_tol;  /* a pivot below pivot_tol * max|diag| is an error   */
+} bddc_options;
+
+typedef struct bddc_ctx bddc_ctx;
+
+typedef struct {
+  int n_primal;                /* coarse space dimension                    */
+  int precision;
+  int64_t local_bytes;         /* bytes of local operators read per apply   */
+  int64_t device_bytes;        /* device memory held by the context         */
+  double setup_flops;          /* algorithmic flops of the last setup       */
+} bddc_info;
+
+/* BDDC setup for the tangent last assembled on P (Section 3.2): subdomain
+   matrices A^(i) from the element matrices; A_II^-1, A_II^-1 A_IG,
+   A_GI A_II^-1 and the Schur complement S_i by a block Gauss-Jordan sweep;
+   the constrained Neumann solution operator on the interface and the
+   minimum-energy coarse basis Phi_i; S_PiPi = sum Phi_i^T S_i Phi_i and its
+   FP64 inverse.  If *inout is NULL a context is created (owned by the
+   caller, release with bddc_destroy); otherwise it is reused, and must
+   have been created for the same P and options.  Synchronises and returns
+   CBDDC_EPIVOT on a tiny pivot. */
+CBDDC_API int bddc_setup(fem_problem* P, const fem_tangent* K, const bddc_options* opt,
+               bddc_ctx** inout, cbddc_stream_t stream);
+
+/* z = M_BDDC^-1 r for the full system: interior correction, interface
+   restriction with counting scaling, constrained local solves plus coarse
+   correction, averaging, harmonic extension.  r, z: dev [n_free], must not
+   alias.  Asynchronous. */
+CBDDC_API int bddc_apply(bddc_ctx* C, const double* r, double* z, cbddc_stream_t stream);
+CBDDC_API void bddc_destroy(bddc_ctx* C);
+CBDDC_API int bddc_get_info(const bddc_ctx* C, bddc_info* info);
+
+/* ---------------------------------------------------- GMRES and Newton */
+
+typedef struct {
+  int restart;         /* Krylov dimension per cycle (default 100)          */
+  int max_iters;       /* total iteration cap                               */
+  double rtol;         /* stop when ||b - K x|| <= rtol ||b||               */
+} gmres_options;
+
+typedef struct {
+  int iterations;
+  int converged;
+  double rel_residual; /* true relative residual at exit                    */
+} gmres_report;
+
+/* Flexible GMRES (right preconditioned by BDDC, Arnoldi by classical
+   Gram-Schmidt applied twice, FP64) for K x = b with the last assembled
+   tangent of P.  b, x: dev [n_free]; x is overwritten (zero initial
+   guess).  Synchronises once per iteration to test convergence.  Returns
+   CBDDC_ENOCONV if max_iters is reached. */
+CBDDC_API int gmres_solve(fem_problem* P, bddc_ctx* C, const double* b, double* x,
+                const gmres_options* opt, gmres_report* rep,
+                cbddc_stream_t stream);
+
+typedef struct {
+  int precision;       /* CBDDC_FP64 or CBDDC_FP32 local operators           */
+  int primal;          /* OR of CBDDC_PRIMAL_*                               */
+  int load_steps;      /* lambda_k = k / load_steps                          */
+  int max_newton;      /* Newton iterations per load step                    */
+  int max_halvings;    /* load-increment halvings before giving up           */
+  int restart;         /* GMRES restart                                      */
+  int max_gmres;       /* GMRES iteration cap per Newton step                */
+  double newton_rtol;  /* ||F(d)|| <= newton_rtol ||F(d^{n,0})||             */
+  double gmres_rtol;   /* relative residual of each tangent solve            */
+  double pivot_tol;
+} solve_options;
+
+#define CBDDC_MAX_RECORDS 512
+typedef struct {
+  double load;         /* load factor of this Newton step                    */
+  int newton;          /* Newton index within the load step                  */
+  int gmres_its;
+  double res;          /* ||F(d)|| before the step                           */
+  double res0;         /* ||F(d^{n,0})|| of the load step                    */
+  float ms_assemble, ms_setup, ms_gmres, ms_total; /* CUDA-event times       */
+} newton_record;
+
+typedef struct {
+  int status;
+  int newton_steps;
+  int load_steps_done;
+  int halvings;
+  int total_gmres_its;
+  double final_rel_residual;
+  int n_records;
+  newton_record rec[CBDDC_MAX_RECORDS];
+} solve_report;
+
+/* One Newton step at load factor lambda (Eq. tangent problem): residual,
+   tangent, BDDC setup (into *ctx, created if NULL), GMRES on
+   DF(d) delta = -F(d), then d += delta.  d: dev [n_free], updated in
+   place.  rec (host, may be NULL) receives the step's timings.
+   Synchronises. */
+CBDDC_API int newton_step(fem_problem* P, bddc_ctx** ctx, const solve_options* opt,
+                double load_factor, double* d, newton_record* rec,
+                cbddc_stream_t stream);
+
+/* Same as newton_step with d in host memory: d is copied to the device,
+   the step runs, and the updated d is copied back before returning. */
+CBDDC_API int newton_step_host(fem_problem* P, bddc_ctx** ctx, const solve_options* opt,
+                     double load_factor, double* d_host, newton_record* rec,
+                     cbddc_stream_t stream);
+
+/* Full load-stepped Newton solve (Section 2): for each load level,
+   Newton from the previous solution until ||F|| <= newton_rtol ||F_0||;
+   the increment is halved on J <= 0 or Newton failure.  d: dev [n_free],
+   in: initial guess (usually zero), out: solution.  rep: host,
+   caller-allocated.  Synchronises. */
+CBDDC_API int newton_gmres_solve(fem_problem* P, const solve_options* opt, double* d,
+                       solve_report* rep, cbddc_stream_t stream);
+
+/* Message for the last non-zero status returned on this thread. */
+CBDDC_API const char* cbddc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CARDIAC_BDDC_H */

@@ -1,0 +1,960 @@
+// Two-level BDDC (Section 3.2 of the paper) on dense per-subdomain
+// operators, for the whole tangent system through the exact interior /
+// interface block factorisation.
+//
+// Setup (per subdomain i, all subdomains batched in each launch):
+//   A^(i) (ordered [I | Gamma_r | Gamma_v]) from the element matrices;
+//   sweep over I  -> [[A_II^-1, A_II^-1 A_IG], [-A_GI A_II^-1, S_i]];
+//   sweep of a copy of S_i over Gamma_r
+//                 -> [[S_rr^-1, S_rr^-1 S_rv], [., S_vv - S_vr S_rr^-1 S_rv]];
+//   averages C (edge/face means per component) on Gamma_r:
+//     Y = S_rr^-1 C^T, Z = C [S_rr^-1 | S_rr^-1 S_rv], G = C Y, W = G^-1 Z,
+//     T_rr = S_rr^-1 - Y W_r        (constrained Neumann solve, zero primal
+//                                    values: the local problem of Sec. 3.2),
+//     Phi_r = [-(S_rr^-1 S_rv - Y W_v) | Y G^-1],  Phi_v = [I | 0]
+//                                   (minimum-energy coarse basis);
+//   S_PiPi = sum_i R_Pi^T Phi_i^T S_i Phi_i R_Pi, inverted in FP64.
+// Apply z = M^-1 r (10 launches, all batched):
+//   u0 = A_II^-1 r_I and h = A_GI A_II^-1 r_I       (one GEMV on [A_II^-1; -H])
+//   g = r_G - sum_i R_i^T h_i ;  g_i = D_i R_i g
+//   w_i = T_i g_i ;  c = sum_i R_Pi^T Phi_i^T g_i ;  u_c = S_PiPi^-1 c
+//   z_G = sum_i R_i^T D_i (w_i + Phi_i R_Pi u_c)
+//   z_I = u0 - A_II^-1 A_IG z_G
+// The local operators are FP64 or FP32 (FP32 accumulation); vectors, the
+// coarse restriction/prolongation sums and the coarse solve are FP64.
+#include <algorithm>
+#include <map>
+
+#include "bddc.h"
+#include "fem.h"
+
+namespace cbddc {
+
+namespace {
+
+__host__ __device__ inline int64_t round_up_dev(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+constexpr int64_t kAlign = 64;  // element alignment of every packed block
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec2<double> { using type = double2; static constexpr int W = 2; };
+
+__device__ inline float vdot(float4 v, const float* x) { return v.x * x[0] + v.y * x[1] + v.z * x[2] + v.w * x[3]; }
+__device__ inline double vdot(double2 v, const double* x) { return v.x * x[0] + v.y * x[1]; }
+
+template <typename T>
+__device__ inline T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Warp dot product of a 16-byte aligned row segment with a shared-memory
+// vector (also 16-byte aligned); streaming loads.
+template <typename T>
+__device__ inline T warp_dot(const T* __restrict__ row, const T* __restrict__ xs, int n, int lane) {
+  using V = typename Vec2<T>::type;
+  constexpr int W = Vec2<T>::W;
+  const int nv = n / W;
+  const V* body = reinterpret_cast<const V*>(row);
+  T acc = T(0);
+  for (int i = lane; i < nv; i += 32) acc += vdot(__ldcs(body + i), xs + i * W);
+  for (int i = nv * W + lane; i < n; i += 32) acc += row[i] * xs[i];
+  return warp_sum(acc);
+}
+
+// ------------------------------------------------------------ setup kernels
+
+template <typename T>
+__global__ void densify_kernel(const int* __restrict__ lsub, const int* __restrict__ lrow,
+                               const int* __restrict__ lcol, const int* __restrict__ lptr,
+                               const int* __restrict__ lsrc, const double* __restrict__ contrib,
+                               int64_t nslots, const int* __restrict__ perm,
+                               const int64_t* __restrict__ offN, const int64_t* __restrict__ offA,
+                               const int* __restrict__ ldA, const int* __restrict__ nI,
+                               T* __restrict__ Aloc) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nslots * 9) return;
+  const int64_t sl = t / 9;
+  const int e = (int)(t % 9), i = e / 3, k = e % 3;
+  const int s = lsub[sl];
+  const int pr = perm[offN[s] + lrow[sl]], pc = perm[offN[s] + lcol[sl]];
+  double v = 0.0;
+  for (int j = lptr[sl]; j < lptr[sl + 1]; ++j) v += contrib[(int64_t)lsrc[j] * 9 + e];
+  const int row = 3 * pr + i;
+  int col = 3 * pc + k;
+  const int ni = nI[s];
+  if (col >= ni) col += (int)(round_up_dev(ni, 4) - ni);
+  Aloc[offA[s] + (int64_t)row * ldA[s] + col] = (T)v;
+}
+
+template <typename T>
+__global__ void copy_schur_kernel(const int* __restrict__ nI, const int* __restrict__ nG,
+                                  const int64_t* __restrict__ offA, const int* __restrict__ ldA,
+                                  const int64_t* __restrict__ offS, const int* __restrict__ ldS,
+                                  const T* __restrict__ Aloc, T* __restrict__ Sw) {
+  const int s = blockIdx.y;
+  const int ng = nG[s], ni = nI[s];
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ng * ng) return;
+  const int i = (int)(t / ng), j = (int)(t % ng);
+  const int cI = (int)round_up_dev(ni, 4);
+  Sw[offS[s] + (int64_t)i * ldS[s] + j] = Aloc[offA[s] + (int64_t)(ni + i) * ldA[s] + cI + j];
+}
+
+// S_rr += alpha C^T C with C the average constraints (alpha = largest |S_ii|
+// of the subdomain, and each class block scaled by its size).  Since C w = 0
+// for every admissible w, the constrained solution operator and the coarse
+// basis are unchanged, while S_rr becomes invertible for floating subdomains
+// whose primal space has no vertices.  Members of different constraints are
+// disjoint, so the updates do not overlap.  One CTA per subdomain.
+template <typename T>
+__global__ void __launch_bounds__(256)
+augment_kernel(const int* __restrict__ nr, const int* __restrict__ na,
+               const int64_t* __restrict__ offCon, const int* __restrict__ cptr,
+               const int* __restrict__ cidx, const double* __restrict__ cw,
+               const int64_t* __restrict__ offS, const int* __restrict__ ldS, T* __restrict__ Sw) {
+  __shared__ double red[256];
+  const int s = blockIdx.x;
+  const int n = nr[s];
+  if (na[s] == 0 || n == 0) return;
+  T* S0 = Sw + offS[s];
+  const int ld = ldS[s];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs((double)S0[(int64_t)i * ld + i]));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double alpha = red[0];
+  for (int q = 0; q < na[s]; ++q) {
+    const int64_t gq = offCon[s] + q;
+    const int b = cptr[gq], cnt = cptr[gq + 1] - b;
+    const T add = (T)(alpha * cw[gq]);  // alpha / |class|
+    for (int t = threadIdx.x; t < cnt * cnt; t += blockDim.x) {
+      const int i = cidx[b + t / cnt], j = cidx[b + t % cnt];
+      S0[(int64_t)i * ld + j] += add;
+    }
+  }
+}
+
+// Y[row][q] = w_q sum_{j in q} Sw[row][j], one warp per row (row < n_r).
+template <typename T>
+__global__ void cons_y_kernel(const int* __restrict__ nr, const int* __restrict__ na,
+                              const int64_t* __restrict__ offCon, const int* __restrict__ cptr,
+                              const int* __restrict__ cidx, const double* __restrict__ cw,
+                              const int64_t* __restrict__ offS, const int* __restrict__ ldS,
+                              const int64_t* __restrict__ offY, const int* __restrict__ ldY,
+                              const T* __restrict__ Sw, T* __restrict__ Y) {
+  const int s = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (row >= nr[s]) return;
+  const T* Srow = Sw + offS[s] + (int64_t)row * ldS[s];
+  for (int q = 0; q < na[s]; ++q) {
+    const int64_t gq = offCon[s] + q;
+    double acc = 0.0;
+    for (int j = cptr[gq] + lane; j < cptr[gq + 1]; j += 32) acc += (double)Srow[cidx[j]];
+    acc = warp_sum(acc);
+    if (lane == 0) Y[offY[s] + (int64_t)row * ldY[s] + q] = (T)(acc * cw[gq]);
+  }
+}
+
+// Zf[q][col] = w_q sum_{j in q} Sw[j][col] for all n_G columns.
+template <typename T>
+__global__ void cons_z_kernel(const int* __restrict__ nG, const int* __restrict__ na,
+                              const int64_t* __restrict__ offCon, const int* __restrict__ cptr,
+                              const int* __restrict__ cidx, const double* __restrict__ cw,
+                              const int64_t* __restrict__ offS, const int* __restrict__ ldS,
+                              const int64_t* __restrict__ offZ, const T* __restrict__ Sw,
+                              T* __restrict__ Zf) {
+  const int s = blockIdx.y;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nG[s]) return;
+  const T* S0 = Sw + offS[s];
+  const int ld = ldS[s];
+  for (int q = 0; q < na[s]; ++q) {
+    const int64_t gq = offCon[s] + q;
+    double acc = 0.0;
+    for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += (double)S0[(int64_t)cidx[j] * ld + col];
+    Zf[offZ[s] + (int64_t)q * ld + col] = (T)(acc * cw[gq]);
+  }
+}
+
+// G[q][q2] = w_q sum_{j in q} Y[j][q2]
+template <typename T>
+__global__ void cons_g_kernel(const int* __restrict__ na, const int64_t* __restrict__ offCon,
+                              const int* __restrict__ cptr, const int* __restrict__ cidx,
+                              const double* __restrict__ cw, const int64_t* __restrict__ offY,
+                              const int* __restrict__ ldY, const int64_t* __restrict__ offG,
+                              const int* __restrict__ ldG, const T* __restrict__ Y, T* __restrict__ G) {
+  const int s = blockIdx.y;
+  const int n = na[s];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int q = t / n, q2 = t % n;
+  const int64_t gq = offCon[s] + q;
+  double acc = 0.0;
+  for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += (double)Y[offY[s] + (int64_t)cidx[j] * ldY[s] + q2];
+  G[offG[s] + (int64_t)q * ldG[s] + q2] = (T)(acc * cw[gq]);
+}
+
+// In-place inverse of each small n_a x n_a block (FP64 Gauss-Jordan).
+template <typename T>
+__global__ void small_inverse_kernel(const int* __restrict__ na, const int64_t* __restrict__ offG,
+                                     const int* __restrict__ ldG, T* __restrict__ G,
+                                     int* __restrict__ status, double tol) {
+  extern __shared__ double sm[];
+  const int s = blockIdx.x;
+  const int n = na[s];
+  if (n == 0) return;
+  double* a = sm;                 // n x (n+1)
+  double* fcol = sm + n * (n + 1);
+  __shared__ double scale;
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  T* g = G + offG[s];
+  const int ld = ldG[s];
+  for (int t = tid; t < n * n; t += blockDim.x) a[(t / n) * (n + 1) + t % n] = (double)g[(int64_t)(t / n) * ld + t % n];
+  if (tid == 0) { bad = 0; scale = 0.0; }
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < n; ++i) m = fmax(m, fabs(a[i * (n + 1) + i]));
+    scale = m;
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const double pv = a[j * (n + 1) + j];
+    if (tid == 0 && (!(fabs(pv) > tol * scale) || !isfinite(pv))) bad = 1;
+    const double inv = 1.0 / pv;
+    for (int i = tid; i < n; i += blockDim.x) fcol[i] = a[i * (n + 1) + j];
+    __syncthreads();
+    for (int c = tid; c < n; c += blockDim.x) a[j * (n + 1) + c] = (c == j) ? inv : a[j * (n + 1) + c] * inv;
+    __syncthreads();
+    for (int t = tid; t < n * n; t += blockDim.x) {
+      const int i = t / n, c = t % n;
+      if (i == j) continue;
+      if (c == j) a[i * (n + 1) + c] = -fcol[i] * inv;
+      else a[i * (n + 1) + c] -= fcol[i] * a[j * (n + 1) + c];
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < n * n; t += blockDim.x) g[(int64_t)(t / n) * ld + t % n] = (T)a[(t / n) * (n + 1) + t % n];
+  if (tid == 0 && bad) atomicOr(status, DEV_PIVOT);
+}
+
+// Phi[0:nr, 0:nv] = -Sw[0:nr, nr:nG] ; Phi[nr:nG, :] = [I 0]
+template <typename T>
+__global__ void phi_vertex_kernel(const int* __restrict__ nG, const int* __restrict__ nr,
+                                  const int* __restrict__ nv, const int* __restrict__ nc,
+                                  const int64_t* __restrict__ offS, const int* __restrict__ ldS,
+                                  const int64_t* __restrict__ offPhi, const int* __restrict__ ldPhi,
+                                  const T* __restrict__ Sw, T* __restrict__ Phi) {
+  const int s = blockIdx.y;
+  const int ncs = nc[s], ng = nG[s], nrs = nr[s], nvs = nv[s];
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ng * ncs) return;
+  const int row = (int)(t / ncs), c = (int)(t % ncs);
+  T* dst = Phi + offPhi[s] + (int64_t)row * ldPhi[s] + c;
+  if (row < nrs) {
+    if (c < nvs) *dst = -Sw[offS[s] + (int64_t)row * ldS[s] + nrs + c];
+  } else {
+    *dst = (c == row - nrs) ? T(1) : T(0);
+  }
+}
+
+__global__ void coarse_assemble_kernel_f(const int* __restrict__ key, const int* __restrict__ ptr,
+                                         const int* __restrict__ src, int64_t n,
+                                         const float* __restrict__ Kc, double* __restrict__ S) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double v = 0.0;
+  for (int j = ptr[t]; j < ptr[t + 1]; ++j) v += (double)Kc[src[j]];
+  S[key[t]] = v;
+}
+__global__ void coarse_assemble_kernel_d(const int* __restrict__ key, const int* __restrict__ ptr,
+                                         const int* __restrict__ src, int64_t n,
+                                         const double* __restrict__ Kc, double* __restrict__ S) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double v = 0.0;
+  for (int j = ptr[t]; j < ptr[t + 1]; ++j) v += Kc[src[j]];
+  S[key[t]] = v;
+}
+
+// ------------------------------------------------------------ apply kernels
+constexpr int AROWS = 32;  // rows per CTA in the batched GEMVs (8 warps x 4)
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+apply_interior_kernel(const int* __restrict__ nI, const int* __restrict__ ns,
+                      const int64_t* __restrict__ offA, const int* __restrict__ ldA,
+                      const int64_t* __restrict__ offI, const int64_t* __restrict__ offGam,
+                      const int* __restrict__ gdofI, const T* __restrict__ Aloc,
+                      const double* __restrict__ r, double* __restrict__ u0, double* __restrict__ hG) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* xs = reinterpret_cast<T*>(smraw);
+  const int s = blockIdx.y;
+  const int ni = nI[s], n = ns[s];
+  const int r0 = blockIdx.x * AROWS;
+  if (r0 >= n) return;
+  for (int j = threadIdx.x; j < ni; j += blockDim.x) xs[j] = (T)r[gdofI[offI[s] + j]];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T* A0 = Aloc + offA[s];
+  const int ld = ldA[s];
+  for (int rr = warp; rr < AROWS; rr += 8) {
+    const int row = r0 + rr;
+    if (row >= n) break;
+    const T v = ni > 0 ? warp_dot(A0 + (int64_t)row * ld, xs, ni, lane) : T(0);
+    if (lane == 0) {
+      if (row < ni) u0[offI[s] + row] = (double)v;
+      else hG[offGam[s] + row - ni] = (double)v;  // = -(A_GI A_II^-1 r_I)
+    }
+  }
+}
+
+__global__ void assemble_g_kernel(const int* __restrict__ if_dof, const int* __restrict__ if_ptr,
+                                  const int* __restrict__ if_src, int n_if, const double* __restrict__ r,
+                                  const double* __restrict__ hG, double* __restrict__ gI) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_if) return;
+  double g = r[if_dof[m]];
+  for (int j = if_ptr[m]; j < if_ptr[m + 1]; ++j) g += hG[if_src[j]];
+  gI[m] = g;
+}
+
+__global__ void restrict_kernel(const int* __restrict__ gam_if, const double* __restrict__ Dg, int64_t n,
+                                const double* __restrict__ gI, double* __restrict__ gl) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  gl[q] = Dg[q] * gI[gam_if[q]];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+apply_local_kernel(const int* __restrict__ nG, const int* __restrict__ nr,
+                   const int64_t* __restrict__ offS, const int* __restrict__ ldS,
+                   const int64_t* __restrict__ offGam, const T* __restrict__ Sw,
+                   const double* __restrict__ gl, double* __restrict__ wG) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* xs = reinterpret_cast<T*>(smraw);
+  const int s = blockIdx.y;
+  const int ng = nG[s], nrs = nr[s];
+  const int r0 = blockIdx.x * AROWS;
+  if (r0 >= ng) return;
+  const int64_t og = offGam[s];
+  for (int j = threadIdx.x; j < nrs; j += blockDim.x) xs[j] = (T)gl[og + j];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T* S0 = Sw + offS[s];
+  const int ld = ldS[s];
+  for (int rr = warp; rr < AROWS; rr += 8) {
+    const int row = r0 + rr;
+    if (row >= ng) break;
+    T v = T(0);
+    if (row < nrs) v = warp_dot(S0 + (int64_t)row * ld, xs, nrs, lane);
+    if (lane == 0) wG[og + row] = (double)v;
+  }
+}
+
+// cl = Phi^T g_i, one CTA per subdomain (FP64 accumulation, n_c <= 128).
+template <typename T>
+__global__ void __launch_bounds__(256)
+apply_phit_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
+                  const int64_t* __restrict__ offPhi, const int* __restrict__ ldPhi,
+                  const int64_t* __restrict__ offGam, const int64_t* __restrict__ offC,
+                  const T* __restrict__ Phi, const double* __restrict__ gl, double* __restrict__ cl) {
+  __shared__ double red[8][128];
+  const int s = blockIdx.x;
+  const int ng = nG[s], ncs = nc[s];
+  if (ncs == 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double acc[4] = {0, 0, 0, 0};
+  const T* P0 = Phi + offPhi[s];
+  const int ld = ldPhi[s];
+  const int64_t og = offGam[s];
+  for (int j = warp; j < ng; j += 8) {
+    const double gj = gl[og + j];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int c = lane + 32 * t;
+      if (c < ncs) acc[t] += (double)P0[(int64_t)j * ld + c] * gj;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) red[warp][lane + 32 * t] = acc[t];
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncs; c += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += red[w][c];
+    cl[offC[s] + c] = v;
+  }
+}
+
+__global__ void gather_sum_kernel(const int* __restrict__ ptr, const int* __restrict__ src, int n,
+                                  const double* __restrict__ x, double* __restrict__ y) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double v = 0.0;
+  for (int j = ptr[m]; j < ptr[m + 1]; ++j) v += x[src[j]];
+  y[m] = v;
+}
+
+__global__ void dense_gemv_kernel(const double* __restrict__ A, int n, const double* __restrict__ x,
+                                  double* __restrict__ y) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* a = A + (int64_t)row * n;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc += a[j] * __ldg(&x[j]);
+  acc = warp_sum(acc);
+  if (lane == 0) y[row] = acc;
+}
+
+// y_i = D_i (w_i + Phi_i R_Pi u_c), one warp per interface row.
+template <typename T>
+__global__ void __launch_bounds__(256)
+apply_prolong_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
+                     const int64_t* __restrict__ offPhi, const int* __restrict__ ldPhi,
+                     const int64_t* __restrict__ offGam, const int64_t* __restrict__ offC,
+                     const int* __restrict__ gprim, const T* __restrict__ Phi,
+                     const double* __restrict__ uc, const double* __restrict__ wG,
+                     const double* __restrict__ Dg, double* __restrict__ yG) {
+  __shared__ double ucl[128];
+  const int s = blockIdx.y;
+  const int ng = nG[s], ncs = nc[s];
+  const int r0 = blockIdx.x * AROWS;
+  if (r0 >= ng) return;
+  for (int c = threadIdx.x; c < ncs; c += blockDim.x) ucl[c] = uc[gprim[offC[s] + c]];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T* P0 = Phi + offPhi[s];
+  const int ld = ldPhi[s];
+  const int64_t og = offGam[s];
+  for (int rr = warp; rr < AROWS; rr += 8) {
+    const int row = r0 + rr;
+    if (row >= ng) break;
+    double acc = 0.0;
+    for (int c = lane; c < ncs; c += 32) acc += (double)P0[(int64_t)row * ld + c] * ucl[c];
+    acc = warp_sum(acc);
+    if (lane == 0) yG[og + row] = Dg[og + row] * (wG[og + row] + acc);
+  }
+}
+
+__global__ void average_kernel(const int* __restrict__ if_dof, const int* __restrict__ if_ptr,
+                               const int* __restrict__ if_src, int n_if, const double* __restrict__ yG,
+                               double* __restrict__ z) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_if) return;
+  double v = 0.0;
+  for (int j = if_ptr[m]; j < if_ptr[m + 1]; ++j) v += yG[if_src[j]];
+  z[if_dof[m]] = v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+apply_extend_kernel(const int* __restrict__ nI, const int* __restrict__ nG,
+                    const int64_t* __restrict__ offA, const int* __restrict__ ldA,
+                    const int64_t* __restrict__ offI, const int64_t* __restrict__ offGam,
+                    const int* __restrict__ gdofI, const int* __restrict__ gdofG,
+                    const T* __restrict__ Aloc, const double* __restrict__ u0, double* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* xs = reinterpret_cast<T*>(smraw);
+  const int s = blockIdx.y;
+  const int ni = nI[s], ng = nG[s];
+  const int r0 = blockIdx.x * AROWS;
+  if (r0 >= ni) return;
+  const int64_t og = offGam[s];
+  for (int j = threadIdx.x; j < ng; j += blockDim.x) xs[j] = (T)z[gdofG[og + j]];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cI = (ni + 3) / 4 * 4;
+  const T* A0 = Aloc + offA[s] + cI;
+  const int ld = ldA[s];
+  for (int rr = warp; rr < AROWS; rr += 8) {
+    const int row = r0 + rr;
+    if (row >= ni) break;
+    T v = T(0);
+    if (ng > 0) v = warp_dot(A0 + (int64_t)row * ld, xs, ng, lane);
+    if (lane == 0) z[gdofI[offI[s] + row]] = u0[offI[s] + row] - (double)v;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ create
+void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
+  CB_CHECK(opt != nullptr, CBDDC_EINVAL, "null options");
+  CB_CHECK(opt->precision == CBDDC_FP64 || opt->precision == CBDDC_FP32, CBDDC_EINVAL, "bad precision");
+  C->P = P;
+  C->precision = opt->precision;
+  C->primal = opt->primal;
+  C->pivot_tol = opt->pivot_tol > 0 ? opt->pivot_tol : 1e-13;
+  C->esize = opt->precision == CBDDC_FP32 ? 4 : 8;
+  const int nsub = P->n_parts;
+  C->nsub = nsub;
+  const bool useV = opt->primal & CBDDC_PRIMAL_V;
+  const bool useE = opt->primal & CBDDC_PRIMAL_E;
+  const bool useF = opt->primal & CBDDC_PRIMAL_F;
+  const int nn = P->n_nodes;
+  std::vector<int> vert_pos(nn, -1);
+  int n_vert = 0;
+  if (useV)
+    for (int v : P->vertices) vert_pos[v] = n_vert++;
+  std::vector<const std::vector<int>*> avg;
+  if (useE) for (auto& e : P->edges) avg.push_back(&e);
+  if (useF) for (auto& f : P->faces) avg.push_back(&f);
+  std::vector<int> node_cls(nn, -1);
+  for (size_t j = 0; j < avg.size(); ++j)
+    for (int v : *avg[j]) node_cls[v] = (int)j;
+  C->n_pi = 3 * n_vert + 3 * (int)avg.size();
+
+  C->nI.assign(nsub, 0); C->nG = C->nr = C->nv = C->na = C->nc = C->ns = C->nI;
+  std::vector<int> perm_h;
+  std::vector<int64_t> offN(nsub + 1, 0);
+  std::vector<int> gdofI, gdofG, gprim;
+  std::vector<double> Dg;
+  std::vector<int> cptr{0}, cidx;
+  std::vector<double> cw;
+  C->offI.assign(nsub + 1, 0);
+  C->offGam.assign(nsub + 1, 0);
+  C->offC.assign(nsub + 1, 0);
+  C->offCon.assign(nsub + 1, 0);
+  const std::vector<int>& n2f = P->node_to_free;
+  for (int s = 0; s < nsub; ++s) {
+    const auto& sub = P->subs[s];
+    const int nl = (int)sub.nodes.size();
+    std::vector<int> I, Gr, Gv;
+    for (int l = 0; l < nl; ++l) {
+      if (!sub.iface[l]) I.push_back(l);
+      else if (vert_pos[sub.nodes[l]] >= 0) Gv.push_back(l);
+      else Gr.push_back(l);
+    }
+    std::vector<int> perm(nl);
+    int pos = 0;
+    for (int l : I) perm[l] = pos++;
+    std::vector<int> rpos(nl, -1);
+    for (int l : Gr) { rpos[l] = pos - (int)I.size(); perm[l] = pos++; }
+    for (int l : Gv) perm[l] = pos++;
+    perm_h.insert(perm_h.end(), perm.begin(), perm.end());
+    offN[s + 1] = offN[s] + nl;
+    C->nI[s] = 3 * (int)I.size();
+    C->nr[s] = 3 * (int)Gr.size();
+    C->nv[s] = 3 * (int)Gv.size();
+    C->nG[s] = C->nr[s] + C->nv[s];
+    C->ns[s] = C->nI[s] + C->nG[s];
+    for (int l : I)
+      for (int c = 0; c < 3; ++c) gdofI.push_back(3 * n2f[sub.nodes[l]] + c);
+    for (const std::vector<int>* lst : {&Gr, &Gv})
+      for (int l : *lst)
+        for (int c = 0; c < 3; ++c) {
+          gdofG.push_back(3 * n2f[sub.nodes[l]] + c);
+          Dg.push_back(1.0 / P->share_count[sub.nodes[l]]);
+        }
+    // average constraints of classes touching this subdomain
+    std::vector<int> cls;
+    for (int l : Gr)
+      if (node_cls[sub.nodes[l]] >= 0) cls.push_back(node_cls[sub.nodes[l]]);
+    std::sort(cls.begin(), cls.end());
+    cls.erase(std::unique(cls.begin(), cls.end()), cls.end());
+    for (int j : cls) {
+      const std::vector<int>& cn = *avg[j];
+      for (int c = 0; c < 3; ++c) {
+        for (int v : cn) {
+          auto it = std::lower_bound(sub.nodes.begin(), sub.nodes.end(), v);
+          CB_CHECK(it != sub.nodes.end() && *it == v, CBDDC_EINVAL, "class node not in subdomain");
+          const int l = (int)(it - sub.nodes.begin());
+          CB_CHECK(rpos[l] >= 0, CBDDC_EINVAL, "class node is not a dual interface node");
+          cidx.push_back(3 * rpos[l] + c);
+        }
+        cptr.push_back((int)cidx.size());
+        cw.push_back(1.0 / (double)cn.size());
+      }
+    }
+    C->na[s] = 3 * (int)cls.size();
+    C->nc[s] = C->nv[s] + C->na[s];
+    CB_CHECK(C->nc[s] <= 128, CBDDC_EINVAL, "more than 128 primal constraints in one subdomain");
+    for (int l : Gv)
+      for (int c = 0; c < 3; ++c) gprim.push_back(3 * vert_pos[sub.nodes[l]] + c);
+    for (int j : cls)
+      for (int c = 0; c < 3; ++c) gprim.push_back(3 * n_vert + 3 * j + c);
+    C->offI[s + 1] = C->offI[s] + C->nI[s];
+    C->offGam[s + 1] = C->offGam[s] + C->nG[s];
+    C->offC[s + 1] = C->offC[s] + C->nc[s];
+    C->offCon[s + 1] = C->offCon[s] + C->na[s];
+  }
+  C->totI = C->offI[nsub];
+  C->totG = C->offGam[nsub];
+  C->totC = C->offC[nsub];
+
+  // interface DoFs: global list and gather lists from packed Gamma positions
+  std::vector<int> node_if(nn, -1);
+  std::vector<int> if_dof;
+  for (int v = 0; v < nn; ++v)
+    if (n2f[v] >= 0 && P->share_count[v] >= 2) {
+      node_if[v] = (int)(if_dof.size() / 3);
+      for (int c = 0; c < 3; ++c) if_dof.push_back(3 * n2f[v] + c);
+    }
+  C->n_if = (int)if_dof.size();
+  std::vector<int> gam_if(C->totG);
+  std::vector<std::pair<int64_t, int>> ikv;
+  {
+    // map free DoF -> interface index
+    std::vector<int> dof_if(P->n_free, -1);
+    for (int m = 0; m < C->n_if; ++m) dof_if[if_dof[m]] = m;
+    for (int64_t q = 0; q < C->totG; ++q) {
+      const int m = dof_if[gdofG[q]];
+      CB_CHECK(m >= 0, CBDDC_EINVAL, "interface DoF without interface index");
+      gam_if[q] = m;
+      ikv.push_back({m, (int)q});
+    }
+  }
+  std::vector<int> if_ptr(C->n_if + 1, 0), if_src(ikv.size());
+  for (auto& e : ikv) if_ptr[e.first + 1]++;
+  for (int m = 0; m < C->n_if; ++m) if_ptr[m + 1] += if_ptr[m];
+  {
+    std::vector<int> fill(if_ptr.begin(), if_ptr.end() - 1);
+    for (auto& e : ikv) if_src[fill[e.first]++] = e.second;
+  }
+  // coarse rhs gather
+  std::vector<int> cg_ptr(C->n_pi + 1, 0), cg_src(C->totC);
+  for (int64_t q = 0; q < C->totC; ++q) cg_ptr[gprim[q] + 1]++;
+  for (int p = 0; p < C->n_pi; ++p) cg_ptr[p + 1] += cg_ptr[p];
+  {
+    std::vector<int> fill(cg_ptr.begin(), cg_ptr.end() - 1);
+    for (int64_t q = 0; q < C->totC; ++q) cg_src[fill[gprim[q]]++] = (int)q;
+  }
+
+  // packed storage layout
+  const int NB = SWEEP_NB;
+  C->ldA.assign(nsub, 0); C->ldS = C->ldPhi = C->ldY = C->ldG = C->ldA;
+  C->offA.assign(nsub + 1, 0); C->offS = C->offPhi = C->offY = C->offZ = C->offG = C->offSPhi =
+      C->offKc = C->offX = C->offYp = C->offP = C->offA;
+  for (int s = 0; s < nsub; ++s) {
+    const int cI = (int)round_up(C->nI[s], 4);
+    C->ldA[s] = (int)round_up(cI + C->nG[s], 8);
+    C->ldS[s] = (int)round_up(std::max(C->nG[s], 1), 8);
+    C->ldPhi[s] = (int)round_up(std::max(C->nc[s], 1), 4);
+    C->ldY[s] = (int)round_up(std::max(C->na[s], 1), 4);
+    C->ldG[s] = C->ldY[s];
+    C->offA[s + 1] = C->offA[s] + round_up((int64_t)C->ns[s] * C->ldA[s], kAlign);
+    C->offS[s + 1] = C->offS[s] + round_up((int64_t)C->nG[s] * C->ldS[s], kAlign);
+    C->offPhi[s + 1] = C->offPhi[s] + round_up((int64_t)C->nG[s] * C->ldPhi[s], kAlign);
+    C->offSPhi[s + 1] = C->offPhi[s + 1];
+    C->offY[s + 1] = C->offY[s] + round_up((int64_t)C->nr[s] * C->ldY[s], kAlign);
+    C->offZ[s + 1] = C->offZ[s] + round_up((int64_t)C->na[s] * C->ldS[s], kAlign);
+    C->offG[s + 1] = C->offG[s] + round_up((int64_t)C->na[s] * C->ldG[s], kAlign);
+    C->offKc[s + 1] = C->offKc[s] + round_up((int64_t)C->nc[s] * C->ldPhi[s], kAlign);
+    C->offX[s + 1] = C->offX[s] + round_up((int64_t)C->ns[s] * NB, kAlign);
+    C->offYp[s + 1] = C->offYp[s] + round_up((int64_t)NB * C->ldA[s], kAlign);
+    C->offP[s + 1] = C->offP[s] + NB * NB;
+    C->maxI = std::max(C->maxI, C->nI[s]);
+    C->maxG = std::max(C->maxG, C->nG[s]);
+    C->maxR = std::max(C->maxR, C->nr[s]);
+    C->maxNs = std::max(C->maxNs, C->ns[s]);
+    C->maxC = std::max(C->maxC, C->nc[s]);
+    C->maxA = std::max(C->maxA, C->na[s]);
+  }
+  const size_t es = C->esize;
+  C->Aloc.alloc(C->offA[nsub] * es);
+  C->Sw.alloc(std::max<int64_t>(C->offS[nsub], 1) * es);
+  C->Phi.alloc(std::max<int64_t>(C->offPhi[nsub], 1) * es);
+  C->SPhi.alloc(std::max<int64_t>(C->offPhi[nsub], 1) * es);
+  C->Y.alloc(std::max<int64_t>(C->offY[nsub], 1) * es);
+  C->Zf.alloc(std::max<int64_t>(C->offZ[nsub], 1) * es);
+  C->Wf.alloc(std::max<int64_t>(C->offZ[nsub], 1) * es);
+  C->G.alloc(std::max<int64_t>(C->offG[nsub], 1) * es);
+  C->Kc.alloc(std::max<int64_t>(C->offKc[nsub], 1) * es);
+  C->Xp.alloc(C->offX[nsub] * es);
+  C->Yp.alloc(C->offYp[nsub] * es);
+  C->Pd.alloc(C->offP[nsub] * es);
+
+  // sweep descriptors and GEMM problem lists
+  std::vector<SweepDesc> sw1(nsub), sw2(nsub);
+  for (int s = 0; s < nsub; ++s) {
+    sw1[s] = SweepDesc{C->ns[s], (int)round_up(C->nI[s], 4) + C->nG[s], C->ldA[s], C->nI[s],
+                       C->offA[s], C->offX[s], C->offYp[s], C->offP[s]};
+    sw2[s] = SweepDesc{C->nG[s], C->nG[s], C->ldS[s], C->nr[s], C->offS[s], C->offX[s], C->offYp[s],
+                       C->offP[s]};
+    C->steps1 = std::max(C->steps1, (int)cdiv(C->nI[s], NB));
+    C->steps2 = std::max(C->steps2, (int)cdiv(C->nr[s], NB));
+  }
+  C->sw1.upload(sw1);
+  C->sw2.upload(sw2);
+  auto sweep_gemms = [NB](const std::vector<SweepDesc>& sw, int steps) {
+    std::vector<GemmProb> g;
+    const int nmat = (int)sw.size();
+    for (int k = 0; k < steps; ++k)
+      for (int s = 0; s < nmat; ++s) {
+        const SweepDesc& d = sw[s];
+        const int kb = std::max(0, std::min(NB, d.p - k * NB));
+        g.push_back(GemmProb{d.rows, d.cols, kb, NB, d.ld, d.ld, d.offX, d.offY, d.off});
+      }
+    return g;
+  };
+  C->g_sw1.upload(sweep_gemms(sw1, C->steps1));
+  C->g_sw2.upload(sweep_gemms(sw2, C->steps2));
+  std::vector<GemmProb> gW, gT, gPA, gSP, gKc;
+  for (int s = 0; s < nsub; ++s) {
+    const int cI = (int)round_up(C->nI[s], 4);
+    gW.push_back(GemmProb{C->na[s], C->nG[s], C->na[s], C->ldG[s], C->ldS[s], C->ldS[s], C->offG[s],
+                          C->offZ[s], C->offZ[s]});
+    gT.push_back(GemmProb{C->nr[s], C->nG[s], C->na[s], C->ldY[s], C->ldS[s], C->ldS[s], C->offY[s],
+                          C->offZ[s], C->offS[s]});
+    gPA.push_back(GemmProb{C->nr[s], C->na[s], C->na[s], C->ldY[s], C->ldG[s], C->ldPhi[s], C->offY[s],
+                           C->offG[s], C->offPhi[s] + C->nv[s]});
+    gSP.push_back(GemmProb{C->nG[s], C->nc[s], C->nG[s], C->ldA[s], C->ldPhi[s], C->ldPhi[s],
+                           C->offA[s] + (int64_t)C->nI[s] * C->ldA[s] + cI, C->offPhi[s], C->offPhi[s]});
+    gKc.push_back(GemmProb{C->nc[s], C->nc[s], C->nG[s], C->ldPhi[s], C->ldPhi[s], C->ldPhi[s],
+                           C->offPhi[s], C->offPhi[s], C->offKc[s]});
+  }
+  C->g_W.upload(gW);
+  C->g_T.upload(gT);
+  C->g_PhiA.upload(gPA);
+  C->g_SPhi.upload(gSP);
+  C->g_Kc.upload(gKc);
+
+  // coarse matrix entries
+  if (C->n_pi > 0) {
+    std::vector<std::pair<int64_t, int>> ckv;
+    for (int s = 0; s < nsub; ++s)
+      for (int i = 0; i < C->nc[s]; ++i)
+        for (int j = 0; j < C->nc[s]; ++j)
+          ckv.push_back({(int64_t)gprim[C->offC[s] + i] * C->n_pi + gprim[C->offC[s] + j],
+                         (int)(C->offKc[s] + (int64_t)i * C->ldPhi[s] + j)});
+    std::sort(ckv.begin(), ckv.end());
+    std::vector<int> key, ptr{0}, src;
+    for (size_t i = 0; i < ckv.size();) {
+      size_t j = i;
+      while (j < ckv.size() && ckv[j].first == ckv[i].first) ++j;
+      key.push_back((int)ckv[i].first);
+      for (size_t q = i; q < j; ++q) src.push_back(ckv[q].second);
+      ptr.push_back((int)src.size());
+      i = j;
+    }
+    CB_CHECK((int64_t)C->n_pi * C->n_pi < INT32_MAX, CBDDC_EINVAL, "coarse space too large");
+    C->n_ce = (int64_t)key.size();
+    C->ce_key.upload(key);
+    C->ce_ptr.upload(ptr);
+    C->ce_src.upload(src);
+    C->Sc.alloc((size_t)C->n_pi * C->n_pi);
+    C->ScX.alloc((size_t)C->n_pi * NB);
+    C->ScY.alloc((size_t)C->n_pi * NB);
+    C->ScP.alloc((size_t)NB * NB);
+    std::vector<SweepDesc> swc{SweepDesc{C->n_pi, C->n_pi, C->n_pi, C->n_pi, 0, 0, 0, 0}};
+    C->swc.upload(swc);
+    C->stepsc = (int)cdiv(C->n_pi, NB);
+    C->g_swc.upload(sweep_gemms(swc, C->stepsc));
+  }
+
+  // device copies of sizes and maps
+  C->d_nI.upload(C->nI); C->d_nG.upload(C->nG); C->d_nr.upload(C->nr); C->d_nv.upload(C->nv);
+  C->d_na.upload(C->na); C->d_nc.upload(C->nc); C->d_ns.upload(C->ns);
+  C->d_ldA.upload(C->ldA); C->d_ldS.upload(C->ldS); C->d_ldPhi.upload(C->ldPhi);
+  C->d_ldY.upload(C->ldY); C->d_ldG.upload(C->ldG);
+  C->d_offA.upload(C->offA); C->d_offS.upload(C->offS); C->d_offPhi.upload(C->offPhi);
+  C->d_offY.upload(C->offY); C->d_offZ.upload(C->offZ); C->d_offG.upload(C->offG);
+  C->d_offSPhi.upload(C->offSPhi); C->d_offKc.upload(C->offKc);
+  C->d_offI.upload(C->offI); C->d_offGam.upload(C->offGam); C->d_offC.upload(C->offC);
+  C->d_offCon.upload(C->offCon); C->d_offN.upload(offN);
+  C->perm.upload(perm_h);
+  C->gdofI.upload(gdofI); C->gdofG.upload(gdofG); C->Dg.upload(Dg);
+  C->gam_if.upload(gam_if); C->if_dof.upload(if_dof); C->if_ptr.upload(if_ptr); C->if_src.upload(if_src);
+  C->cons_ptr.upload(cptr); C->cons_idx.upload(cidx); C->cons_w.upload(cw);
+  C->gprim.upload(gprim); C->cg_ptr.upload(cg_ptr); C->cg_src.upload(cg_src);
+  C->u0.alloc(std::max<int64_t>(C->totI, 1));
+  C->hG.alloc(std::max<int64_t>(C->totG, 1));
+  C->wG.alloc(std::max<int64_t>(C->totG, 1));
+  C->yG.alloc(std::max<int64_t>(C->totG, 1));
+  C->gI.alloc(std::max(C->n_if, 1));
+  C->cl.alloc(std::max<int64_t>(C->totC, 1));
+  C->rc.alloc(std::max(C->n_pi, 1));
+  C->uc.alloc(std::max(C->n_pi, 1));
+  C->gl.alloc(std::max<int64_t>(C->totG, 1));
+  // flops of one setup and bytes of local operators read per apply
+  double fl = 0.0;
+  int64_t lb = 0;
+  for (int s = 0; s < nsub; ++s) {
+    const double n = C->ns[s], ni = C->nI[s], ng = C->nG[s], nr = C->nr[s], na = C->na[s], nc = C->nc[s];
+    fl += 2.0 * n * (n) * ni + 2.0 * ng * ng * nr + 2.0 * na * na * ng + 2.0 * nr * na * ng +
+          2.0 * nr * na * na + 2.0 * ng * ng * nc + 2.0 * nc * nc * ng;
+    lb += (int64_t)((n * ni + ni * ng + nr * nr + 2.0 * ng * nc) * C->esize);
+  }
+  fl += 2.0 * (double)C->n_pi * C->n_pi * C->n_pi;
+  lb += (int64_t)C->n_pi * C->n_pi * 8;
+  C->setup_flops = fl;
+  C->local_bytes = lb;
+}
+
+// ------------------------------------------------------------------- setup
+template <typename T>
+static void run_sweep(const DVec<SweepDesc>& desc, int nmat, int steps, const DVec<GemmProb>& gp,
+                      int maxRows, int maxCols, T* mat, T* X, T* Y, T* Pbuf, int* status, double tol,
+                      cudaStream_t s) {
+  for (int k = 0; k < steps; ++k) {
+    sweep_diag_kernel<T><<<nmat, 256, 0, s>>>(desc.p, k, mat, Pbuf, status, tol);
+    CB_LAUNCH();
+    dim3 grid(cdiv(std::max(maxRows, maxCols), 64), nmat);
+    sweep_panel_kernel<T><<<grid, 256, 0, s>>>(desc.p, k, mat, Pbuf, X, Y);
+    CB_LAUNCH();
+    launch_gemm<T, false, false>(gp.p + (int64_t)k * nmat, nmat, maxRows, maxCols, X, Y, mat, T(-1), T(1), s);
+  }
+}
+
+template <typename T>
+static void setup_impl(bddc_ctx* C, cudaStream_t s) {
+  fem_problem* P = C->P;
+  const int nsub = C->nsub;
+  T* Aloc = reinterpret_cast<T*>(C->Aloc.p);
+  T* Sw = reinterpret_cast<T*>(C->Sw.p);
+  T* Phi = reinterpret_cast<T*>(C->Phi.p);
+  T* SPhi = reinterpret_cast<T*>(C->SPhi.p);
+  T* Y = reinterpret_cast<T*>(C->Y.p);
+  T* Zf = reinterpret_cast<T*>(C->Zf.p);
+  T* Wf = reinterpret_cast<T*>(C->Wf.p);
+  T* G = reinterpret_cast<T*>(C->G.p);
+  T* Kc = reinterpret_cast<T*>(C->Kc.p);
+  T* Xp = reinterpret_cast<T*>(C->Xp.p);
+  T* Yp = reinterpret_cast<T*>(C->Yp.p);
+  T* Pd = reinterpret_cast<T*>(C->Pd.p);
+  int* status = P->status.p;
+  const double tol = C->pivot_tol;
+  // 1. subdomain matrices
+  CB_CUDA(cudaMemsetAsync(C->Aloc.p, 0, C->Aloc.bytes(), s));
+  densify_kernel<T><<<cdiv(P->n_lslots * 9, 256), 256, 0, s>>>(
+      P->lslot_sub.p, P->lslot_row.p, P->lslot_col.p, P->lslot_ptr.p, P->lslot_src.p, P->contrib.p,
+      P->n_lslots, C->perm.p, C->d_offN.p, C->d_offA.p, C->d_ldA.p, C->d_nI.p, Aloc);
+  CB_LAUNCH();
+  // 2. sweep over the interior pivots
+  int maxCols = 0;
+  for (int q = 0; q < nsub; ++q) maxCols = std::max(maxCols, (int)round_up(C->nI[q], 4) + C->nG[q]);
+  run_sweep<T>(C->sw1, nsub, C->steps1, C->g_sw1, C->maxNs, maxCols, Aloc, Xp, Yp, Pd, status, tol, s);
+  if (C->maxG == 0) return;  // one subdomain: no interface
+  // 3. Schur complement copy and sweep over Gamma_r
+  copy_schur_kernel<T><<<dim3(cdiv((int64_t)C->maxG * C->maxG, 256), nsub), 256, 0, s>>>(
+      C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offS.p, C->d_ldS.p, Aloc, Sw);
+  CB_LAUNCH();
+  if (C->maxA > 0) {
+    augment_kernel<T><<<nsub, 256, 0, s>>>(C->d_nr.p, C->d_na.p, C->d_offCon.p, C->cons_ptr.p,
+                                          C->cons_idx.p, C->cons_w.p, C->d_offS.p, C->d_ldS.p, Sw);
+    CB_LAUNCH();
+  }
+  run_sweep<T>(C->sw2, nsub, C->steps2, C->g_sw2, C->maxG, C->maxG, Sw, Xp, Yp, Pd, status, tol, s);
+  // 4. average constraints
+  if (C->maxA > 0) {
+    cons_y_kernel<T><<<dim3(cdiv(C->maxR, 8), nsub), 256, 0, s>>>(
+        C->d_nr.p, C->d_na.p, C->d_offCon.p, C->cons_ptr.p, C->cons_idx.p, C->cons_w.p, C->d_offS.p,
+        C->d_ldS.p, C->d_offY.p, C->d_ldY.p, Sw, Y);
+    CB_LAUNCH();
+    cons_z_kernel<T><<<dim3(cdiv(C->maxG, 128), nsub), 128, 0, s>>>(
+        C->d_nG.p, C->d_na.p, C->d_offCon.p, C->cons_ptr.p, C->cons_idx.p, C->cons_w.p, C->d_offS.p,
+        C->d_ldS.p, C->d_offZ.p, Sw, Zf);
+    CB_LAUNCH();
+    cons_g_kernel<T><<<dim3(cdiv(C->maxA * C->maxA, 256), nsub), 256, 0, s>>>(
+        C->d_na.p, C->d_offCon.p, C->cons_ptr.p, C->cons_idx.p, C->cons_w.p, C->d_offY.p, C->d_ldY.p,
+        C->d_offG.p, C->d_ldG.p, Y, G);
+    CB_LAUNCH();
+    const size_t smem = (size_t)C->maxA * (C->maxA + 2) * sizeof(double);
+    if (smem > 48 * 1024)
+      CB_CUDA(cudaFuncSetAttribute(small_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+    small_inverse_kernel<T><<<nsub, 256, smem, s>>>(C->d_na.p, C->d_offG.p, C->d_ldG.p, G, status, tol);
+    CB_LAUNCH();
+    launch_gemm<T, false, false>(C->g_W.p, nsub, C->maxA, C->maxG, G, Zf, Wf, T(1), T(0), s);
+    launch_gemm<T, false, false>(C->g_T.p, nsub, C->maxR, C->maxG, Y, Wf, Sw, T(-1), T(1), s);
+    launch_gemm<T, false, false>(C->g_PhiA.p, nsub, C->maxR, C->maxA, Y, G, Phi, T(1), T(0), s);
+  }
+  // 5. vertex columns of Phi and the identity block
+  phi_vertex_kernel<T><<<dim3(cdiv((int64_t)C->maxG * C->maxC, 256), nsub), 256, 0, s>>>(
+      C->d_nG.p, C->d_nr.p, C->d_nv.p, C->d_nc.p, C->d_offS.p, C->d_ldS.p, C->d_offPhi.p, C->d_ldPhi.p,
+      Sw, Phi);
+  CB_LAUNCH();
+  // 6. local coarse matrices Phi^T S Phi and the FP64 coarse inverse
+  if (C->n_pi > 0) {
+    launch_gemm<T, false, false>(C->g_SPhi.p, nsub, C->maxG, C->maxC, Aloc, Phi, SPhi, T(1), T(0), s);
+    launch_gemm<T, true, false>(C->g_Kc.p, nsub, C->maxC, C->maxC, Phi, SPhi, Kc, T(1), T(0), s);
+    CB_CUDA(cudaMemsetAsync(C->Sc.p, 0, C->Sc.bytes(), s));
+    if (sizeof(T) == 4)
+      coarse_assemble_kernel_f<<<cdiv(C->n_ce, 256), 256, 0, s>>>(
+          C->ce_key.p, C->ce_ptr.p, C->ce_src.p, C->n_ce, reinterpret_cast<const float*>(Kc), C->Sc.p);
+    else
+      coarse_assemble_kernel_d<<<cdiv(C->n_ce, 256), 256, 0, s>>>(
+          C->ce_key.p, C->ce_ptr.p, C->ce_src.p, C->n_ce, reinterpret_cast<const double*>(Kc), C->Sc.p);
+    CB_LAUNCH();
+    run_sweep<double>(C->swc, 1, C->stepsc, C->g_swc, C->n_pi, C->n_pi, C->Sc.p, C->ScX.p, C->ScY.p,
+                      C->ScP.p, status, tol, s);
+  }
+}
+
+void bddc_run_setup(bddc_ctx* C, cudaStream_t s) {
+  if (C->precision == CBDDC_FP32) setup_impl<float>(C, s);
+  else setup_impl<double>(C, s);
+}
+
+// ------------------------------------------------------------------- apply
+template <typename T>
+static void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
+  const int nsub = C->nsub;
+  const T* Aloc = reinterpret_cast<const T*>(C->Aloc.p);
+  const T* Sw = reinterpret_cast<const T*>(C->Sw.p);
+  const T* Phi = reinterpret_cast<const T*>(C->Phi.p);
+  double* gl = C->gl.p;
+  apply_interior_kernel<T><<<dim3(cdiv(C->maxNs, AROWS), nsub), 256,
+                             (size_t)round_up(std::max(C->maxI, 4), 4) * sizeof(T), s>>>(
+      C->d_nI.p, C->d_ns.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, Aloc, r,
+      C->u0.p, C->hG.p);
+  CB_LAUNCH();
+  if (C->n_if > 0) {
+    assemble_g_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
+                                                        r, C->hG.p, C->gI.p);
+    CB_LAUNCH();
+    restrict_kernel<<<cdiv(C->totG, 256), 256, 0, s>>>(C->gam_if.p, C->Dg.p, C->totG, C->gI.p, gl);
+    CB_LAUNCH();
+    apply_local_kernel<T><<<dim3(cdiv(C->maxG, AROWS), nsub), 256,
+                            (size_t)round_up(std::max(C->maxR, 4), 4) * sizeof(T), s>>>(
+        C->d_nG.p, C->d_nr.p, C->d_offS.p, C->d_ldS.p, C->d_offGam.p, Sw, gl, C->wG.p);
+    CB_LAUNCH();
+    if (C->n_pi > 0) {
+      apply_phit_kernel<T><<<nsub, 256, 0, s>>>(C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p,
+                                                C->d_offGam.p, C->d_offC.p, Phi, gl, C->cl.p);
+      CB_LAUNCH();
+      gather_sum_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, C->cl.p,
+                                                           C->rc.p);
+      CB_LAUNCH();
+      dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, C->rc.p,
+                                                                         C->uc.p);
+      CB_LAUNCH();
+    }
+    apply_prolong_kernel<T><<<dim3(cdiv(C->maxG, AROWS), nsub), 256, 0, s>>>(
+        C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, C->gprim.p, Phi,
+        C->uc.p, C->wG.p, C->Dg.p, C->yG.p);
+    CB_LAUNCH();
+    average_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
+                                                     C->yG.p, z);
+    CB_LAUNCH();
+  }
+  apply_extend_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), AROWS), nsub), 256,
+                           (size_t)round_up(std::max(C->maxG, 4), 4) * sizeof(T), s>>>(
+      C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, C->gdofG.p,
+      Aloc, C->u0.p, z);
+  CB_LAUNCH();
+}
+
+void bddc_run_apply(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
+  if (C->precision == CBDDC_FP32) apply_impl<float>(C, r, z, s);
+  else apply_impl<double>(C, r, z, s);
+}
+
+}  // namespace cbddc
+
+int64_t bddc_ctx::device_bytes() const {
+  return (int64_t)(Aloc.bytes() + Sw.bytes() + Phi.bytes() + Y.bytes() + Zf.bytes() + Wf.bytes() +
+                   G.bytes() + SPhi.bytes() + Kc.bytes() + Xp.bytes() + Yp.bytes() + Pd.bytes() +
+                   Sc.bytes() + ScX.bytes() + ScY.bytes() + ScP.bytes() + u0.bytes() + hG.bytes() +
+                   gI.bytes() + wG.bytes() + cl.bytes() + rc.bytes() + uc.bytes() + yG.bytes() + gl.bytes());
+}

@@ -1,0 +1,314 @@
+// Flexible GMRES (FP64) preconditioned by BDDC, and the Newton iteration of
+// Eq. (tangent problem): d^{n,k} = d^{n,k-1} + delta, DF(d) delta = -F(d).
+//
+// GMRES: Arnoldi basis V (column j contiguous), preconditioned vectors
+// Z_j = M^-1 v_j, classical Gram-Schmidt applied twice (two passes of
+// h = V^T w, w -= V h), Givens rotations and the least-squares residual
+// |g_{j+1}| kept on the device; restart after m steps with the true
+// residual recomputed.
+#include <cmath>
+
+#include "bddc.h"
+#include "fem.h"
+#include "krylov.h"
+
+namespace cbddc {
+
+namespace {
+
+constexpr int DOT_ROWS = 1024;  // rows per CTA in the block dot products
+constexpr int MAXV = 128;       // maximum Krylov vectors per dot launch
+
+__device__ inline double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial[c][j] = sum over rows of chunk c of V_j[row] * w[row]
+__global__ void __launch_bounds__(256)
+block_dots_kernel(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ w,
+                  int64_t n, double* __restrict__ partial, const int* __restrict__ done) {
+  if (done && *done) return;
+  __shared__ double red[8][MAXV];
+  const int64_t r0 = (int64_t)blockIdx.x * DOT_ROWS;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  double wv[DOT_ROWS / 256];
+#pragma unroll
+  for (int t = 0; t < DOT_ROWS / 256; ++t) {
+    const int64_t row = r0 + tid + 256 * t;
+    wv[t] = row < n ? w[row] : 0.0;
+  }
+  for (int j = 0; j < nvec; ++j) {
+    const double* v = V + (int64_t)j * ldv;
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < DOT_ROWS / 256; ++t) {
+      const int64_t row = r0 + tid + 256 * t;
+      if (row < n) acc += v[row] * wv[t];
+    }
+    acc = wsum(acc);
+    if (lane == 0) red[warp][j] = acc;
+  }
+  __syncthreads();
+  for (int j = tid; j < nvec; j += 256) {
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += red[q][j];
+    partial[(int64_t)blockIdx.x * MAXV + j] = s;
+  }
+}
+
+// out[j] (+)= sum_c partial[c][j]
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nchunks, int nvec,
+                                       double* __restrict__ out, int accumulate,
+                                       const int* __restrict__ done) {
+  if (done && *done) return;
+  const int j = threadIdx.x;
+  if (j >= nvec) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += partial[(int64_t)c * MAXV + j];
+  out[j] = accumulate ? out[j] + s : s;
+}
+
+// w -= V h
+__global__ void update_kernel(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ h,
+                              double* __restrict__ w, int64_t n, const int* __restrict__ done) {
+  if (done && *done) return;
+  __shared__ double hs[MAXV];
+  for (int j = threadIdx.x; j < nvec; j += blockDim.x) hs[j] = h[j];
+  __syncthreads();
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  double acc = w[row];
+  for (int j = 0; j < nvec; ++j) acc -= V[(int64_t)j * ldv + row] * hs[j];
+  w[row] = acc;
+}
+
+// Column j of the Hessenberg matrix from h1 + h2 (the two CGS passes) and
+// ||w||^2, previous rotations, the new rotation and the residual estimate.
+// scal[0] = |g_{j+1}| / ||b||, scal[1] = 1 / h_{j+1,j}, scal[2] = ||b||.
+__global__ void givens_kernel(int j, int m, double* __restrict__ H, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g,
+                              const double* __restrict__ h, const double* __restrict__ wn2,
+                              double* __restrict__ scal, double rtol, int* __restrict__ done,
+                              int* __restrict__ iters) {
+  if (*done) return;
+  double* col = H + (int64_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = h[i];
+  const double hn = sqrt(fmax(wn2[0], 0.0));
+  col[j + 1] = hn;
+  scal[1] = hn > 0.0 ? 1.0 / hn : 0.0;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  cs[j] = den > 0.0 ? col[j] / den : 1.0;
+  sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  const double res = fabs(g[j + 1]) / scal[2];
+  scal[0] = res;
+  *iters += 1;
+  if (res <= rtol || hn == 0.0) *done = 1;
+}
+
+__global__ void scale_kernel(const double* __restrict__ w, double* __restrict__ v, int64_t n,
+                             const double* __restrict__ scal, int idx, const int* __restrict__ done) {
+  if (done && *done) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) v[i] = w[i] * scal[idx];
+}
+
+// y = R^-1 g (upper triangular, k columns), single thread
+__global__ void backsolve_kernel(const double* __restrict__ H, int m, const int* __restrict__ kp,
+                                 const double* __restrict__ g, double* __restrict__ y) {
+  const int k = *kp;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int c = i + 1; c < k; ++c) s -= H[(int64_t)c * (m + 1) + i] * y[c];
+    y[i] = s / H[(int64_t)i * (m + 1) + i];
+  }
+}
+
+// x += Z y  (k = number of columns)
+__global__ void combine_kernel(const double* __restrict__ Z, int64_t ldz, const int* __restrict__ kp,
+                               const double* __restrict__ y, double* __restrict__ x, int64_t n) {
+  __shared__ double ys[MAXV];
+  const int k = *kp;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
+  __syncthreads();
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  double acc = x[row];
+  for (int j = 0; j < k; ++j) acc += Z[(int64_t)j * ldz + row] * ys[j];
+  x[row] = acc;
+}
+
+__global__ void axpby_kernel(double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                             double* __restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+// start of a cycle: beta = ||r|| -> g = (beta, 0, ...), scal[1] = 1/beta;
+// the first cycle also records ||b||.
+__global__ void cycle_start_kernel(const double* __restrict__ rn2, double* __restrict__ g, int m,
+                                   double* __restrict__ scal, int first, double rtol,
+                                   int* __restrict__ done, int* __restrict__ kcount) {
+  const double beta = sqrt(fmax(rn2[0], 0.0));
+  if (first) scal[2] = beta;
+  for (int i = 0; i <= m; ++i) g[i] = 0.0;
+  g[0] = beta;
+  scal[1] = beta > 0.0 ? 1.0 / beta : 0.0;
+  scal[0] = scal[2] > 0.0 ? beta / scal[2] : 0.0;
+  *kcount = 0;
+  *done = (beta <= rtol * scal[2]) ? 1 : 0;
+}
+
+}  // namespace
+
+void Gmres::ensure_small(int64_t n_) {
+  if (partial.p && nchunks == (int)cdiv(n_, DOT_ROWS)) return;
+  nchunks = (int)cdiv(n_, DOT_ROWS);
+  partial.alloc((size_t)nchunks * MAXV);
+  h.alloc(3 * MAXV);
+  scal.alloc(8);
+  flags.alloc(4);
+  if (!host_scal) CB_CUDA(cudaMallocHost(&host_scal, 64));
+  if (!host_flags) CB_CUDA(cudaMallocHost(&host_flags, 16));
+}
+
+void Gmres::ensure(int64_t n_, int m_) {
+  ensure_small(n_);
+  if (n == n_ && m == m_) return;
+  CB_CHECK(m_ >= 1 && m_ < MAXV, CBDDC_EINVAL, "restart must be in [1, 127]");
+  n = n_;
+  m = m_;
+  V.alloc((size_t)(m + 1) * n);
+  Zb.alloc((size_t)m * n);
+  w.alloc(n);
+  r.alloc(n);
+  H.alloc((size_t)(m + 1) * m);
+  cs.alloc(m);
+  sn.alloc(m);
+  g.alloc(m + 1);
+  y.alloc(m);
+}
+
+Gmres::~Gmres() {
+  if (host_scal) cudaFreeHost(host_scal);
+  if (host_flags) cudaFreeHost(host_flags);
+}
+
+// dot products of nvec columns of V (stride n) with w into out (+=)
+static void block_dots(Gmres& G, const double* V, int nvec, const double* w, double* out, int accumulate,
+                       const int* done, cudaStream_t s) {
+  block_dots_kernel<<<G.nchunks, 256, 0, s>>>(V, G.n, nvec, w, G.n, G.partial.p, done);
+  CB_LAUNCH();
+  reduce_partials_kernel<<<1, MAXV, 0, s>>>(G.partial.p, G.nchunks, nvec, out, accumulate, done);
+  CB_LAUNCH();
+}
+
+int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x, int restart,
+              int max_iters, double rtol, int* iters_out, double* relres_out, cudaStream_t s) {
+  const int64_t n = P->n_free;
+  G.ensure(n, restart);
+  const int m = restart;
+  const unsigned nb = cdiv(n, 256);
+  int* done = G.flags.p;
+  int* kcount = G.flags.p + 1;
+  CB_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  int total = 0;
+  bool first = true;
+  int* hflags = G.host_flags;
+  bool converged = false;
+  while (true) {
+    // r = b - K x
+    if (first) {
+      CB_CUDA(cudaMemcpyAsync(G.r.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      bsr_spmv(P, x, G.w.p, s);
+      axpby_kernel<<<nb, 256, 0, s>>>(1.0, b, -1.0, G.w.p, G.r.p, n);
+      CB_LAUNCH();
+    }
+    block_dots(G, G.r.p, 1, G.r.p, G.h.p, 0, nullptr, s);
+    cycle_start_kernel<<<1, 1, 0, s>>>(G.h.p, G.g.p, m, G.scal.p, first ? 1 : 0, rtol, done, kcount);
+    CB_LAUNCH();
+    scale_kernel<<<nb, 256, 0, s>>>(G.r.p, G.V.p, n, G.scal.p, 1, nullptr);
+    CB_LAUNCH();
+    CB_CUDA(cudaMemcpyAsync(G.host_scal, G.scal.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CB_CUDA(cudaMemcpyAsync(hflags, done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CB_CUDA(cudaStreamSynchronize(s));
+    first = false;
+    *relres_out = G.host_scal[0];
+    if (hflags[0]) { converged = true; break; }
+    if (total >= max_iters) break;
+    int j = 0;
+    for (; j < m && total < max_iters; ++j) {
+      double* vj = G.V.p + (int64_t)j * n;
+      double* zj = G.Zb.p + (int64_t)j * n;
+      bddc_run_apply(C, vj, zj, s);
+      bsr_spmv(P, zj, G.w.p, s);
+      // classical Gram-Schmidt, twice
+      block_dots(G, G.V.p, j + 1, G.w.p, G.h.p, 0, done, s);
+      update_kernel<<<nb, 256, 0, s>>>(G.V.p, n, j + 1, G.h.p, G.w.p, n, done);
+      CB_LAUNCH();
+      block_dots(G, G.V.p, j + 1, G.w.p, G.h.p + MAXV, 0, done, s);
+      update_kernel<<<nb, 256, 0, s>>>(G.V.p, n, j + 1, G.h.p + MAXV, G.w.p, n, done);
+      CB_LAUNCH();
+      axpby_kernel<<<1, MAXV, 0, s>>>(1.0, G.h.p, 1.0, G.h.p + MAXV, G.h.p, j + 1);
+      CB_LAUNCH();
+      block_dots(G, G.w.p, 1, G.w.p, G.h.p + 2 * MAXV, 0, done, s);
+      givens_kernel<<<1, 1, 0, s>>>(j, m, G.H.p, G.cs.p, G.sn.p, G.g.p, G.h.p, G.h.p + 2 * MAXV, G.scal.p,
+                                    rtol, done, kcount);
+      CB_LAUNCH();
+      scale_kernel<<<nb, 256, 0, s>>>(G.w.p, G.V.p + (int64_t)(j + 1) * n, n, G.scal.p, 1, done);
+      CB_LAUNCH();
+      CB_CUDA(cudaMemcpyAsync(hflags, done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CB_CUDA(cudaStreamSynchronize(s));
+      ++total;
+      if (hflags[0]) { ++j; break; }
+    }
+    // x += Z y over the columns built in this cycle
+    backsolve_kernel<<<1, 1, 0, s>>>(G.H.p, m, kcount, G.g.p, G.y.p);
+    CB_LAUNCH();
+    combine_kernel<<<nb, 256, 0, s>>>(G.Zb.p, n, kcount, G.y.p, x, n);
+    CB_LAUNCH();
+    if (total >= max_iters && !hflags[0]) {
+      // final true residual
+      bsr_spmv(P, x, G.w.p, s);
+      axpby_kernel<<<nb, 256, 0, s>>>(1.0, b, -1.0, G.w.p, G.r.p, n);
+      CB_LAUNCH();
+      block_dots(G, G.r.p, 1, G.r.p, G.h.p, 0, nullptr, s);
+      CB_CUDA(cudaMemcpyAsync(G.host_scal + 4, G.h.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CB_CUDA(cudaMemcpyAsync(G.host_scal, G.scal.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CB_CUDA(cudaStreamSynchronize(s));
+      *relres_out = G.host_scal[2] > 0 ? std::sqrt(G.host_scal[4]) / G.host_scal[2] : 0.0;
+      break;
+    }
+    // next cycle (or final check) recomputes the true residual
+  }
+  *iters_out = total;
+  return converged ? CBDDC_OK : CBDDC_ENOCONV;
+}
+
+double device_norm(fem_problem* P, Gmres& G, const double* v, cudaStream_t s) {
+  G.ensure_small(P->n_free);
+  block_dots_kernel<<<G.nchunks, 256, 0, s>>>(v, P->n_free, 1, v, P->n_free, G.partial.p, nullptr);
+  CB_LAUNCH();
+  reduce_partials_kernel<<<1, MAXV, 0, s>>>(G.partial.p, G.nchunks, 1, G.h.p, 0, nullptr);
+  CB_LAUNCH();
+  CB_CUDA(cudaMemcpyAsync(G.host_scal + 4, G.h.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
+  return std::sqrt(G.host_scal[4]);
+}
+
+void axpby(double a, const double* x, double b, const double* y, double* out, int64_t n, cudaStream_t s) {
+  axpby_kernel<<<cdiv(n, 256), 256, 0, s>>>(a, x, b, y, out, n);
+  CB_LAUNCH();
+}
+
+}  // namespace cbddc

@@ -1,0 +1,30 @@
+// GMRES workspace and Newton helpers (internal).
+#pragma once
+#include "common.h"
+
+struct bddc_ctx;
+
+namespace cbddc {
+
+struct Gmres {
+  int64_t n = 0;
+  int m = 0;
+  int nchunks = 0;
+  DVec<double> V, Zb, w, r, H, cs, sn, g, y, h, partial, scal;
+  DVec<int> flags;
+  double* host_scal = nullptr;
+  int* host_flags = nullptr;
+  void ensure_small(int64_t n_);
+  void ensure(int64_t n_, int m_);
+  Gmres() = default;
+  Gmres(const Gmres&) = delete;
+  Gmres& operator=(const Gmres&) = delete;
+  ~Gmres();
+};
+
+int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x, int restart,
+              int max_iters, double rtol, int* iters_out, double* relres_out, cudaStream_t s);
+double device_norm(fem_problem* P, Gmres& G, const double* v, cudaStream_t s);
+void axpby(double a, const double* x, double b, const double* y, double* out, int64_t n, cudaStream_t s);
+
+}  // namespace cbddc
