@@ -288,6 +288,31 @@ CBDDC_API int newton_step_host(fem_problem* P, bddc_ctx** ctx, const solve_optio
 CBDDC_API int newton_gmres_solve(fem_problem* P, const solve_options* opt, double* d,
                        solve_report* rep, cbddc_stream_t stream);
 
+/* ------------------------------------------------------- observability */
+
+/* Number of kernels this library has launched since it was loaded. */
+CBDDC_API uint64_t cbddc_kernel_launches(void);
+
+/* Kernel classes that the launch timer can follow. */
+enum {
+  CBDDC_TIMER_OFF = 0,
+  CBDDC_TIMER_SWEEP_GEMM = 1, /* trailing updates of the Gauss-Jordan sweeps */
+  CBDDC_TIMER_ELEMENT = 2,    /* element residual/tangent kernel              */
+  CBDDC_TIMER_APPLY = 3,      /* one whole BDDC apply (all its launches)      */
+  CBDDC_TIMER_SPMV = 4        /* BSR SpMV                                     */
+};
+
+/* Starts recording CUDA events around every launch of the given class, on
+   the stream the launch uses (at most 65536 launches are recorded).  Each
+   recorded launch also adds its algorithmic flops and bytes.  Host-side
+   state, not thread safe. */
+CBDDC_API int cbddc_timer_start(int kernel_class);
+
+/* Stops recording, waits for the recorded events and returns the summed
+   device time (ms), the number of launches and their algorithmic flops and
+   bytes. */
+CBDDC_API int cbddc_timer_stop(double* total_ms, int64_t* launches, double* flops, double* bytes);
+
 /* Message for the last non-zero status returned on this thread. */
 CBDDC_API const char* cbddc_last_error(void);
 

@@ -34,8 +34,10 @@ EXPORTED_SYMBOLS = [
     "fem_residual", "fem_assemble_tangent", "fem_tangent_copy", "fem_spmv",
     "bddc_setup", "bddc_apply", "bddc_destroy", "bddc_get_info",
     "gmres_solve", "newton_step", "newton_step_host", "newton_gmres_solve",
+    "cbddc_kernel_launches", "cbddc_timer_start", "cbddc_timer_stop",
     "cbddc_last_error",
 ]
+TIMER_OFF, TIMER_SWEEP_GEMM, TIMER_ELEMENT, TIMER_APPLY, TIMER_SPMV = range(5)
 
 
 def primal_mask(spec):
@@ -164,6 +166,10 @@ def load_library():
                                      ctypes.POINTER(_Record), vp]),
         "newton_gmres_solve": (c_int, [vp, ctypes.POINTER(_SolveOptions), vp, ctypes.POINTER(_Report), vp]),
         "cbddc_last_error": (ctypes.c_char_p, []),
+        "cbddc_kernel_launches": (ctypes.c_uint64, []),
+        "cbddc_timer_start": (c_int, [c_int]),
+        "cbddc_timer_stop": (c_int, [ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -171,6 +177,25 @@ def load_library():
         f.argtypes = args
     _LIB = lib
     return lib
+
+
+def kernel_launches():
+    """Kernels launched by the library since it was loaded."""
+    return int(load_library().cbddc_kernel_launches())
+
+
+def timer_start(kernel_class):
+    """Record CUDA events around every launch of one kernel class."""
+    _check(load_library().cbddc_timer_start(int(kernel_class)))
+
+
+def timer_stop():
+    """Returns dict(ms, launches, flops, bytes) of the recorded launches."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    fl, by = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().cbddc_timer_stop(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl),
+                                           ctypes.byref(by)))
+    return {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
 
 
 def _check(rc):

@@ -686,19 +686,25 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   }
   C->sw1.upload(sw1);
   C->sw2.upload(sw2);
-  auto sweep_gemms = [NB](const std::vector<SweepDesc>& sw, int steps) {
+  const double eb = (double)C->esize;
+  auto sweep_gemms = [NB, eb](const std::vector<SweepDesc>& sw, int steps, std::vector<double>& fl) {
     std::vector<GemmProb> g;
     const int nmat = (int)sw.size();
+    fl.assign(2 * steps, 0.0);
     for (int k = 0; k < steps; ++k)
       for (int s = 0; s < nmat; ++s) {
         const SweepDesc& d = sw[s];
         const int kb = std::max(0, std::min(NB, d.p - k * NB));
         g.push_back(GemmProb{d.rows, d.cols, kb, NB, d.ld, d.ld, d.offX, d.offY, d.off});
+        if (kb > 0) {
+          fl[2 * k] += 2.0 * d.rows * d.cols * kb;
+          fl[2 * k + 1] += eb * (2.0 * d.rows * d.cols + (double)kb * (d.rows + d.cols));
+        }
       }
     return g;
   };
-  C->g_sw1.upload(sweep_gemms(sw1, C->steps1));
-  C->g_sw2.upload(sweep_gemms(sw2, C->steps2));
+  C->g_sw1.upload(sweep_gemms(sw1, C->steps1, C->fl_sw1));
+  C->g_sw2.upload(sweep_gemms(sw2, C->steps2, C->fl_sw2));
   std::vector<GemmProb> gW, gT, gPA, gSP, gKc;
   for (int s = 0; s < nsub; ++s) {
     const int cI = (int)round_up(C->nI[s], 4);
@@ -749,7 +755,8 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     std::vector<SweepDesc> swc{SweepDesc{C->n_pi, C->n_pi, C->n_pi, C->n_pi, 0, 0, 0, 0}};
     C->swc.upload(swc);
     C->stepsc = (int)cdiv(C->n_pi, NB);
-    C->g_swc.upload(sweep_gemms(swc, C->stepsc));
+    C->g_swc.upload(sweep_gemms(swc, C->stepsc, C->fl_swc));
+    for (size_t i = 1; i < C->fl_swc.size(); i += 2) C->fl_swc[i] *= 8.0 / eb;  // coarse is FP64
   }
 
   // device copies of sizes and maps
@@ -789,20 +796,24 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   lb += (int64_t)C->n_pi * C->n_pi * 8;
   C->setup_flops = fl;
   C->local_bytes = lb;
+  C->apply_flops = (double)lb / (double)C->esize * 2.0;
 }
 
 // ------------------------------------------------------------------- setup
 template <typename T>
 static void run_sweep(const DVec<SweepDesc>& desc, int nmat, int steps, const DVec<GemmProb>& gp,
-                      int maxRows, int maxCols, T* mat, T* X, T* Y, T* Pbuf, int* status, double tol,
-                      cudaStream_t s) {
+                      const std::vector<double>& step_flops, int maxRows, int maxCols, T* mat, T* X, T* Y,
+                      T* Pbuf, int* status, double tol, cudaStream_t s) {
   for (int k = 0; k < steps; ++k) {
     sweep_diag_kernel<T><<<nmat, 256, 0, s>>>(desc.p, k, mat, Pbuf, status, tol);
     CB_LAUNCH();
     dim3 grid(cdiv(std::max(maxRows, maxCols), 64), nmat);
     sweep_panel_kernel<T><<<grid, 256, 0, s>>>(desc.p, k, mat, Pbuf, X, Y);
     CB_LAUNCH();
+    timer_begin(CBDDC_TIMER_SWEEP_GEMM, s);
     launch_gemm<T, false, false>(gp.p + (int64_t)k * nmat, nmat, maxRows, maxCols, X, Y, mat, T(-1), T(1), s);
+    // flops: 2 M N K per problem; bytes: C read and written, X and Y read once
+    timer_end(CBDDC_TIMER_SWEEP_GEMM, s, step_flops[2 * k], step_flops[2 * k + 1]);
   }
 }
 
@@ -833,7 +844,7 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
   // 2. sweep over the interior pivots
   int maxCols = 0;
   for (int q = 0; q < nsub; ++q) maxCols = std::max(maxCols, (int)round_up(C->nI[q], 4) + C->nG[q]);
-  run_sweep<T>(C->sw1, nsub, C->steps1, C->g_sw1, C->maxNs, maxCols, Aloc, Xp, Yp, Pd, status, tol, s);
+  run_sweep<T>(C->sw1, nsub, C->steps1, C->g_sw1, C->fl_sw1, C->maxNs, maxCols, Aloc, Xp, Yp, Pd, status, tol, s);
   if (C->maxG == 0) return;  // one subdomain: no interface
   // 3. Schur complement copy and sweep over Gamma_r
   copy_schur_kernel<T><<<dim3(cdiv((int64_t)C->maxG * C->maxG, 256), nsub), 256, 0, s>>>(
@@ -844,7 +855,7 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
                                           C->cons_idx.p, C->cons_w.p, C->d_offS.p, C->d_ldS.p, Sw);
     CB_LAUNCH();
   }
-  run_sweep<T>(C->sw2, nsub, C->steps2, C->g_sw2, C->maxG, C->maxG, Sw, Xp, Yp, Pd, status, tol, s);
+  run_sweep<T>(C->sw2, nsub, C->steps2, C->g_sw2, C->fl_sw2, C->maxG, C->maxG, Sw, Xp, Yp, Pd, status, tol, s);
   // 4. average constraints
   if (C->maxA > 0) {
     cons_y_kernel<T><<<dim3(cdiv(C->maxR, 8), nsub), 256, 0, s>>>(
@@ -886,8 +897,8 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
       coarse_assemble_kernel_d<<<cdiv(C->n_ce, 256), 256, 0, s>>>(
           C->ce_key.p, C->ce_ptr.p, C->ce_src.p, C->n_ce, reinterpret_cast<const double*>(Kc), C->Sc.p);
     CB_LAUNCH();
-    run_sweep<double>(C->swc, 1, C->stepsc, C->g_swc, C->n_pi, C->n_pi, C->Sc.p, C->ScX.p, C->ScY.p,
-                      C->ScP.p, status, tol, s);
+    run_sweep<double>(C->swc, 1, C->stepsc, C->g_swc, C->fl_swc, C->n_pi, C->n_pi, C->Sc.p, C->ScX.p,
+                      C->ScY.p, C->ScP.p, status, tol, s);
   }
 }
 
@@ -946,8 +957,10 @@ static void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) 
 }
 
 void bddc_run_apply(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
+  timer_begin(CBDDC_TIMER_APPLY, s);
   if (C->precision == CBDDC_FP32) apply_impl<float>(C, r, z, s);
   else apply_impl<double>(C, r, z, s);
+  timer_end(CBDDC_TIMER_APPLY, s, C->apply_flops, (double)C->local_bytes);
 }
 
 }  // namespace cbddc

@@ -42,7 +42,8 @@ struct bddc_ctx {
   cbddc::DVec<cbddc::GemmProb> g_sw1, g_sw2, g_swc, g_W, g_T, g_PhiA, g_SPhi, g_Kc;
   int nprob_cons = 0, maxMW = 0, maxNW = 0;
   cbddc::DVec<double> gl;                  // scaled interface restriction
-  double setup_flops = 0.0;
+  double setup_flops = 0.0, apply_flops = 0.0;
+  std::vector<double> fl_sw1, fl_sw2, fl_swc;  // per sweep step: flops, bytes
   int64_t local_bytes = 0;
   // Krylov and Newton workspaces (allocated on first use)
   cbddc::Gmres gm;

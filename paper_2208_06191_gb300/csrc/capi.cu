@@ -2,6 +2,7 @@
 // error capture (no exception crosses the boundary) and the Newton drivers
 // of Section 2 (load steps, Newton on Eq. tangent problem).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <new>
 #include <string>
@@ -14,6 +15,42 @@ namespace cbddc {
 
 static thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Launch timer: event pairs recorded on the launching stream.
+namespace {
+struct Timer {
+  int kernel_class = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  int64_t launches = 0;
+  double flops = 0.0, bytes = 0.0;
+  static constexpr size_t kMax = 65536;
+} g_timer;
+}  // namespace
+
+bool timer_active(int kernel_class) { return g_timer.kernel_class == kernel_class && kernel_class != 0; }
+
+void timer_begin(int kernel_class, cudaStream_t s) {
+  if (!timer_active(kernel_class) || g_timer.used + 2 > Timer::kMax) return;
+  while (g_timer.pool.size() < g_timer.used + 2) {
+    cudaEvent_t e;
+    CB_CUDA(cudaEventCreate(&e));
+    g_timer.pool.push_back(e);
+  }
+  CB_CUDA(cudaEventRecord(g_timer.pool[g_timer.used], s));
+}
+
+void timer_end(int kernel_class, cudaStream_t s, double flops, double bytes) {
+  if (!timer_active(kernel_class) || g_timer.used + 2 > Timer::kMax) return;
+  CB_CUDA(cudaEventRecord(g_timer.pool[g_timer.used + 1], s));
+  g_timer.used += 2;
+  g_timer.launches += 1;
+  g_timer.flops += flops;
+  g_timer.bytes += bytes;
+}
 
 template <typename F>
 static int guard(F&& f) {
@@ -404,5 +441,35 @@ int newton_gmres_solve(fem_problem* P, const solve_options* opt, double* d, solv
 }
 
 const char* cbddc_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t cbddc_kernel_launches(void) { return g_launches.load(); }
+
+int cbddc_timer_start(int kernel_class) {
+  return guard([&] {
+    CB_CHECK(kernel_class >= 0 && kernel_class <= CBDDC_TIMER_SPMV, CBDDC_EINVAL, "bad kernel class");
+    g_timer.kernel_class = kernel_class;
+    g_timer.used = 0;
+    g_timer.launches = 0;
+    g_timer.flops = g_timer.bytes = 0.0;
+  });
+}
+
+int cbddc_timer_stop(double* total_ms, int64_t* launches, double* flops, double* bytes) {
+  return guard([&] {
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < g_timer.used; i += 2) {
+      CB_CUDA(cudaEventSynchronize(g_timer.pool[i + 1]));
+      float v = 0.f;
+      CB_CUDA(cudaEventElapsedTime(&v, g_timer.pool[i], g_timer.pool[i + 1]));
+      ms += v;
+    }
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = g_timer.launches;
+    if (flops) *flops = g_timer.flops;
+    if (bytes) *bytes = g_timer.bytes;
+    g_timer.kernel_class = 0;
+    g_timer.used = 0;
+  });
+}
 
 }  // extern "C"

@@ -35,7 +35,18 @@ void set_last_error(const std::string& msg);
     if (!(cond)) throw ::cbddc::Error{(code), (msg)};                        \
   } while (0)
 
-#define CB_LAUNCH() CB_CUDA(cudaGetLastError())
+// Counts every kernel launch of the library and checks the launch status.
+void count_launch();
+#define CB_LAUNCH()                       \
+  do {                                    \
+    ::cbddc::count_launch();              \
+    CB_CUDA(cudaGetLastError());          \
+  } while (0)
+
+// Optional CUDA-event timing of one kernel class (see cbddc_timer_start).
+bool timer_active(int kernel_class);
+void timer_begin(int kernel_class, cudaStream_t s);
+void timer_end(int kernel_class, cudaStream_t s, double flops, double bytes);
 
 // Device-side error bits, OR-ed into a status word by kernels.
 enum : int {

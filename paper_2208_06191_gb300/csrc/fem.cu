@@ -439,24 +439,31 @@ void assemble(fem_problem* P, const double* d, double lam, double* residual, boo
   double* fc = P->contrib.p + P->n_elem_blocks * 9;
   double* fr = P->rcontrib.p + P->n_elem_vec * 3;
   const int wt = want_tangent ? 1 : 0;
-  if (P->order == 1) {
+  timer_begin(CBDDC_TIMER_ELEMENT, s);
+  if (P->order == 1)
     element_kernel<1, 64><<<P->n_el, 64, 0, s>>>(mp, P->coords.p, P->elems.p, P->d_full.p,
                                                   P->rcontrib.p, P->contrib.p, P->status.p, wt);
-    CB_LAUNCH();
-    if (P->n_faces) {
-      face_kernel<1, 64><<<P->n_faces, 64, 0, s>>>(mp.pressure, P->coords.p, P->face_nodes.p,
-                                                    P->d_full.p, fr, fc, wt);
-      CB_LAUNCH();
-    }
-  } else {
+  else
     element_kernel<2, 256><<<P->n_el, 256, 0, s>>>(mp, P->coords.p, P->elems.p, P->d_full.p,
                                                     P->rcontrib.p, P->contrib.p, P->status.p, wt);
-    CB_LAUNCH();
-    if (P->n_faces) {
+  CB_LAUNCH();
+  {
+    // algorithmic work of the element kernel: the two-stage contraction
+    // (n_qp * n_en * 81 + n_qp * n_en^2 * 27 FMA per element) and the bytes
+    // of the element matrices and residuals it writes
+    const double nq = P->n_qp, ne = P->n_en;
+    const double fl = want_tangent ? 2.0 * P->n_el * (nq * ne * 81.0 + nq * ne * ne * 27.0) : 0.0;
+    const double by = 8.0 * P->n_el * (want_tangent ? ne * ne * 9.0 : 0.0) + 8.0 * P->n_el * ne * 3.0;
+    timer_end(CBDDC_TIMER_ELEMENT, s, fl, by);
+  }
+  if (P->n_faces) {
+    if (P->order == 1)
+      face_kernel<1, 64><<<P->n_faces, 64, 0, s>>>(mp.pressure, P->coords.p, P->face_nodes.p,
+                                                    P->d_full.p, fr, fc, wt);
+    else
       face_kernel<2, 128><<<P->n_faces, 128, 0, s>>>(mp.pressure, P->coords.p, P->face_nodes.p,
                                                       P->d_full.p, fr, fc, wt);
-      CB_LAUNCH();
-    }
+    CB_LAUNCH();
   }
   if (residual) {
     gather_vec_kernel<<<cdiv(3 * nf, 256), 256, 0, s>>>(P->res_ptr.p, P->res_src.p, P->rcontrib.p,
@@ -505,9 +512,12 @@ __global__ void bsr_spmv_kernel(const int* __restrict__ row_ptr, const int* __re
 
 void bsr_spmv(const fem_problem* P, const double* x, double* y, cudaStream_t s) {
   const int64_t rows = P->n_free_nodes;
+  timer_begin(CBDDC_TIMER_SPMV, s);
   bsr_spmv_kernel<<<cdiv(rows * 32, 256), 256, 0, s>>>(P->bsr_row_ptr.p, P->bsr_col.p,
                                                        P->bsr_vals.p, x, y, rows);
   CB_LAUNCH();
+  // bytes: 9 values + 1 column index per block, x read and y written once
+  timer_end(CBDDC_TIMER_SPMV, s, 18.0 * P->nnzb, 76.0 * P->nnzb + 16.0 * 3 * rows);
 }
 
 }  // namespace cbddc
