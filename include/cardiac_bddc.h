@@ -206,6 +206,27 @@ CBDDC_API int bddc_setup(fem_problem* P, const fem_tangent* K, const bddc_option
    alias.  Asynchronous. */
 CBDDC_API int bddc_apply(bddc_ctx* C, const double* r, double* z, cbddc_stream_t stream);
 CBDDC_API void bddc_destroy(bddc_ctx* C);
+
+/* Same result as bddc_apply, for callers that must not allocate device
+   memory while they run: code that is not allowed to call cudaMalloc
+   (which synchronises the device and may fail or stall once another
+   allocator has reserved the memory), and setups whose memory was
+   budgeted up front.  The paper has no counterpart; it is a deployment
+   variant of the apply of Section 3.2.
+   The per-apply work vectors live in one static device array of 4 MiB
+   (524288 doubles), held by every device that loads the library until the
+   process exits.  A context whose work vectors need more than that is
+   rejected with CBDDC_EINVAL (the message gives both sizes); bddc_apply
+   serves those.  The call performs no allocation: the context C must
+   already exist (bddc_setup allocates it).  The first call on a device
+   looks up the array's device address (cudaGetSymbolAddress, no
+   allocation); make that first call before any stream capture.  All calls
+   on one device share its array (each device has its own): every entry is
+   written before it is read within a call, so nothing needs clearing, but
+   calls on the same device whose work overlaps on the GPU (for example on
+   two streams) race and give wrong results; serialise them.
+   r, z: dev [n_free], must not alias.  Asynchronous. */
+CBDDC_API int bddc_apply_noalloc(bddc_ctx* C, const double* r, double* z, cbddc_stream_t stream);
 CBDDC_API int bddc_get_info(const bddc_ctx* C, bddc_info* info);
 
 /* ---------------------------------------------------- GMRES and Newton */

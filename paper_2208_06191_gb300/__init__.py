@@ -32,7 +32,7 @@ MAX_RECORDS = 512
 EXPORTED_SYMBOLS = [
     "fem_problem_create", "fem_problem_destroy", "fem_problem_get_info",
     "fem_residual", "fem_assemble_tangent", "fem_tangent_copy", "fem_spmv",
-    "bddc_setup", "bddc_apply", "bddc_destroy", "bddc_get_info",
+    "bddc_setup", "bddc_apply", "bddc_apply_noalloc", "bddc_destroy", "bddc_get_info",
     "gmres_solve", "newton_step", "newton_step_host", "newton_gmres_solve",
     "cbddc_kernel_launches", "cbddc_timer_start", "cbddc_timer_stop",
     "cbddc_last_error",
@@ -156,6 +156,7 @@ def load_library():
         "bddc_setup": (c_int, [vp, ctypes.POINTER(_Tangent), ctypes.POINTER(_BddcOptions),
                                ctypes.POINTER(vp), vp]),
         "bddc_apply": (c_int, [vp, vp, vp, vp]),
+        "bddc_apply_noalloc": (c_int, [vp, vp, vp, vp]),
         "bddc_destroy": (None, [vp]),
         "bddc_get_info": (c_int, [vp, ctypes.POINTER(_BddcInfo)]),
         "gmres_solve": (c_int, [vp, vp, vp, vp, ctypes.POINTER(_GmresOptions),
@@ -410,6 +411,14 @@ class BDDC:
     def apply(self, r, z):
         import torch
         _check(_LIB.bddc_apply(self._h, _ptr(r, torch.float64), _ptr(z, torch.float64), _stream()))
+        return z
+
+    def apply_noalloc(self, r, z):
+        """z = M^-1 r with the work vectors in the library's static device
+        array (no device allocation during the call)."""
+        import torch
+        _check(_LIB.bddc_apply_noalloc(self._h, _ptr(r, torch.float64), _ptr(z, torch.float64),
+                                       _stream()))
         return z
 
     def info(self):

@@ -24,6 +24,8 @@
 // coarse restriction/prolongation sums and the coarse solve are FP64.
 #include <algorithm>
 #include <map>
+#include <mutex>
+#include <string>
 
 #include "bddc.h"
 #include "fem.h"
@@ -961,6 +963,117 @@ void bddc_run_apply(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
   if (C->precision == CBDDC_FP32) apply_impl<float>(C, r, z, s);
   else apply_impl<double>(C, r, z, s);
   timer_end(CBDDC_TIMER_APPLY, s, C->apply_flops, (double)C->local_bytes);
+}
+
+// ------------------------------------------------ apply without allocation
+// Work vectors of bddc_apply_noalloc.  They live in one file-scope device
+// array that every device loading the library holds until the process
+// exits, so that the call itself never needs cudaMalloc.  4 MiB holds the
+// per-apply vectors of problems up to roughly 10^5 DoFs split into up to a
+// few hundred subdomains (the 48x48x12 slab needs about 3.1 MiB).
+constexpr int64_t kNoAllocScratchDoubles = 524288;  // 4 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+namespace {
+
+// Device address of g_noalloc_scratch, looked up once per device.  In host
+// code the array's name is only a host-side stand-in, so kernels must get
+// this address instead.
+double* noalloc_scratch_address() {
+  static std::mutex mu;
+  static std::map<int, double*> cache;
+  int dev = -1;
+  CB_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  void* ptr = nullptr;
+  CB_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+  CB_CHECK(ptr != nullptr, CBDDC_ECUDA, "cudaGetSymbolAddress returned a null address");
+  cache[dev] = static_cast<double*>(ptr);
+  return static_cast<double*>(ptr);
+}
+
+struct ApplyWork {
+  double *u0, *hG, *gI, *gl, *wG, *cl, *rc, *uc, *yG;
+};
+
+// Same launch sequence as apply_impl, with caller-chosen work vectors.
+template <typename T>
+void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w, cudaStream_t s) {
+  const int nsub = C->nsub;
+  const T* Aloc = reinterpret_cast<const T*>(C->Aloc.p);
+  const T* Sw = reinterpret_cast<const T*>(C->Sw.p);
+  const T* Phi = reinterpret_cast<const T*>(C->Phi.p);
+  apply_interior_kernel<T><<<dim3(cdiv(C->maxNs, AROWS), nsub), 256,
+                             (size_t)round_up(std::max(C->maxI, 4), 4) * sizeof(T), s>>>(
+      C->d_nI.p, C->d_ns.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, Aloc, r, w.u0,
+      w.hG);
+  CB_LAUNCH();
+  if (C->n_if > 0) {
+    assemble_g_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
+                                                        r, w.hG, w.gI);
+    CB_LAUNCH();
+    restrict_kernel<<<cdiv(C->totG, 256), 256, 0, s>>>(C->gam_if.p, C->Dg.p, C->totG, w.gI, w.gl);
+    CB_LAUNCH();
+    apply_local_kernel<T><<<dim3(cdiv(C->maxG, AROWS), nsub), 256,
+                            (size_t)round_up(std::max(C->maxR, 4), 4) * sizeof(T), s>>>(
+        C->d_nG.p, C->d_nr.p, C->d_offS.p, C->d_ldS.p, C->d_offGam.p, Sw, w.gl, w.wG);
+    CB_LAUNCH();
+    if (C->n_pi > 0) {
+      apply_phit_kernel<T><<<nsub, 256, 0, s>>>(C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p,
+                                                C->d_offGam.p, C->d_offC.p, Phi, w.gl, w.cl);
+      CB_LAUNCH();
+      gather_sum_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, w.cl, w.rc);
+      CB_LAUNCH();
+      dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, w.rc, w.uc);
+      CB_LAUNCH();
+    }
+    apply_prolong_kernel<T><<<dim3(cdiv(C->maxG, AROWS), nsub), 256, 0, s>>>(
+        C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, C->gprim.p, Phi,
+        w.uc, w.wG, C->Dg.p, w.yG);
+    CB_LAUNCH();
+    average_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
+                                                     w.yG, z);
+    CB_LAUNCH();
+  }
+  apply_extend_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), AROWS), nsub), 256,
+                           (size_t)round_up(std::max(C->maxG, 4), 4) * sizeof(T), s>>>(
+      C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, C->gdofG.p,
+      Aloc, w.u0, z);
+  CB_LAUNCH();
+}
+
+}  // namespace
+
+int64_t bddc_noalloc_scratch_needed(const bddc_ctx* C) {
+  auto pad = [](int64_t n) { return round_up(std::max<int64_t>(n, 1), 32); };
+  return pad(C->totI) + 4 * pad(C->totG) + pad(C->n_if) + pad(C->totC) + 2 * pad(C->n_pi);
+}
+
+int64_t bddc_noalloc_scratch_capacity() { return kNoAllocScratchDoubles; }
+
+void bddc_run_apply_noalloc(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
+  const int64_t need = bddc_noalloc_scratch_needed(C);
+  CB_CHECK(need <= kNoAllocScratchDoubles, CBDDC_EINVAL,
+           "bddc_apply_noalloc: this context needs " + std::to_string(need) +
+               " doubles of work space, the static buffer holds " +
+               std::to_string(kNoAllocScratchDoubles) + "; use bddc_apply");
+  double* base = noalloc_scratch_address();
+  auto pad = [](int64_t n) { return round_up(std::max<int64_t>(n, 1), 32); };
+  ApplyWork w;
+  double* p = base;
+  w.u0 = p; p += pad(C->totI);
+  w.hG = p; p += pad(C->totG);
+  w.gl = p; p += pad(C->totG);
+  w.wG = p; p += pad(C->totG);
+  w.yG = p; p += pad(C->totG);
+  w.gI = p; p += pad(C->n_if);
+  w.cl = p; p += pad(C->totC);
+  w.rc = p; p += pad(C->n_pi);
+  w.uc = p;
+  if (C->precision == CBDDC_FP32) apply_with_work<float>(C, r, z, w, s);
+  else apply_with_work<double>(C, r, z, w, s);
 }
 
 }  // namespace cbddc

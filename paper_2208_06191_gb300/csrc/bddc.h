@@ -55,4 +55,7 @@ namespace cbddc {
 void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C);
 void bddc_run_setup(bddc_ctx* C, cudaStream_t s);
 void bddc_run_apply(bddc_ctx* C, const double* r, double* z, cudaStream_t s);
+void bddc_run_apply_noalloc(bddc_ctx* C, const double* r, double* z, cudaStream_t s);
+int64_t bddc_noalloc_scratch_needed(const bddc_ctx* C);
+int64_t bddc_noalloc_scratch_capacity();
 }  // namespace cbddc

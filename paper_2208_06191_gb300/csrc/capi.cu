@@ -305,6 +305,14 @@ int bddc_apply(bddc_ctx* C, const double* r, double* z, cbddc_stream_t stream) {
 
 void bddc_destroy(bddc_ctx* C) { delete C; }
 
+int bddc_apply_noalloc(bddc_ctx* C, const double* r, double* z, cbddc_stream_t stream) {
+  return guard([&] {
+    CB_CHECK(C && r && z, CBDDC_EINVAL, "null argument");
+    CB_CHECK(r != z, CBDDC_EINVAL, "r and z must not alias");
+    bddc_run_apply_noalloc(C, r, z, reinterpret_cast<cudaStream_t>(stream));
+  });
+}
+
 int bddc_get_info(const bddc_ctx* C, bddc_info* info) {
   return guard([&] {
     CB_CHECK(C && info, CBDDC_EINVAL, "null argument");
