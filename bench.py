@@ -49,6 +49,9 @@ def _parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-budget-s", type=float, default=150.0)
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
+                    help="kernels: one BDDC setup and a few applies and SpMVs of the workload "
+                         "(a short program for profiler captures)")
     return ap.parse_args()
 
 
@@ -280,6 +283,21 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop()
     ms32 = _max_over_ranks(e0.elapsed_time(e1) / K, world)
 
+    # per-class kernel times over two more FP32 steps each (after the timed
+    # region, so the timed numbers carry no extra events)
+    kernels = {}
+    for name, cls in (("bddc_apply", pkg.TIMER_APPLY), ("bsr_spmv", pkg.TIMER_SPMV),
+                      ("element_kernel", pkg.TIMER_ELEMENT)):
+        pkg.timer_start(cls)
+        ctx32 = run_steps(2, opts32, ctx32)
+        t = pkg.timer_stop()
+        if t["launches"]:
+            ms = t["ms"] / t["launches"]
+            kernels[name] = {"launches": t["launches"], "ms_per_launch": ms,
+                             "GB_per_launch": t["bytes"] / t["launches"] / 1e9,
+                             "GBps": t["bytes"] / t["launches"] / (ms * 1e-3) / 1e9,
+                             "GFLOP_per_launch": t["flops"] / t["launches"] / 1e9}
+
     # ---- FP64 local operators
     ctx64 = run_steps(1, opts64, None)
     recs64 = []
@@ -350,6 +368,7 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "kernels": kernels,
     }
     if clk:
         line["clocks"] = clk
@@ -367,9 +386,36 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_kernels(args):
+    """One assembly, one FP32 BDDC setup, then 3 applies and 3 SpMVs."""
+    import torch
+
+    import paper_2208_06191_gb300 as pkg
+    from workloads import slab_config
+
+    pkg.build()
+    pkg.load_library()
+    prob = slab_config(WORKLOAD)
+    P = pkg.Problem(prob)
+    d = torch.zeros(P.n_free, dtype=torch.float64, device="cuda")
+    r = torch.empty_like(d)
+    P.assemble_tangent(d, 1.0 / prob["load_steps"], r)
+    pc = pkg.BDDC(P, precision=pkg.FP32, primal=prob["primal"]).setup()
+    z = torch.empty_like(d)
+    y = torch.empty_like(d)
+    for _ in range(3):
+        pc.apply(r, z)
+        P.spmv(z, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "kernels", "n_free": P.n_free, "apply_norm": float(z.norm())}))
+
+
 def main():
     args = _parse()
     world, rank, local = _dist_init()
+    if args.mode == "kernels":
+        run_kernels(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

@@ -42,27 +42,82 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float4; static constexpr int W = 4; };
 template <> struct Vec2<double> { using type = double2; static constexpr int W = 2; };
 
-__device__ inline float vdot(float4 v, const float* x) { return v.x * x[0] + v.y * x[1] + v.z * x[2] + v.w * x[3]; }
-__device__ inline double vdot(double2 v, const double* x) { return v.x * x[0] + v.y * x[1]; }
-
 template <typename T>
 __device__ inline T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Warp dot product of a 16-byte aligned row segment with a shared-memory
-// vector (also 16-byte aligned); streaming loads.
+__device__ inline float vdot2(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+__device__ inline double vdot2(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
+
+// Dot products of two rows (16-byte aligned) with a shared-memory vector,
+// one warp: 2 x 4 streaming 16-byte loads in flight per lane, no barriers.
 template <typename T>
-__device__ inline T warp_dot(const T* __restrict__ row, const T* __restrict__ xs, int n, int lane) {
+__device__ __forceinline__ void warp_dot2(const T* __restrict__ ra, const T* __restrict__ rb, bool has_b,
+                                          const T* __restrict__ xs, int n, int lane, T& oa, T& ob) {
   using V = typename Vec2<T>::type;
   constexpr int W = Vec2<T>::W;
+  constexpr int U = 4;
   const int nv = n / W;
-  const V* body = reinterpret_cast<const V*>(row);
-  T acc = T(0);
-  for (int i = lane; i < nv; i += 32) acc += vdot(__ldcs(body + i), xs + i * W);
-  for (int i = nv * W + lane; i < n; i += 32) acc += row[i] * xs[i];
-  return warp_sum(acc);
+  const V* va = reinterpret_cast<const V*>(ra);
+  const V* vb = reinterpret_cast<const V*>(rb);
+  const V* xv = reinterpret_cast<const V*>(xs);
+  T acc_a = T(0), acc_b = T(0);
+  int i = lane;
+  for (; i + 32 * (U - 1) < nv; i += 32 * U) {
+    V la[U], lb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) la[u] = __ldcs(va + i + 32 * u);
+    if (has_b) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) lb[u] = __ldcs(vb + i + 32 * u);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const V x = xv[i + 32 * u];
+      acc_a += vdot2(la[u], x);
+      if (has_b) acc_b += vdot2(lb[u], x);
+    }
+  }
+  for (; i < nv; i += 32) {
+    const V x = xv[i];
+    acc_a += vdot2(__ldcs(va + i), x);
+    if (has_b) acc_b += vdot2(__ldcs(vb + i), x);
+  }
+  for (int c = nv * W + lane; c < n; c += 32) {
+    acc_a += ra[c] * xs[c];
+    if (has_b) acc_b += rb[c] * xs[c];
+  }
+  oa = warp_sum(acc_a);
+  ob = has_b ? warp_sum(acc_b) : T(0);
+}
+
+// Row-block GEMV driver: rows [rb, re) of a matrix with leading dimension
+// ld, 8 warps x two rows at a time; f(row, value) stores each result.
+template <typename T, typename F>
+__device__ __forceinline__ void gemv_rows(const T* __restrict__ A, int64_t ld, int rb, int re,
+                                          const T* __restrict__ xs, int n, F f) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = rb + 2 * warp; r < re; r += 16) {
+    const bool hb = (r + 1) < re;
+    T va, vb;
+    warp_dot2<T>(A + (int64_t)r * ld, A + (int64_t)(hb ? r + 1 : r) * ld, hb, xs, n, lane, va, vb);
+    if (lane == 0) {
+      f(r, va);
+      if (hb) f(r + 1, vb);
+    }
+  }
+}
+
+constexpr int GROWS = 16;   // rows per group of the row-block GEMVs
+constexpr int GGROUPS = 4;  // groups per CTA (64 rows share one x load)
+
+// xs[0:n] = (T) x[0:n] from a packed FP64 vector (coalesced).
+template <typename T>
+__device__ __forceinline__ void load_x(T* __restrict__ xs, const double* __restrict__ x, int n) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) xs[j] = (T)x[j];
+  __syncthreads();
 }
 
 // ------------------------------------------------------------ setup kernels
@@ -102,6 +157,21 @@ __global__ void copy_schur_kernel(const int* __restrict__ nI, const int* __restr
   const int i = (int)(t / ng), j = (int)(t % ng);
   const int cI = (int)round_up_dev(ni, 4);
   Sw[offS[s] + (int64_t)i * ldS[s] + j] = Aloc[offA[s] + (int64_t)(ni + i) * ldA[s] + cI + j];
+}
+
+// A_IG block <- E (the harmonic-extension operator A_II^-1 A_IG).
+template <typename T>
+__global__ void copy_e_kernel(const int* __restrict__ nI, const int* __restrict__ nG,
+                              const int64_t* __restrict__ offA, const int* __restrict__ ldA,
+                              const int64_t* __restrict__ offE, const int* __restrict__ ldE,
+                              const T* __restrict__ Et, T* __restrict__ Aloc) {
+  const int s = blockIdx.y;
+  const int ng = nG[s], ni = nI[s];
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ni * ng) return;
+  const int i = (int)(t / ng), j = (int)(t % ng);
+  const int cI = (int)round_up_dev(ni, 4);
+  Aloc[offA[s] + (int64_t)i * ldA[s] + cI + j] = Et[offE[s] + (int64_t)i * ldE[s] + j];
 }
 
 // S_rr += alpha C^T C with C the average constraints (alpha = largest |S_ii|
@@ -290,33 +360,54 @@ __global__ void coarse_assemble_kernel_d(const int* __restrict__ key, const int*
 // ------------------------------------------------------------ apply kernels
 constexpr int AROWS = 32;  // rows per CTA in the batched GEMVs (8 warps x 4)
 
+// xI = r[gdof of the interior DoFs], packed per subdomain.
+__global__ void gather_kernel(const int* __restrict__ idx, int64_t n, const double* __restrict__ x,
+                              double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = x[idx[i]];
+}
+
+// u0 = A_II^-1 r_I (rows of the A_II^-1 block), 64 rows per CTA.
 template <typename T>
 __global__ void __launch_bounds__(256)
-apply_interior_kernel(const int* __restrict__ nI, const int* __restrict__ ns,
-                      const int64_t* __restrict__ offA, const int* __restrict__ ldA,
-                      const int64_t* __restrict__ offI, const int64_t* __restrict__ offGam,
-                      const int* __restrict__ gdofI, const T* __restrict__ Aloc,
-                      const double* __restrict__ r, double* __restrict__ u0, double* __restrict__ hG) {
+apply_interior_kernel(const int* __restrict__ nI, const int64_t* __restrict__ offA,
+                      const int* __restrict__ ldA, const int64_t* __restrict__ offI,
+                      const T* __restrict__ Aloc, const double* __restrict__ xI, double* __restrict__ u0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* xs = reinterpret_cast<T*>(smraw);
   const int s = blockIdx.y;
-  const int ni = nI[s], n = ns[s];
-  const int r0 = blockIdx.x * AROWS;
-  if (r0 >= n) return;
-  for (int j = threadIdx.x; j < ni; j += blockDim.x) xs[j] = (T)r[gdofI[offI[s] + j]];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const T* A0 = Aloc + offA[s];
-  const int ld = ldA[s];
-  for (int rr = warp; rr < AROWS; rr += 8) {
-    const int row = r0 + rr;
-    if (row >= n) break;
-    const T v = ni > 0 ? warp_dot(A0 + (int64_t)row * ld, xs, ni, lane) : T(0);
-    if (lane == 0) {
-      if (row < ni) u0[offI[s] + row] = (double)v;
-      else hG[offGam[s] + row - ni] = (double)v;  // = -(A_GI A_II^-1 r_I)
-    }
+  const int ni = nI[s];
+  const int rb = blockIdx.x * GROWS * GGROUPS;
+  if (rb >= ni) return;
+  load_x<T>(xs, xI + offI[s], ni);
+  double* out = u0 + offI[s];
+  gemv_rows<T>(Aloc + offA[s], ldA[s], rb, min(ni, rb + GROWS * GGROUPS), xs, ni,
+               [&](int row, T v) { out[row] = (double)v; });
+}
+
+// hG = -A_GI u0 (the interface part of the interior correction).
+template <typename T>
+__global__ void __launch_bounds__(256)
+apply_gi_kernel(const int* __restrict__ nI, const int* __restrict__ nG, const int64_t* __restrict__ offA,
+                const int* __restrict__ ldA, const int64_t* __restrict__ offI,
+                const int64_t* __restrict__ offGam, const T* __restrict__ Aloc,
+                const double* __restrict__ u0, double* __restrict__ hG) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* xs = reinterpret_cast<T*>(smraw);
+  const int s = blockIdx.y;
+  const int ni = nI[s], ng = nG[s];
+  const int rb = blockIdx.x * GROWS * GGROUPS;
+  if (rb >= ng) return;
+  const int re = min(ng, rb + GROWS * GGROUPS);
+  double* out = hG + offGam[s];
+  if (ni == 0) {
+    for (int row = rb + threadIdx.x; row < re; row += blockDim.x) out[row] = 0.0;
+    return;
   }
+  load_x<T>(xs, u0 + offI[s], ni);
+  const int ld = ldA[s];
+  gemv_rows<T>(Aloc + offA[s] + (int64_t)ni * ld, ld, rb, re, xs, ni,
+               [&](int row, T v) { out[row] = -(double)v; });
 }
 
 __global__ void assemble_g_kernel(const int* __restrict__ if_dof, const int* __restrict__ if_ptr,
@@ -346,32 +437,32 @@ apply_local_kernel(const int* __restrict__ nG, const int* __restrict__ nr,
   T* xs = reinterpret_cast<T*>(smraw);
   const int s = blockIdx.y;
   const int ng = nG[s], nrs = nr[s];
-  const int r0 = blockIdx.x * AROWS;
-  if (r0 >= ng) return;
+  const int rb = blockIdx.x * GROWS * GGROUPS;
+  if (rb >= ng) return;
   const int64_t og = offGam[s];
-  for (int j = threadIdx.x; j < nrs; j += blockDim.x) xs[j] = (T)gl[og + j];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const T* S0 = Sw + offS[s];
-  const int ld = ldS[s];
-  for (int rr = warp; rr < AROWS; rr += 8) {
-    const int row = r0 + rr;
-    if (row >= ng) break;
-    T v = T(0);
-    if (row < nrs) v = warp_dot(S0 + (int64_t)row * ld, xs, nrs, lane);
-    if (lane == 0) wG[og + row] = (double)v;
-  }
+  const int re = min(ng, rb + GROWS * GGROUPS);
+  double* out = wG + og;
+  // vertex rows: the local solution vanishes there
+  for (int row = max(rb, nrs) + threadIdx.x; row < re; row += blockDim.x) out[row] = 0.0;
+  if (rb >= nrs) return;
+  load_x<T>(xs, gl + og, nrs);
+  gemv_rows<T>(Sw + offS[s], ldS[s], rb, min(nrs, re), xs, nrs, [&](int row, T v) { out[row] = (double)v; });
 }
 
-// cl = Phi^T g_i, one CTA per subdomain (FP64 accumulation, n_c <= 128).
+// Partial coarse restriction Phi^T g_i over one chunk of PHIT_ROWS interface
+// rows: clp[(offC[s] + c) * nchunk + chunk] (FP64 accumulation, n_c <= 128).
+// Chunks past the subdomain's rows write zeros, so the coarse gather can sum
+// every chunk of every entry in a fixed order.
+constexpr int PHIT_ROWS = 128;
 template <typename T>
 __global__ void __launch_bounds__(256)
 apply_phit_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
                   const int64_t* __restrict__ offPhi, const int* __restrict__ ldPhi,
                   const int64_t* __restrict__ offGam, const int64_t* __restrict__ offC,
-                  const T* __restrict__ Phi, const double* __restrict__ gl, double* __restrict__ cl) {
+                  const T* __restrict__ Phi, const double* __restrict__ gl, double* __restrict__ clp,
+                  int nchunk) {
   __shared__ double red[8][128];
-  const int s = blockIdx.x;
+  const int s = blockIdx.y, chunk = blockIdx.x;
   const int ng = nG[s], ncs = nc[s];
   if (ncs == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -379,12 +470,14 @@ apply_phit_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
   const T* P0 = Phi + offPhi[s];
   const int ld = ldPhi[s];
   const int64_t og = offGam[s];
-  for (int j = warp; j < ng; j += 8) {
+  const int r0 = chunk * PHIT_ROWS, r1 = min(ng, r0 + PHIT_ROWS);
+  for (int j = r0 + warp; j < r1; j += 8) {
     const double gj = gl[og + j];
+    const T* row = P0 + (int64_t)j * ld;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int c = lane + 32 * t;
-      if (c < ncs) acc[t] += (double)P0[(int64_t)j * ld + c] * gj;
+      if (c < ncs) acc[t] += (double)row[c] * gj;
     }
   }
 #pragma unroll
@@ -393,17 +486,21 @@ apply_phit_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
   for (int c = threadIdx.x; c < ncs; c += blockDim.x) {
     double v = 0.0;
     for (int w = 0; w < 8; ++w) v += red[w][c];
-    cl[offC[s] + c] = v;
+    clp[(offC[s] + c) * nchunk + chunk] = v;
   }
 }
 
-__global__ void gather_sum_kernel(const int* __restrict__ ptr, const int* __restrict__ src, int n,
-                                  const double* __restrict__ x, double* __restrict__ y) {
+// rc[p] = sum over the listed local primal entries of all their chunks.
+__global__ void coarse_rhs_kernel(const int* __restrict__ ptr, const int* __restrict__ src, int n,
+                                  const double* __restrict__ clp, int nchunk, double* __restrict__ rc) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n) return;
   double v = 0.0;
-  for (int j = ptr[m]; j < ptr[m + 1]; ++j) v += x[src[j]];
-  y[m] = v;
+  for (int j = ptr[m]; j < ptr[m + 1]; ++j) {
+    const double* q = clp + (int64_t)src[j] * nchunk;
+    for (int c = 0; c < nchunk; ++c) v += q[c];
+  }
+  rc[m] = v;
 }
 
 __global__ void dense_gemv_kernel(const double* __restrict__ A, int n, const double* __restrict__ x,
@@ -418,7 +515,7 @@ __global__ void dense_gemv_kernel(const double* __restrict__ A, int n, const dou
   if (lane == 0) y[row] = acc;
 }
 
-// y_i = D_i (w_i + Phi_i R_Pi u_c), one warp per interface row.
+// y_i = D_i (w_i + Phi_i R_Pi u_c); 8 lanes per interface row.
 template <typename T>
 __global__ void __launch_bounds__(256)
 apply_prolong_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
@@ -434,28 +531,33 @@ apply_prolong_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
   if (r0 >= ng) return;
   for (int c = threadIdx.x; c < ncs; c += blockDim.x) ucl[c] = uc[gprim[offC[s] + c]];
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const T* P0 = Phi + offPhi[s];
-  const int ld = ldPhi[s];
-  const int64_t og = offGam[s];
-  for (int rr = warp; rr < AROWS; rr += 8) {
-    const int row = r0 + rr;
-    if (row >= ng) break;
-    double acc = 0.0;
-    for (int c = lane; c < ncs; c += 32) acc += (double)P0[(int64_t)row * ld + c] * ucl[c];
-    acc = warp_sum(acc);
-    if (lane == 0) yG[og + row] = Dg[og + row] * (wG[og + row] + acc);
+  const int sub = threadIdx.x & 7, grp = threadIdx.x >> 3;  // 32 groups of 8 lanes
+  const int row = r0 + grp;
+  double acc = 0.0;
+  if (row < ng) {
+    const T* pr = Phi + offPhi[s] + (int64_t)row * ldPhi[s];
+    for (int c = sub; c < ncs; c += 8) acc += (double)pr[c] * ucl[c];
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  if (row < ng && sub == 0) {
+    const int64_t og = offGam[s];
+    yG[og + row] = Dg[og + row] * (wG[og + row] + acc);
   }
 }
 
+// z_G = sum over sharing subdomains of yG; also written to every packed
+// local interface position (zl), the input of the harmonic extension.
 __global__ void average_kernel(const int* __restrict__ if_dof, const int* __restrict__ if_ptr,
                                const int* __restrict__ if_src, int n_if, const double* __restrict__ yG,
-                               double* __restrict__ z) {
+                               double* __restrict__ z, double* __restrict__ zl) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_if) return;
   double v = 0.0;
   for (int j = if_ptr[m]; j < if_ptr[m + 1]; ++j) v += yG[if_src[j]];
   z[if_dof[m]] = v;
+  for (int j = if_ptr[m]; j < if_ptr[m + 1]; ++j) zl[if_src[j]] = v;
 }
 
 template <typename T>
@@ -463,28 +565,24 @@ __global__ void __launch_bounds__(256)
 apply_extend_kernel(const int* __restrict__ nI, const int* __restrict__ nG,
                     const int64_t* __restrict__ offA, const int* __restrict__ ldA,
                     const int64_t* __restrict__ offI, const int64_t* __restrict__ offGam,
-                    const int* __restrict__ gdofI, const int* __restrict__ gdofG,
-                    const T* __restrict__ Aloc, const double* __restrict__ u0, double* __restrict__ z) {
+                    const int* __restrict__ gdofI, const T* __restrict__ Aloc,
+                    const double* __restrict__ zl, const double* __restrict__ u0, double* __restrict__ z) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* xs = reinterpret_cast<T*>(smraw);
   const int s = blockIdx.y;
   const int ni = nI[s], ng = nG[s];
-  const int r0 = blockIdx.x * AROWS;
-  if (r0 >= ni) return;
-  const int64_t og = offGam[s];
-  for (int j = threadIdx.x; j < ng; j += blockDim.x) xs[j] = (T)z[gdofG[og + j]];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cI = (ni + 3) / 4 * 4;
-  const T* A0 = Aloc + offA[s] + cI;
-  const int ld = ldA[s];
-  for (int rr = warp; rr < AROWS; rr += 8) {
-    const int row = r0 + rr;
-    if (row >= ni) break;
-    T v = T(0);
-    if (ng > 0) v = warp_dot(A0 + (int64_t)row * ld, xs, ng, lane);
-    if (lane == 0) z[gdofI[offI[s] + row]] = u0[offI[s] + row] - (double)v;
+  const int rb = blockIdx.x * GROWS * GGROUPS;
+  if (rb >= ni) return;
+  const int re = min(ni, rb + GROWS * GGROUPS);
+  const int64_t oi = offI[s];
+  if (ng == 0) {
+    for (int row = rb + threadIdx.x; row < re; row += blockDim.x) z[gdofI[oi + row]] = u0[oi + row];
+    return;
   }
+  load_x<T>(xs, zl + offGam[s], ng);
+  const int cI = (ni + 3) / 4 * 4;
+  gemv_rows<T>(Aloc + offA[s] + cI, ldA[s], rb, re, xs, ng,
+               [&](int row, T v) { z[gdofI[oi + row]] = u0[oi + row] - (double)v; });
 }
 
 }  // namespace
@@ -636,7 +734,7 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   const int NB = SWEEP_NB;
   C->ldA.assign(nsub, 0); C->ldS = C->ldPhi = C->ldY = C->ldG = C->ldA;
   C->offA.assign(nsub + 1, 0); C->offS = C->offPhi = C->offY = C->offZ = C->offG = C->offSPhi =
-      C->offKc = C->offX = C->offYp = C->offP = C->offA;
+      C->offKc = C->offX = C->offYp = C->offP = C->offE = C->offA;
   for (int s = 0; s < nsub; ++s) {
     const int cI = (int)round_up(C->nI[s], 4);
     C->ldA[s] = (int)round_up(cI + C->nG[s], 8);
@@ -655,6 +753,7 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     C->offX[s + 1] = C->offX[s] + round_up((int64_t)C->ns[s] * NB, kAlign);
     C->offYp[s + 1] = C->offYp[s] + round_up((int64_t)NB * C->ldA[s], kAlign);
     C->offP[s + 1] = C->offP[s] + NB * NB;
+    C->offE[s + 1] = C->offE[s] + round_up((int64_t)C->nI[s] * C->ldS[s], kAlign);
     C->maxI = std::max(C->maxI, C->nI[s]);
     C->maxG = std::max(C->maxG, C->nG[s]);
     C->maxR = std::max(C->maxR, C->nr[s]);
@@ -662,25 +761,31 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     C->maxC = std::max(C->maxC, C->nc[s]);
     C->maxA = std::max(C->maxA, C->na[s]);
   }
+  // every operand buffer gets kAlign elements of slack for masked vector loads
   const size_t es = C->esize;
-  C->Aloc.alloc(C->offA[nsub] * es);
-  C->Sw.alloc(std::max<int64_t>(C->offS[nsub], 1) * es);
-  C->Phi.alloc(std::max<int64_t>(C->offPhi[nsub], 1) * es);
-  C->SPhi.alloc(std::max<int64_t>(C->offPhi[nsub], 1) * es);
-  C->Y.alloc(std::max<int64_t>(C->offY[nsub], 1) * es);
-  C->Zf.alloc(std::max<int64_t>(C->offZ[nsub], 1) * es);
-  C->Wf.alloc(std::max<int64_t>(C->offZ[nsub], 1) * es);
-  C->G.alloc(std::max<int64_t>(C->offG[nsub], 1) * es);
-  C->Kc.alloc(std::max<int64_t>(C->offKc[nsub], 1) * es);
-  C->Xp.alloc(C->offX[nsub] * es);
-  C->Yp.alloc(C->offYp[nsub] * es);
-  C->Pd.alloc(C->offP[nsub] * es);
+  auto sized = [&](int64_t n) { return (size_t)(std::max<int64_t>(n, 1) + kAlign) * es; };
+  C->Aloc.alloc(sized(C->offA[nsub]));
+  C->Sw.alloc(sized(C->offS[nsub]));
+  C->Phi.alloc(sized(C->offPhi[nsub]));
+  C->SPhi.alloc(sized(C->offPhi[nsub]));
+  C->Y.alloc(sized(C->offY[nsub]));
+  C->Zf.alloc(sized(C->offZ[nsub]));
+  C->Wf.alloc(sized(C->offZ[nsub]));
+  C->G.alloc(sized(C->offG[nsub]));
+  C->Kc.alloc(sized(C->offKc[nsub]));
+  C->Xp.alloc(sized(C->offX[nsub]));
+  C->Yp.alloc(sized(C->offYp[nsub]));
+  C->Pd.alloc(sized(C->offP[nsub]));
+  C->Et.alloc(sized(C->offE[nsub]));
 
-  // sweep descriptors and GEMM problem lists
+  // sweep descriptors and GEMM problem lists.
+  // Interior elimination: sweep of the A_II block alone (A_II^-1 in place),
+  // then E = A_II^-1 A_IG and S = A_GG - A_GI E as two large-K GEMMs; E is
+  // copied over A_IG afterwards (A_IG is not needed once S is formed).
   std::vector<SweepDesc> sw1(nsub), sw2(nsub);
   for (int s = 0; s < nsub; ++s) {
-    sw1[s] = SweepDesc{C->ns[s], (int)round_up(C->nI[s], 4) + C->nG[s], C->ldA[s], C->nI[s],
-                       C->offA[s], C->offX[s], C->offYp[s], C->offP[s]};
+    sw1[s] = SweepDesc{C->nI[s], C->nI[s], C->ldA[s], C->nI[s], C->offA[s], C->offX[s], C->offYp[s],
+                       C->offP[s]};
     sw2[s] = SweepDesc{C->nG[s], C->nG[s], C->ldS[s], C->nr[s], C->offS[s], C->offX[s], C->offYp[s],
                        C->offP[s]};
     C->steps1 = std::max(C->steps1, (int)cdiv(C->nI[s], NB));
@@ -688,44 +793,49 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   }
   C->sw1.upload(sw1);
   C->sw2.upload(sw2);
-  const double eb = (double)C->esize;
-  auto sweep_gemms = [NB, eb](const std::vector<SweepDesc>& sw, int steps, std::vector<double>& fl) {
-    std::vector<GemmProb> g;
+  auto sweep_gemms = [NB, es](const std::vector<SweepDesc>& sw, int steps, std::vector<GemmList>& out) {
     const int nmat = (int)sw.size();
-    fl.assign(2 * steps, 0.0);
-    for (int k = 0; k < steps; ++k)
+    out.clear();
+    out.resize(steps);
+    for (int k = 0; k < steps; ++k) {
+      std::vector<GemmProb> g;
       for (int s = 0; s < nmat; ++s) {
         const SweepDesc& d = sw[s];
         const int kb = std::max(0, std::min(NB, d.p - k * NB));
         g.push_back(GemmProb{d.rows, d.cols, kb, NB, d.ld, d.ld, d.offX, d.offY, d.off});
-        if (kb > 0) {
-          fl[2 * k] += 2.0 * d.rows * d.cols * kb;
-          fl[2 * k + 1] += eb * (2.0 * d.rows * d.cols + (double)kb * (d.rows + d.cols));
-        }
       }
-    return g;
+      out[k].set(g, es);
+    }
   };
-  C->g_sw1.upload(sweep_gemms(sw1, C->steps1, C->fl_sw1));
-  C->g_sw2.upload(sweep_gemms(sw2, C->steps2, C->fl_sw2));
-  std::vector<GemmProb> gW, gT, gPA, gSP, gKc;
+  sweep_gemms(sw1, C->steps1, C->gl_sw1);
+  sweep_gemms(sw2, C->steps2, C->gl_sw2);
+  std::vector<GemmProb> gE, gS, gW, gT, gPA, gSP, gKc;
   for (int s = 0; s < nsub; ++s) {
     const int cI = (int)round_up(C->nI[s], 4);
+    const int64_t aII = C->offA[s], aIG = C->offA[s] + cI;
+    const int64_t aGI = C->offA[s] + (int64_t)C->nI[s] * C->ldA[s], aGG = aGI + cI;
+    gE.push_back(GemmProb{C->nI[s], C->nG[s], C->nI[s], C->ldA[s], C->ldA[s], C->ldS[s], aII, aIG,
+                          C->offE[s]});
+    gS.push_back(GemmProb{C->nG[s], C->nG[s], C->nI[s], C->ldA[s], C->ldS[s], C->ldA[s], aGI, C->offE[s],
+                          aGG});
     gW.push_back(GemmProb{C->na[s], C->nG[s], C->na[s], C->ldG[s], C->ldS[s], C->ldS[s], C->offG[s],
                           C->offZ[s], C->offZ[s]});
     gT.push_back(GemmProb{C->nr[s], C->nG[s], C->na[s], C->ldY[s], C->ldS[s], C->ldS[s], C->offY[s],
                           C->offZ[s], C->offS[s]});
     gPA.push_back(GemmProb{C->nr[s], C->na[s], C->na[s], C->ldY[s], C->ldG[s], C->ldPhi[s], C->offY[s],
                            C->offG[s], C->offPhi[s] + C->nv[s]});
-    gSP.push_back(GemmProb{C->nG[s], C->nc[s], C->nG[s], C->ldA[s], C->ldPhi[s], C->ldPhi[s],
-                           C->offA[s] + (int64_t)C->nI[s] * C->ldA[s] + cI, C->offPhi[s], C->offPhi[s]});
+    gSP.push_back(GemmProb{C->nG[s], C->nc[s], C->nG[s], C->ldA[s], C->ldPhi[s], C->ldPhi[s], aGG,
+                           C->offPhi[s], C->offPhi[s]});
     gKc.push_back(GemmProb{C->nc[s], C->nc[s], C->nG[s], C->ldPhi[s], C->ldPhi[s], C->ldPhi[s],
                            C->offPhi[s], C->offPhi[s], C->offKc[s]});
   }
-  C->g_W.upload(gW);
-  C->g_T.upload(gT);
-  C->g_PhiA.upload(gPA);
-  C->g_SPhi.upload(gSP);
-  C->g_Kc.upload(gKc);
+  C->gl_E.set(gE, es);
+  C->gl_S.set(gS, es);
+  C->gl_W.set(gW, es);
+  C->gl_T.set(gT, es);
+  C->gl_PhiA.set(gPA, es);
+  C->gl_SPhi.set(gSP, es);
+  C->gl_Kc.set(gKc, es, true);
 
   // coarse matrix entries
   if (C->n_pi > 0) {
@@ -757,8 +867,19 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     std::vector<SweepDesc> swc{SweepDesc{C->n_pi, C->n_pi, C->n_pi, C->n_pi, 0, 0, 0, 0}};
     C->swc.upload(swc);
     C->stepsc = (int)cdiv(C->n_pi, NB);
-    C->g_swc.upload(sweep_gemms(swc, C->stepsc, C->fl_swc));
-    for (size_t i = 1; i < C->fl_swc.size(); i += 2) C->fl_swc[i] *= 8.0 / eb;  // coarse is FP64
+    {
+      // the coarse matrix is FP64 whatever the local precision
+      const int nmat = 1;
+      C->gl_swc.clear();
+      C->gl_swc.resize(C->stepsc);
+      for (int k = 0; k < C->stepsc; ++k) {
+        const SweepDesc& d = swc[0];
+        const int kb = std::max(0, std::min(NB, d.p - k * NB));
+        std::vector<GemmProb> g{GemmProb{d.rows, d.cols, kb, NB, d.ld, d.ld, d.offX, d.offY, d.off}};
+        C->gl_swc[k].set(g, 8);
+        (void)nmat;
+      }
+    }
   }
 
   // device copies of sizes and maps
@@ -768,7 +889,7 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   C->d_ldY.upload(C->ldY); C->d_ldG.upload(C->ldG);
   C->d_offA.upload(C->offA); C->d_offS.upload(C->offS); C->d_offPhi.upload(C->offPhi);
   C->d_offY.upload(C->offY); C->d_offZ.upload(C->offZ); C->d_offG.upload(C->offG);
-  C->d_offSPhi.upload(C->offSPhi); C->d_offKc.upload(C->offKc);
+  C->d_offSPhi.upload(C->offSPhi); C->d_offKc.upload(C->offKc); C->d_offE.upload(C->offE);
   C->d_offI.upload(C->offI); C->d_offGam.upload(C->offGam); C->d_offC.upload(C->offC);
   C->d_offCon.upload(C->offCon); C->d_offN.upload(offN);
   C->perm.upload(perm_h);
@@ -777,11 +898,13 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   C->cons_ptr.upload(cptr); C->cons_idx.upload(cidx); C->cons_w.upload(cw);
   C->gprim.upload(gprim); C->cg_ptr.upload(cg_ptr); C->cg_src.upload(cg_src);
   C->u0.alloc(std::max<int64_t>(C->totI, 1));
+  C->xI.alloc(std::max<int64_t>(C->totI, 1));
+  C->zl.alloc(std::max<int64_t>(C->totG, 1));
   C->hG.alloc(std::max<int64_t>(C->totG, 1));
   C->wG.alloc(std::max<int64_t>(C->totG, 1));
   C->yG.alloc(std::max<int64_t>(C->totG, 1));
   C->gI.alloc(std::max(C->n_if, 1));
-  C->cl.alloc(std::max<int64_t>(C->totC, 1));
+  C->cl.alloc(std::max<int64_t>(C->totC * (int64_t)cdiv(std::max(C->maxG, 1), PHIT_ROWS), 1));
   C->rc.alloc(std::max(C->n_pi, 1));
   C->uc.alloc(std::max(C->n_pi, 1));
   C->gl.alloc(std::max<int64_t>(C->totG, 1));
@@ -790,9 +913,11 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   int64_t lb = 0;
   for (int s = 0; s < nsub; ++s) {
     const double n = C->ns[s], ni = C->nI[s], ng = C->nG[s], nr = C->nr[s], na = C->na[s], nc = C->nc[s];
-    fl += 2.0 * n * (n) * ni + 2.0 * ng * ng * nr + 2.0 * na * na * ng + 2.0 * nr * na * ng +
-          2.0 * nr * na * na + 2.0 * ng * ng * nc + 2.0 * nc * nc * ng;
-    lb += (int64_t)((n * ni + ni * ng + nr * nr + 2.0 * ng * nc) * C->esize);
+    (void)n;
+    fl += 2.0 * ni * ni * ni + 2.0 * ni * ni * ng + 2.0 * ng * ng * ni + 2.0 * ng * ng * nr +
+          2.0 * na * na * ng + 2.0 * nr * na * ng + 2.0 * nr * na * na + 2.0 * ng * ng * nc +
+          2.0 * nc * nc * ng;
+    lb += (int64_t)((ni * ni + 2.0 * ni * ng + nr * nr + 2.0 * ng * nc) * C->esize);
   }
   fl += 2.0 * (double)C->n_pi * C->n_pi * C->n_pi;
   lb += (int64_t)C->n_pi * C->n_pi * 8;
@@ -803,19 +928,16 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
 
 // ------------------------------------------------------------------- setup
 template <typename T>
-static void run_sweep(const DVec<SweepDesc>& desc, int nmat, int steps, const DVec<GemmProb>& gp,
-                      const std::vector<double>& step_flops, int maxRows, int maxCols, T* mat, T* X, T* Y,
-                      T* Pbuf, int* status, double tol, cudaStream_t s) {
-  for (int k = 0; k < steps; ++k) {
+static void run_sweep(const DVec<SweepDesc>& desc, int nmat, const std::vector<GemmList>& lists,
+                      int maxRows, int maxCols, T* mat, T* X, T* Y, T* Pbuf, int* status, double tol,
+                      cudaStream_t s) {
+  for (int k = 0; k < (int)lists.size(); ++k) {
     sweep_diag_kernel<T><<<nmat, 256, 0, s>>>(desc.p, k, mat, Pbuf, status, tol);
     CB_LAUNCH();
     dim3 grid(cdiv(std::max(maxRows, maxCols), 64), nmat);
     sweep_panel_kernel<T><<<grid, 256, 0, s>>>(desc.p, k, mat, Pbuf, X, Y);
     CB_LAUNCH();
-    timer_begin(CBDDC_TIMER_SWEEP_GEMM, s);
-    launch_gemm<T, false, false>(gp.p + (int64_t)k * nmat, nmat, maxRows, maxCols, X, Y, mat, T(-1), T(1), s);
-    // flops: 2 M N K per problem; bytes: C read and written, X and Y read once
-    timer_end(CBDDC_TIMER_SWEEP_GEMM, s, step_flops[2 * k], step_flops[2 * k + 1]);
+    launch_list<T, false, false>(lists[k], X, Y, mat, T(-1), T(1), s);
   }
 }
 
@@ -835,6 +957,7 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
   T* Xp = reinterpret_cast<T*>(C->Xp.p);
   T* Yp = reinterpret_cast<T*>(C->Yp.p);
   T* Pd = reinterpret_cast<T*>(C->Pd.p);
+  T* Et = reinterpret_cast<T*>(C->Et.p);
   int* status = P->status.p;
   const double tol = C->pivot_tol;
   // 1. subdomain matrices
@@ -843,12 +966,16 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
       P->lslot_sub.p, P->lslot_row.p, P->lslot_col.p, P->lslot_ptr.p, P->lslot_src.p, P->contrib.p,
       P->n_lslots, C->perm.p, C->d_offN.p, C->d_offA.p, C->d_ldA.p, C->d_nI.p, Aloc);
   CB_LAUNCH();
-  // 2. sweep over the interior pivots
-  int maxCols = 0;
-  for (int q = 0; q < nsub; ++q) maxCols = std::max(maxCols, (int)round_up(C->nI[q], 4) + C->nG[q]);
-  run_sweep<T>(C->sw1, nsub, C->steps1, C->g_sw1, C->fl_sw1, C->maxNs, maxCols, Aloc, Xp, Yp, Pd, status, tol, s);
+  // 2. interior elimination: A_II^-1 by a sweep of the II block, then
+  //    E = A_II^-1 A_IG and S = A_GG - A_GI E, and E stored over A_IG
+  run_sweep<T>(C->sw1, nsub, C->gl_sw1, C->maxI, C->maxI, Aloc, Xp, Yp, Pd, status, tol, s);
   if (C->maxG == 0) return;  // one subdomain: no interface
-  // 3. Schur complement copy and sweep over Gamma_r
+  launch_list<T, false, false>(C->gl_E, Aloc, Aloc, Et, T(1), T(0), s);
+  launch_list<T, false, false>(C->gl_S, Aloc, Et, Aloc, T(-1), T(1), s);
+  copy_e_kernel<T><<<dim3(cdiv((int64_t)C->maxI * C->maxG, 256), nsub), 256, 0, s>>>(
+      C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offE.p, C->d_ldS.p, Et, Aloc);
+  CB_LAUNCH();
+  // 3. Schur complement copy, augmentation and sweep over Gamma_r
   copy_schur_kernel<T><<<dim3(cdiv((int64_t)C->maxG * C->maxG, 256), nsub), 256, 0, s>>>(
       C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offS.p, C->d_ldS.p, Aloc, Sw);
   CB_LAUNCH();
@@ -857,7 +984,7 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
                                           C->cons_idx.p, C->cons_w.p, C->d_offS.p, C->d_ldS.p, Sw);
     CB_LAUNCH();
   }
-  run_sweep<T>(C->sw2, nsub, C->steps2, C->g_sw2, C->fl_sw2, C->maxG, C->maxG, Sw, Xp, Yp, Pd, status, tol, s);
+  run_sweep<T>(C->sw2, nsub, C->gl_sw2, C->maxG, C->maxG, Sw, Xp, Yp, Pd, status, tol, s);
   // 4. average constraints
   if (C->maxA > 0) {
     cons_y_kernel<T><<<dim3(cdiv(C->maxR, 8), nsub), 256, 0, s>>>(
@@ -878,9 +1005,9 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
                                    (int)smem));
     small_inverse_kernel<T><<<nsub, 256, smem, s>>>(C->d_na.p, C->d_offG.p, C->d_ldG.p, G, status, tol);
     CB_LAUNCH();
-    launch_gemm<T, false, false>(C->g_W.p, nsub, C->maxA, C->maxG, G, Zf, Wf, T(1), T(0), s);
-    launch_gemm<T, false, false>(C->g_T.p, nsub, C->maxR, C->maxG, Y, Wf, Sw, T(-1), T(1), s);
-    launch_gemm<T, false, false>(C->g_PhiA.p, nsub, C->maxR, C->maxA, Y, G, Phi, T(1), T(0), s);
+    launch_list<T, false, false>(C->gl_W, G, Zf, Wf, T(1), T(0), s);
+    launch_list<T, false, false>(C->gl_T, Y, Wf, Sw, T(-1), T(1), s);
+    launch_list<T, false, false>(C->gl_PhiA, Y, G, Phi, T(1), T(0), s);
   }
   // 5. vertex columns of Phi and the identity block
   phi_vertex_kernel<T><<<dim3(cdiv((int64_t)C->maxG * C->maxC, 256), nsub), 256, 0, s>>>(
@@ -889,8 +1016,8 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
   CB_LAUNCH();
   // 6. local coarse matrices Phi^T S Phi and the FP64 coarse inverse
   if (C->n_pi > 0) {
-    launch_gemm<T, false, false>(C->g_SPhi.p, nsub, C->maxG, C->maxC, Aloc, Phi, SPhi, T(1), T(0), s);
-    launch_gemm<T, true, false>(C->g_Kc.p, nsub, C->maxC, C->maxC, Phi, SPhi, Kc, T(1), T(0), s);
+    launch_list<T, false, false>(C->gl_SPhi, Aloc, Phi, SPhi, T(1), T(0), s);
+    launch_list<T, true, false>(C->gl_Kc, Phi, SPhi, Kc, T(1), T(0), s);
     CB_CUDA(cudaMemsetAsync(C->Sc.p, 0, C->Sc.bytes(), s));
     if (sizeof(T) == 4)
       coarse_assemble_kernel_f<<<cdiv(C->n_ce, 256), 256, 0, s>>>(
@@ -899,8 +1026,8 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
       coarse_assemble_kernel_d<<<cdiv(C->n_ce, 256), 256, 0, s>>>(
           C->ce_key.p, C->ce_ptr.p, C->ce_src.p, C->n_ce, reinterpret_cast<const double*>(Kc), C->Sc.p);
     CB_LAUNCH();
-    run_sweep<double>(C->swc, 1, C->stepsc, C->g_swc, C->fl_swc, C->n_pi, C->n_pi, C->Sc.p, C->ScX.p,
-                      C->ScY.p, C->ScP.p, status, tol, s);
+    run_sweep<double>(C->swc, 1, C->gl_swc, C->n_pi, C->n_pi, C->Sc.p, C->ScX.p, C->ScY.p, C->ScP.p,
+                      status, tol, s);
   }
 }
 
@@ -917,26 +1044,34 @@ static void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) 
   const T* Sw = reinterpret_cast<const T*>(C->Sw.p);
   const T* Phi = reinterpret_cast<const T*>(C->Phi.p);
   double* gl = C->gl.p;
-  apply_interior_kernel<T><<<dim3(cdiv(C->maxNs, AROWS), nsub), 256,
-                             (size_t)round_up(std::max(C->maxI, 4), 4) * sizeof(T), s>>>(
-      C->d_nI.p, C->d_ns.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, Aloc, r,
-      C->u0.p, C->hG.p);
+  const size_t smI = (size_t)round_up(std::max(C->maxI, 4), 4) * sizeof(T);
+  gather_kernel<<<cdiv(std::max<int64_t>(C->totI, 1), 256), 256, 0, s>>>(C->gdofI.p, C->totI, r, C->xI.p);
   CB_LAUNCH();
+  apply_interior_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), GROWS * GGROUPS), nsub), 256, smI, s>>>(
+      C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, Aloc, C->xI.p, C->u0.p);
+  CB_LAUNCH();
+  if (C->maxG > 0) {
+    apply_gi_kernel<T><<<dim3(cdiv(C->maxG, GROWS * GGROUPS), nsub), 256, smI, s>>>(
+        C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, Aloc, C->u0.p, C->hG.p);
+    CB_LAUNCH();
+  }
   if (C->n_if > 0) {
     assemble_g_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
                                                         r, C->hG.p, C->gI.p);
     CB_LAUNCH();
     restrict_kernel<<<cdiv(C->totG, 256), 256, 0, s>>>(C->gam_if.p, C->Dg.p, C->totG, C->gI.p, gl);
     CB_LAUNCH();
-    apply_local_kernel<T><<<dim3(cdiv(C->maxG, AROWS), nsub), 256,
+    apply_local_kernel<T><<<dim3(cdiv(C->maxG, GROWS * GGROUPS), nsub), 256,
                             (size_t)round_up(std::max(C->maxR, 4), 4) * sizeof(T), s>>>(
         C->d_nG.p, C->d_nr.p, C->d_offS.p, C->d_ldS.p, C->d_offGam.p, Sw, gl, C->wG.p);
     CB_LAUNCH();
     if (C->n_pi > 0) {
-      apply_phit_kernel<T><<<nsub, 256, 0, s>>>(C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p,
-                                                C->d_offGam.p, C->d_offC.p, Phi, gl, C->cl.p);
+      const int nch = (int)cdiv(C->maxG, PHIT_ROWS);
+      apply_phit_kernel<T><<<dim3(nch, nsub), 256, 0, s>>>(C->d_nG.p, C->d_nc.p, C->d_offPhi.p,
+                                                          C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, Phi,
+                                                          gl, C->cl.p, nch);
       CB_LAUNCH();
-      gather_sum_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, C->cl.p,
+      coarse_rhs_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, C->cl.p, nch,
                                                            C->rc.p);
       CB_LAUNCH();
       dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, C->rc.p,
@@ -948,13 +1083,13 @@ static void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) 
         C->uc.p, C->wG.p, C->Dg.p, C->yG.p);
     CB_LAUNCH();
     average_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
-                                                     C->yG.p, z);
+                                                     C->yG.p, z, C->zl.p);
     CB_LAUNCH();
   }
-  apply_extend_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), AROWS), nsub), 256,
+  apply_extend_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), GROWS * GGROUPS), nsub), 256,
                            (size_t)round_up(std::max(C->maxG, 4), 4) * sizeof(T), s>>>(
-      C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, C->gdofG.p,
-      Aloc, C->u0.p, z);
+      C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, Aloc,
+      C->zl.p, C->u0.p, z);
   CB_LAUNCH();
 }
 
@@ -995,7 +1130,7 @@ double* noalloc_scratch_address() {
 }
 
 struct ApplyWork {
-  double *u0, *hG, *gI, *gl, *wG, *cl, *rc, *uc, *yG;
+  double *u0, *hG, *gI, *gl, *wG, *cl, *rc, *uc, *yG, *xI, *zl;
 };
 
 // Same launch sequence as apply_impl, with caller-chosen work vectors.
@@ -1005,26 +1140,35 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
   const T* Aloc = reinterpret_cast<const T*>(C->Aloc.p);
   const T* Sw = reinterpret_cast<const T*>(C->Sw.p);
   const T* Phi = reinterpret_cast<const T*>(C->Phi.p);
-  apply_interior_kernel<T><<<dim3(cdiv(C->maxNs, AROWS), nsub), 256,
-                             (size_t)round_up(std::max(C->maxI, 4), 4) * sizeof(T), s>>>(
-      C->d_nI.p, C->d_ns.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, Aloc, r, w.u0,
-      w.hG);
+  const size_t smI = (size_t)round_up(std::max(C->maxI, 4), 4) * sizeof(T);
+  gather_kernel<<<cdiv(std::max<int64_t>(C->totI, 1), 256), 256, 0, s>>>(C->gdofI.p, C->totI, r, w.xI);
   CB_LAUNCH();
+  apply_interior_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), GROWS * GGROUPS), nsub), 256, smI, s>>>(
+      C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, Aloc, w.xI, w.u0);
+  CB_LAUNCH();
+  if (C->maxG > 0) {
+    apply_gi_kernel<T><<<dim3(cdiv(C->maxG, GROWS * GGROUPS), nsub), 256, smI, s>>>(
+        C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, Aloc, w.u0, w.hG);
+    CB_LAUNCH();
+  }
   if (C->n_if > 0) {
     assemble_g_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
                                                         r, w.hG, w.gI);
     CB_LAUNCH();
     restrict_kernel<<<cdiv(C->totG, 256), 256, 0, s>>>(C->gam_if.p, C->Dg.p, C->totG, w.gI, w.gl);
     CB_LAUNCH();
-    apply_local_kernel<T><<<dim3(cdiv(C->maxG, AROWS), nsub), 256,
+    apply_local_kernel<T><<<dim3(cdiv(C->maxG, GROWS * GGROUPS), nsub), 256,
                             (size_t)round_up(std::max(C->maxR, 4), 4) * sizeof(T), s>>>(
         C->d_nG.p, C->d_nr.p, C->d_offS.p, C->d_ldS.p, C->d_offGam.p, Sw, w.gl, w.wG);
     CB_LAUNCH();
     if (C->n_pi > 0) {
-      apply_phit_kernel<T><<<nsub, 256, 0, s>>>(C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p,
-                                                C->d_offGam.p, C->d_offC.p, Phi, w.gl, w.cl);
+      const int nch = (int)cdiv(C->maxG, PHIT_ROWS);
+      apply_phit_kernel<T><<<dim3(nch, nsub), 256, 0, s>>>(C->d_nG.p, C->d_nc.p, C->d_offPhi.p,
+                                                          C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, Phi,
+                                                          w.gl, w.cl, nch);
       CB_LAUNCH();
-      gather_sum_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, w.cl, w.rc);
+      coarse_rhs_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, w.cl, nch,
+                                                           w.rc);
       CB_LAUNCH();
       dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, w.rc, w.uc);
       CB_LAUNCH();
@@ -1034,13 +1178,13 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
         w.uc, w.wG, C->Dg.p, w.yG);
     CB_LAUNCH();
     average_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
-                                                     w.yG, z);
+                                                     w.yG, z, w.zl);
     CB_LAUNCH();
   }
-  apply_extend_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), AROWS), nsub), 256,
+  apply_extend_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), GROWS * GGROUPS), nsub), 256,
                            (size_t)round_up(std::max(C->maxG, 4), 4) * sizeof(T), s>>>(
-      C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, C->gdofG.p,
-      Aloc, w.u0, z);
+      C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, Aloc,
+      w.zl, w.u0, z);
   CB_LAUNCH();
 }
 
@@ -1048,7 +1192,8 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
 
 int64_t bddc_noalloc_scratch_needed(const bddc_ctx* C) {
   auto pad = [](int64_t n) { return round_up(std::max<int64_t>(n, 1), 32); };
-  return pad(C->totI) + 4 * pad(C->totG) + pad(C->n_if) + pad(C->totC) + 2 * pad(C->n_pi);
+  const int64_t nch = cdiv(std::max(C->maxG, 1), PHIT_ROWS);
+  return 2 * pad(C->totI) + 5 * pad(C->totG) + pad(C->n_if) + pad(C->totC * nch) + 2 * pad(C->n_pi);
 }
 
 int64_t bddc_noalloc_scratch_capacity() { return kNoAllocScratchDoubles; }
@@ -1064,12 +1209,14 @@ void bddc_run_apply_noalloc(bddc_ctx* C, const double* r, double* z, cudaStream_
   ApplyWork w;
   double* p = base;
   w.u0 = p; p += pad(C->totI);
+  w.xI = p; p += pad(C->totI);
+  w.zl = p; p += pad(C->totG);
   w.hG = p; p += pad(C->totG);
   w.gl = p; p += pad(C->totG);
   w.wG = p; p += pad(C->totG);
   w.yG = p; p += pad(C->totG);
   w.gI = p; p += pad(C->n_if);
-  w.cl = p; p += pad(C->totC);
+  w.cl = p; p += pad(C->totC * (int64_t)cdiv(std::max(C->maxG, 1), PHIT_ROWS));
   w.rc = p; p += pad(C->n_pi);
   w.uc = p;
   if (C->precision == CBDDC_FP32) apply_with_work<float>(C, r, z, w, s);
@@ -1080,7 +1227,7 @@ void bddc_run_apply_noalloc(bddc_ctx* C, const double* r, double* z, cudaStream_
 
 int64_t bddc_ctx::device_bytes() const {
   return (int64_t)(Aloc.bytes() + Sw.bytes() + Phi.bytes() + Y.bytes() + Zf.bytes() + Wf.bytes() +
-                   G.bytes() + SPhi.bytes() + Kc.bytes() + Xp.bytes() + Yp.bytes() + Pd.bytes() +
+                   G.bytes() + SPhi.bytes() + Kc.bytes() + Xp.bytes() + Yp.bytes() + Pd.bytes() + Et.bytes() +
                    Sc.bytes() + ScX.bytes() + ScY.bytes() + ScP.bytes() + u0.bytes() + hG.bytes() +
-                   gI.bytes() + wG.bytes() + cl.bytes() + rc.bytes() + uc.bytes() + yG.bytes() + gl.bytes());
+                   gI.bytes() + wG.bytes() + cl.bytes() + rc.bytes() + uc.bytes() + yG.bytes() + gl.bytes() + xI.bytes() + zl.bytes());
 }

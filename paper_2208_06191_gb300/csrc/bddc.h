@@ -12,19 +12,19 @@ struct bddc_ctx {
   size_t esize = 8;  // bytes per element of the local operators
   // per-subdomain sizes (host)
   std::vector<int> nI, nG, nr, nv, na, nc, ns, ldA, ldS, ldPhi, ldY, ldG;
-  std::vector<int64_t> offA, offS, offPhi, offY, offZ, offG, offSPhi, offKc, offX, offYp, offP;
+  std::vector<int64_t> offA, offS, offPhi, offY, offZ, offG, offSPhi, offKc, offX, offYp, offP, offE;
   std::vector<int64_t> offI, offGam, offC, offCon;
   int maxI = 0, maxG = 0, maxR = 0, maxNs = 0, maxC = 0, maxA = 0;
   int n_pi = 0, n_if = 0;
   int64_t totI = 0, totG = 0, totC = 0;
   // device size/offset arrays
   cbddc::DVec<int> d_nI, d_nG, d_nr, d_nv, d_na, d_nc, d_ns, d_ldA, d_ldS, d_ldPhi, d_ldY, d_ldG;
-  cbddc::DVec<int64_t> d_offA, d_offS, d_offPhi, d_offY, d_offZ, d_offG, d_offSPhi, d_offKc;
+  cbddc::DVec<int64_t> d_offA, d_offS, d_offPhi, d_offY, d_offZ, d_offG, d_offSPhi, d_offKc, d_offE;
   cbddc::DVec<int64_t> d_offI, d_offGam, d_offC, d_offCon, d_offN;
   // local node ordering [I | Gamma_r | Gamma_v]: local node index -> position
   cbddc::DVec<int> perm;
   // local operators (element type float or double, raw storage)
-  cbddc::DVec<unsigned char> Aloc, Sw, Phi, Y, Zf, Wf, G, SPhi, Kc, Xp, Yp, Pd;
+  cbddc::DVec<unsigned char> Aloc, Sw, Phi, Y, Zf, Wf, G, SPhi, Kc, Xp, Yp, Pd, Et;
   // apply maps
   cbddc::DVec<int> gdofI, gdofG, gam_if, if_dof, if_ptr, if_src;
   cbddc::DVec<double> Dg;
@@ -35,15 +35,14 @@ struct bddc_ctx {
   int64_t n_ce = 0;
   cbddc::DVec<double> Sc, ScX, ScY, ScP;   // coarse matrix (inverted in place)
   // apply work vectors
-  cbddc::DVec<double> u0, hG, gI, wG, cl, rc, uc, yG;
+  cbddc::DVec<double> u0, hG, gI, wG, cl, rc, uc, yG, xI, zl;
   // sweep descriptors and GEMM problem lists
   cbddc::DVec<cbddc::SweepDesc> sw1, sw2, swc;
   int steps1 = 0, steps2 = 0, stepsc = 0;
-  cbddc::DVec<cbddc::GemmProb> g_sw1, g_sw2, g_swc, g_W, g_T, g_PhiA, g_SPhi, g_Kc;
-  int nprob_cons = 0, maxMW = 0, maxNW = 0;
+  std::vector<cbddc::GemmList> gl_sw1, gl_sw2, gl_swc;
+  cbddc::GemmList gl_E, gl_S, gl_W, gl_T, gl_PhiA, gl_SPhi, gl_Kc;
   cbddc::DVec<double> gl;                  // scaled interface restriction
   double setup_flops = 0.0, apply_flops = 0.0;
-  std::vector<double> fl_sw1, fl_sw2, fl_swc;  // per sweep step: flops, bytes
   int64_t local_bytes = 0;
   // Krylov and Newton workspaces (allocated on first use)
   cbddc::Gmres gm;

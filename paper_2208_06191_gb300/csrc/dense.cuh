@@ -15,6 +15,9 @@
 // which is the rank-kb form of the sweep.  No pivoting: a pivot below
 // tol * max|diag| (or non-finite) sets DEV_PIVOT in the status word.
 #pragma once
+#include <algorithm>
+#include <vector>
+
 #include "common.h"
 
 namespace cbddc {
@@ -104,15 +107,198 @@ gemm_grouped_kernel(const GemmProb* __restrict__ probs, const T* __restrict__ A,
   }
 }
 
+// Fast path for C = alpha A B + beta C (both operands row-major, not
+// transposed): tiles of (32 VEC) x (32 VEC) with VEC = 16 / sizeof(T) (128 x
+// 128 for FP32, 64 x 64 for FP64), 256 threads, a 2 VEC x 2 VEC split
+// micro-tile per thread, 128-bit global loads staged through registers so
+// the next K slice loads while the current one is multiplied, and one
+// barrier per K slice.  Operands must start on 16-byte boundaries with
+// leading dimensions that are multiples of VEC (checked on the host); loads
+// past M, N or K are masked to zero, and every operand buffer carries at
+// least 64 elements of slack so that a masked vector load never leaves its
+// allocation.
+template <typename T> struct VecT;
+template <> struct VecT<float> { using V = float4; static constexpr int W = 4; };
+template <> struct VecT<double> { using V = double2; static constexpr int W = 2; };
+
+template <typename T>
+__device__ inline void vstore4(T* dst, const typename VecT<T>::V& v);
+template <>
+__device__ inline void vstore4<float>(float* d, const float4& v) { d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w; }
+template <>
+__device__ inline void vstore4<double>(double* d, const double2& v) { d[0] = v.x; d[1] = v.y; }
+
+template <typename T>
+__device__ inline typename VecT<T>::V vmask(typename VecT<T>::V v, int valid);
+template <>
+__device__ inline float4 vmask<float>(float4 v, int valid) {
+  if (valid < 4) v.w = 0.f;
+  if (valid < 3) v.z = 0.f;
+  if (valid < 2) v.y = 0.f;
+  if (valid < 1) v.x = 0.f;
+  return v;
+}
+template <>
+__device__ inline double2 vmask<double>(double2 v, int valid) {
+  if (valid < 2) v.y = 0.0;
+  if (valid < 1) v.x = 0.0;
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+gemm_nn_kernel(const GemmProb* __restrict__ probs, const T* __restrict__ A, const T* __restrict__ B,
+               T* __restrict__ C, T alpha, T beta) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  constexpr int BM = 32 * W, BN = 32 * W, BK = 8;
+  constexpr int HALF = BM / 2;
+  const GemmProb p = probs[blockIdx.z];
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if (m0 >= p.M || n0 >= p.N || p.K <= 0) return;
+  __shared__ __align__(16) T As[2][BK][BM + 4];
+  __shared__ __align__(16) T Bs[2][BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  // global load coordinates (one vector of A and one of B per thread)
+  const int am = tid / (BK / W), ak = (tid % (BK / W)) * W;
+  const int bk = tid / (BN / W), bn = (tid % (BN / W)) * W;
+  const T* Ab = A + p.a + (int64_t)(m0 + am) * p.lda + ak;
+  const T* Bb = B + p.b + (int64_t)bk * p.ldb + n0 + bn;
+  const bool a_row = (m0 + am) < p.M;
+  const int b_col_valid = p.N - (n0 + bn);
+  auto load_a = [&](int k0) -> V {
+    V v;
+    const int valid = p.K - (k0 + ak);
+    if (a_row && valid > 0) {
+      v = *reinterpret_cast<const V*>(Ab + k0);
+      v = vmask<T>(v, valid);
+    } else {
+      v = vmask<T>(V{}, 0);
+    }
+    return v;
+  };
+  auto load_b = [&](int k0) -> V {
+    V v;
+    if ((k0 + bk) < p.K && b_col_valid > 0) {
+      v = *reinterpret_cast<const V*>(Bb + (int64_t)k0 * p.ldb);
+      v = vmask<T>(v, b_col_valid);
+    } else {
+      v = vmask<T>(V{}, 0);
+    }
+    return v;
+  };
+  T acc[2 * W][2 * W];
+#pragma unroll
+  for (int i = 0; i < 2 * W; ++i)
+#pragma unroll
+    for (int j = 0; j < 2 * W; ++j) acc[i][j] = T(0);
+  V ra = load_a(0), rb = load_b(0);
+  int buf = 0;
+  {
+    T tmp[W];
+    vstore4<T>(tmp, ra);
+#pragma unroll
+    for (int q = 0; q < W; ++q) As[0][ak + q][am] = tmp[q];
+    *reinterpret_cast<V*>(&Bs[0][bk][bn]) = rb;
+  }
+  __syncthreads();
+  for (int k0 = 0; k0 < p.K; k0 += BK) {
+    const bool more = (k0 + BK) < p.K;
+    if (more) {
+      ra = load_a(k0 + BK);
+      rb = load_b(k0 + BK);
+    }
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      T a[2 * W], b[2 * W];
+      vstore4<T>(a, *reinterpret_cast<const V*>(&As[buf][k][ty * W]));
+      vstore4<T>(a + W, *reinterpret_cast<const V*>(&As[buf][k][HALF + ty * W]));
+      vstore4<T>(b, *reinterpret_cast<const V*>(&Bs[buf][k][tx * W]));
+      vstore4<T>(b + W, *reinterpret_cast<const V*>(&Bs[buf][k][HALF + tx * W]));
+#pragma unroll
+      for (int i = 0; i < 2 * W; ++i)
+#pragma unroll
+        for (int j = 0; j < 2 * W; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      T tmp[W];
+      vstore4<T>(tmp, ra);
+#pragma unroll
+      for (int q = 0; q < W; ++q) As[buf ^ 1][ak + q][am] = tmp[q];
+      *reinterpret_cast<V*>(&Bs[buf ^ 1][bk][bn]) = rb;
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+  T* Cb = C + p.c;
+#pragma unroll
+  for (int i = 0; i < 2 * W; ++i) {
+    const int gm = m0 + (i < W ? ty * W + i : HALF + ty * W + (i - W));
+    if (gm >= p.M) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gn0 = n0 + h * HALF + tx * W;
+      T* cp = Cb + (int64_t)gm * p.ldc + gn0;
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        if (gn0 + j >= p.N) break;
+        const T v = alpha * acc[i][h * W + j];
+        cp[j] = (beta == T(0)) ? v : v + beta * cp[j];
+      }
+    }
+  }
+}
+
+// A list of grouped GEMM problems with its host-side totals.
+struct GemmList {
+  DVec<GemmProb> d;
+  int n = 0, maxM = 0, maxN = 0;
+  double flops = 0.0, bytes = 0.0;
+  bool fast = true;  // every problem meets the vector-load alignment
+  void set(const std::vector<GemmProb>& v, size_t esize, bool ta = false) {
+    n = (int)v.size();
+    maxM = maxN = 0;
+    flops = bytes = 0.0;
+    const int w = (int)(16 / esize);
+    fast = !ta;
+    for (const GemmProb& q : v) {
+      if (q.M <= 0 || q.N <= 0 || q.K <= 0) continue;
+      maxM = std::max(maxM, q.M);
+      maxN = std::max(maxN, q.N);
+      flops += 2.0 * q.M * q.N * q.K;
+      bytes += (double)esize * (2.0 * q.M * q.N + (double)q.K * (q.M + q.N));
+      if (q.a % w || q.b % w || q.lda % w || q.ldb % w) fast = false;
+    }
+    d.upload(v);
+  }
+};
+
 template <typename T, bool TA, bool TB>
 void launch_gemm(const GemmProb* probs, int nprob, int maxM, int maxN, const T* A, const T* B, T* C,
-                 T alpha, T beta, cudaStream_t s) {
+                 T alpha, T beta, cudaStream_t s, bool fast = false) {
   if (nprob == 0 || maxM <= 0 || maxN <= 0) return;
+  if (!TA && !TB && fast) {
+    constexpr int BMf = 32 * VecT<T>::W;
+    dim3 grid(cdiv(maxN, BMf), cdiv(maxM, BMf), nprob);
+    gemm_nn_kernel<T><<<grid, 256, 0, s>>>(probs, A, B, C, alpha, beta);
+    CB_LAUNCH();
+    return;
+  }
   constexpr int BM = GemmCfg<T>::BM, BN = GemmCfg<T>::BN;
   constexpr int NT = (BM / GemmCfg<T>::TM) * (BN / GemmCfg<T>::TN);
   dim3 grid(cdiv(maxN, BN), cdiv(maxM, BM), nprob);
   gemm_grouped_kernel<T, TA, TB><<<grid, NT, 0, s>>>(probs, A, B, C, alpha, beta);
   CB_LAUNCH();
+}
+
+// Launch of a whole list (timed as a setup GEMM when the timer follows them).
+template <typename T, bool TA, bool TB>
+void launch_list(const GemmList& g, const T* A, const T* B, T* C, T alpha, T beta, cudaStream_t s) {
+  if (g.n == 0 || g.maxM == 0) return;
+  timer_begin(CBDDC_TIMER_SWEEP_GEMM, s);
+  launch_gemm<T, TA, TB>(g.d.p, g.n, g.maxM, g.maxN, A, B, C, alpha, beta, s, g.fast);
+  timer_end(CBDDC_TIMER_SWEEP_GEMM, s, g.flops, g.bytes);
 }
 
 // --------------------------------------------------------------- sweeps
@@ -126,14 +312,16 @@ struct SweepDesc {
   int64_t offP;           // diagonal inverse (NB x NB)
 };
 
-// P = inverse of the kb x kb diagonal block of pivot step k (FP64 in smem).
+// P = inverse of the kb x kb diagonal block of pivot step k, by in-place
+// Gauss-Jordan in shared memory in the operator precision T (FP64 for the
+// FP64 path and the coarse matrix, FP32 for FP32 local operators).
 template <typename T>
 __global__ void __launch_bounds__(256)
 sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat, T* __restrict__ Pbuf,
                   int* __restrict__ status, double tol) {
   constexpr int NB = SWEEP_NB;
-  __shared__ double a[NB][NB + 1];
-  __shared__ double fcol[NB];
+  __shared__ T a[NB][NB + 1];
+  __shared__ T fcol[NB];
   __shared__ double piv_scale;
   __shared__ int bad;
   const SweepDesc d = desc[blockIdx.x];
@@ -144,20 +332,20 @@ sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat
   const T* A = mat + d.off;
   for (int t = tid; t < kb * kb; t += blockDim.x) {
     int i = t / kb, j = t % kb;
-    a[i][j] = (double)A[(int64_t)(k0 + i) * d.ld + k0 + j];
+    a[i][j] = A[(int64_t)(k0 + i) * d.ld + k0 + j];
   }
   if (tid == 0) { bad = 0; piv_scale = 0.0; }
   __syncthreads();
   if (tid == 0) {
-    double s = 0.0;
-    for (int i = 0; i < kb; ++i) s = fmax(s, fabs(a[i][i]));
-    piv_scale = s;
+    double sc = 0.0;
+    for (int i = 0; i < kb; ++i) sc = fmax(sc, fabs((double)a[i][i]));
+    piv_scale = sc;
   }
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
-    const double pv = a[j][j];
-    if (tid == 0 && (!(fabs(pv) > tol * piv_scale) || !isfinite(pv))) bad = 1;
-    const double inv = 1.0 / pv;
+    const T pv = a[j][j];
+    if (tid == 0 && (!(fabs((double)pv) > tol * piv_scale) || !isfinite((double)pv))) bad = 1;
+    const T inv = T(1) / pv;
     if (tid < kb) fcol[tid] = a[tid][j];
     __syncthreads();
     // scale row j (in-place Gauss-Jordan inverse)
@@ -166,7 +354,7 @@ sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat
     for (int t = tid; t < kb * kb; t += blockDim.x) {
       int i = t / kb, c = t % kb;
       if (i == j) continue;
-      const double f = fcol[i];
+      const T f = fcol[i];
       if (c == j) a[i][c] = -f * inv;
       else a[i][c] -= f * a[j][c];
     }
@@ -175,7 +363,7 @@ sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat
   T* P = Pbuf + d.offP;
   for (int t = tid; t < kb * kb; t += blockDim.x) {
     int i = t / kb, j = t % kb;
-    P[i * NB + j] = (T)a[i][j];
+    P[i * NB + j] = a[i][j];
   }
   if (tid == 0 && bad) atomicOr(status, DEV_PIVOT);
 }

@@ -478,43 +478,43 @@ void assemble(fem_problem* P, const double* d, double lam, double* residual, boo
   }
 }
 
-// y = K x, 3x3 BSR, one warp per block row; lanes stream the row's values
-// contiguously (coalesced) and gather x through the read-only path.
+// y = K x, 3x3 BSR, one warp per block row.  Lane L < 24 owns row
+// r = L % 3 of the blocks k, k + 8, k + 16, ... (k = L / 3): each value costs
+// one FP64 FMA (FP64 issue is the scarce resource here), loads stay within
+// the row's contiguous value segment, and three shuffle steps (12, 6, 3)
+// sum the eight partial rows.
 __global__ void bsr_spmv_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
                                 const double* __restrict__ vals, const double* __restrict__ x,
-                                double* __restrict__ y, int64_t nrows) {
-  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+                                double* __restrict__ y, int nrows) {
+  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= nrows) return;
-  const int b0 = row_ptr[row], b1 = row_ptr[row + 1];
-  const int64_t v0 = (int64_t)b0 * 9, v1 = (int64_t)b1 * 9;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int64_t v = v0 + lane; v < v1; v += 32) {
-    const int64_t blk = v / 9;
-    const int ent = (int)(v - blk * 9);
-    const int r = ent / 3, c = ent - 3 * (ent / 3);
-    const double p = vals[v] * __ldg(&x[(int64_t)col[blk] * 3 + c]);
-    s0 += (r == 0) ? p : 0.0;
-    s1 += (r == 1) ? p : 0.0;
-    s2 += (r == 2) ? p : 0.0;
+  const int b0 = row_ptr[row], nb = row_ptr[row + 1] - b0;
+  const int r = lane % 3, k = lane / 3;
+  double acc = 0.0;
+  if (lane < 24) {
+    const double* v = vals + (int64_t)b0 * 9 + r * 3;
+    const int* c = col + b0;
+#pragma unroll 4
+    for (int b = k; b < nb; b += 8) {
+      const double* vb = v + (int64_t)b * 9;
+      const double* xb = x + (int64_t)__ldg(c + b) * 3;
+      acc = fma(__ldcs(vb + 0), __ldg(xb + 0), acc);
+      acc = fma(__ldcs(vb + 1), __ldg(xb + 1), acc);
+      acc = fma(__ldcs(vb + 2), __ldg(xb + 2), acc);
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-  }
-  if (lane == 0) {
-    y[row * 3 + 0] = s0;
-    y[row * 3 + 1] = s1;
-    y[row * 3 + 2] = s2;
-  }
+  acc += __shfl_down_sync(0xffffffffu, acc, 12);
+  acc += __shfl_down_sync(0xffffffffu, acc, 6);
+  acc += __shfl_down_sync(0xffffffffu, acc, 3);
+  if (lane < 3) y[(int64_t)row * 3 + lane] = acc;
 }
 
 void bsr_spmv(const fem_problem* P, const double* x, double* y, cudaStream_t s) {
   const int64_t rows = P->n_free_nodes;
   timer_begin(CBDDC_TIMER_SPMV, s);
   bsr_spmv_kernel<<<cdiv(rows * 32, 256), 256, 0, s>>>(P->bsr_row_ptr.p, P->bsr_col.p,
-                                                       P->bsr_vals.p, x, y, rows);
+                                                       P->bsr_vals.p, x, y, (int)rows);
   CB_LAUNCH();
   // bytes: 9 values + 1 column index per block, x read and y written once
   timer_end(CBDDC_TIMER_SPMV, s, 18.0 * P->nnzb, 76.0 * P->nnzb + 16.0 * 3 * rows);

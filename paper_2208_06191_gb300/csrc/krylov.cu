@@ -16,7 +16,7 @@ namespace cbddc {
 
 namespace {
 
-constexpr int DOT_ROWS = 1024;  // rows per CTA in the block dot products
+constexpr int DOT_ROWS = 512;   // rows per CTA in the block dot products
 constexpr int MAXV = 128;       // maximum Krylov vectors per dot launch
 
 __device__ inline double wsum(double v) {
@@ -24,63 +24,84 @@ __device__ inline double wsum(double v) {
   return v;
 }
 
-// partial[c][j] = sum over rows of chunk c of V_j[row] * w[row]
-__global__ void __launch_bounds__(256)
-block_dots_kernel(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ w,
-                  int64_t n, double* __restrict__ partial, const int* __restrict__ done) {
-  if (done && *done) return;
+// Block dot products with a last-block reduction: every CTA writes the
+// partial sums of its DOT_ROWS rows to partial[blockIdx][j]; the CTA that
+// finishes last (atomic ticket) sums them over all CTAs in CTA order, so the
+// result does not depend on scheduling.  Optionally the rows of w are first
+// updated, w -= V hin, which fuses the second Gram-Schmidt pass (or the
+// final update) with the next reduction.
+struct DotArgs {
+  const double* V;      // nvec columns of length n, stride ldv
+  int64_t ldv;
+  int nvec;
+  double* w;            // [n]
+  int64_t n;
+  const double* hin;    // if non-null: w -= V hin before the dots
+  int self_norm;        // dots of w with itself instead of with V
+  double* partial;      // [gridDim.x][MAXV]
+  unsigned* ticket;     // zero on entry, reset by the last CTA
+  double* out;          // [nvec] (or [1] for the norm)
+  const int* done;      // skip everything once GMRES has converged
+};
+
+__device__ inline void last_block_sum(const DotArgs& a, int nout, bool& is_last) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  is_last = last;
+  if (!last) return;
+  for (int j = threadIdx.x; j < nout; j += blockDim.x) {
+    double sum = 0.0;
+    for (unsigned c = 0; c < gridDim.x; ++c) sum += __ldcg(a.partial + (int64_t)c * MAXV + j);
+    a.out[j] = sum;
+  }
+  if (threadIdx.x == 0) *a.ticket = 0u;
+  __threadfence();
+}
+
+__global__ void __launch_bounds__(256) fused_dots_kernel(DotArgs a) {
+  if (a.done && *a.done) return;
   __shared__ double red[8][MAXV];
+  __shared__ double hs[MAXV];
   const int64_t r0 = (int64_t)blockIdx.x * DOT_ROWS;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  double wv[DOT_ROWS / 256];
-#pragma unroll
-  for (int t = 0; t < DOT_ROWS / 256; ++t) {
-    const int64_t row = r0 + tid + 256 * t;
-    wv[t] = row < n ? w[row] : 0.0;
+  constexpr int R = DOT_ROWS / 256;
+  double wv[R];
+  if (a.hin) {
+    for (int j = tid; j < a.nvec; j += 256) hs[j] = a.hin[j];
+    __syncthreads();
   }
-  for (int j = 0; j < nvec; ++j) {
-    const double* v = V + (int64_t)j * ldv;
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int64_t row = r0 + tid + 256 * t;
+    double x = row < a.n ? a.w[row] : 0.0;
+    if (a.hin && row < a.n) {
+      for (int j = 0; j < a.nvec; ++j) x -= a.V[(int64_t)j * a.ldv + row] * hs[j];
+      a.w[row] = x;
+    }
+    wv[t] = x;
+  }
+  const int nout = a.self_norm ? 1 : a.nvec;
+  for (int j = 0; j < nout; ++j) {
     double acc = 0.0;
 #pragma unroll
-    for (int t = 0; t < DOT_ROWS / 256; ++t) {
+    for (int t = 0; t < R; ++t) {
       const int64_t row = r0 + tid + 256 * t;
-      if (row < n) acc += v[row] * wv[t];
+      if (row < a.n) acc += (a.self_norm ? wv[t] : a.V[(int64_t)j * a.ldv + row]) * wv[t];
     }
     acc = wsum(acc);
     if (lane == 0) red[warp][j] = acc;
   }
   __syncthreads();
-  for (int j = tid; j < nvec; j += 256) {
-    double s = 0.0;
-    for (int q = 0; q < 8; ++q) s += red[q][j];
-    partial[(int64_t)blockIdx.x * MAXV + j] = s;
+  for (int j = tid; j < nout; j += 256) {
+    double sm = 0.0;
+    for (int q = 0; q < 8; ++q) sm += red[q][j];
+    a.partial[(int64_t)blockIdx.x * MAXV + j] = sm;
   }
-}
-
-// out[j] (+)= sum_c partial[c][j]
-__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nchunks, int nvec,
-                                       double* __restrict__ out, int accumulate,
-                                       const int* __restrict__ done) {
-  if (done && *done) return;
-  const int j = threadIdx.x;
-  if (j >= nvec) return;
-  double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += partial[(int64_t)c * MAXV + j];
-  out[j] = accumulate ? out[j] + s : s;
-}
-
-// w -= V h
-__global__ void update_kernel(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ h,
-                              double* __restrict__ w, int64_t n, const int* __restrict__ done) {
-  if (done && *done) return;
-  __shared__ double hs[MAXV];
-  for (int j = threadIdx.x; j < nvec; j += blockDim.x) hs[j] = h[j];
-  __syncthreads();
-  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (row >= n) return;
-  double acc = w[row];
-  for (int j = 0; j < nvec; ++j) acc -= V[(int64_t)j * ldv + row] * hs[j];
-  w[row] = acc;
+  bool last;
+  last_block_sum(a, nout, last);
 }
 
 // Column j of the Hessenberg matrix from h1 + h2 (the two CGS passes) and
@@ -88,12 +109,12 @@ __global__ void update_kernel(const double* __restrict__ V, int64_t ldv, int nve
 // scal[0] = |g_{j+1}| / ||b||, scal[1] = 1 / h_{j+1,j}, scal[2] = ||b||.
 __global__ void givens_kernel(int j, int m, double* __restrict__ H, double* __restrict__ cs,
                               double* __restrict__ sn, double* __restrict__ g,
-                              const double* __restrict__ h, const double* __restrict__ wn2,
-                              double* __restrict__ scal, double rtol, int* __restrict__ done,
-                              int* __restrict__ iters) {
+                              const double* __restrict__ h1, const double* __restrict__ h2,
+                              const double* __restrict__ wn2, double* __restrict__ scal, double rtol,
+                              int* __restrict__ done, int* __restrict__ iters) {
   if (*done) return;
   double* col = H + (int64_t)j * (m + 1);
-  for (int i = 0; i <= j; ++i) col[i] = h[i];
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
   const double hn = sqrt(fmax(wn2[0], 0.0));
   col[j + 1] = hn;
   scal[1] = hn > 0.0 ? 1.0 / hn : 0.0;
@@ -174,6 +195,8 @@ void Gmres::ensure_small(int64_t n_) {
   if (partial.p && nchunks == (int)cdiv(n_, DOT_ROWS)) return;
   nchunks = (int)cdiv(n_, DOT_ROWS);
   partial.alloc((size_t)nchunks * MAXV);
+  ticket.alloc(1);
+  CB_CUDA(cudaMemset(ticket.p, 0, sizeof(unsigned)));
   h.alloc(3 * MAXV);
   scal.alloc(8);
   flags.alloc(4);
@@ -203,12 +226,12 @@ Gmres::~Gmres() {
   if (host_flags) cudaFreeHost(host_flags);
 }
 
-// dot products of nvec columns of V (stride n) with w into out (+=)
-static void block_dots(Gmres& G, const double* V, int nvec, const double* w, double* out, int accumulate,
-                       const int* done, cudaStream_t s) {
-  block_dots_kernel<<<G.nchunks, 256, 0, s>>>(V, G.n, nvec, w, G.n, G.partial.p, done);
-  CB_LAUNCH();
-  reduce_partials_kernel<<<1, MAXV, 0, s>>>(G.partial.p, G.nchunks, nvec, out, accumulate, done);
+// out = V^T w over nvec columns (stride ldv), optionally after w -= V hin,
+// or out[0] = ||w||^2 with self_norm; one launch with a last-block reduction.
+static void fused_dots(Gmres& G, const double* V, int64_t ldv, int nvec, double* w, int64_t n,
+                       const double* hin, int self_norm, double* out, const int* done, cudaStream_t s) {
+  DotArgs a{V, ldv, nvec, w, n, hin, self_norm, G.partial.p, G.ticket.p, out, done};
+  fused_dots_kernel<<<(unsigned)cdiv(n, DOT_ROWS), 256, 0, s>>>(a);
   CB_LAUNCH();
 }
 
@@ -234,7 +257,7 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
       axpby_kernel<<<nb, 256, 0, s>>>(1.0, b, -1.0, G.w.p, G.r.p, n);
       CB_LAUNCH();
     }
-    block_dots(G, G.r.p, 1, G.r.p, G.h.p, 0, nullptr, s);
+    fused_dots(G, G.r.p, n, 1, G.r.p, n, nullptr, 1, G.h.p, nullptr, s);
     cycle_start_kernel<<<1, 1, 0, s>>>(G.h.p, G.g.p, m, G.scal.p, first ? 1 : 0, rtol, done, kcount);
     CB_LAUNCH();
     scale_kernel<<<nb, 256, 0, s>>>(G.r.p, G.V.p, n, G.scal.p, 1, nullptr);
@@ -252,18 +275,16 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
       double* zj = G.Zb.p + (int64_t)j * n;
       bddc_run_apply(C, vj, zj, s);
       bsr_spmv(P, zj, G.w.p, s);
-      // classical Gram-Schmidt, twice
-      block_dots(G, G.V.p, j + 1, G.w.p, G.h.p, 0, done, s);
-      update_kernel<<<nb, 256, 0, s>>>(G.V.p, n, j + 1, G.h.p, G.w.p, n, done);
-      CB_LAUNCH();
-      block_dots(G, G.V.p, j + 1, G.w.p, G.h.p + MAXV, 0, done, s);
-      update_kernel<<<nb, 256, 0, s>>>(G.V.p, n, j + 1, G.h.p + MAXV, G.w.p, n, done);
-      CB_LAUNCH();
-      axpby_kernel<<<1, MAXV, 0, s>>>(1.0, G.h.p, 1.0, G.h.p + MAXV, G.h.p, j + 1);
-      CB_LAUNCH();
-      block_dots(G, G.w.p, 1, G.w.p, G.h.p + 2 * MAXV, 0, done, s);
-      givens_kernel<<<1, 1, 0, s>>>(j, m, G.H.p, G.cs.p, G.sn.p, G.g.p, G.h.p, G.h.p + 2 * MAXV, G.scal.p,
-                                    rtol, done, kcount);
+      // classical Gram-Schmidt, twice: h1 = V^T w; w -= V h1 and h2 = V^T w;
+      // w -= V h2 and ||w||^2 (three launches)
+      double* h1 = G.h.p;
+      double* h2 = G.h.p + MAXV;
+      double* wn2 = G.h.p + 2 * MAXV;
+      fused_dots(G, G.V.p, n, j + 1, G.w.p, n, nullptr, 0, h1, done, s);
+      fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h1, 0, h2, done, s);
+      fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h2, 1, wn2, done, s);
+      givens_kernel<<<1, 1, 0, s>>>(j, m, G.H.p, G.cs.p, G.sn.p, G.g.p, h1, h2, wn2, G.scal.p, rtol, done,
+                                    kcount);
       CB_LAUNCH();
       scale_kernel<<<nb, 256, 0, s>>>(G.w.p, G.V.p + (int64_t)(j + 1) * n, n, G.scal.p, 1, done);
       CB_LAUNCH();
@@ -282,7 +303,7 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
       bsr_spmv(P, x, G.w.p, s);
       axpby_kernel<<<nb, 256, 0, s>>>(1.0, b, -1.0, G.w.p, G.r.p, n);
       CB_LAUNCH();
-      block_dots(G, G.r.p, 1, G.r.p, G.h.p, 0, nullptr, s);
+      fused_dots(G, G.r.p, n, 1, G.r.p, n, nullptr, 1, G.h.p, nullptr, s);
       CB_CUDA(cudaMemcpyAsync(G.host_scal + 4, G.h.p, sizeof(double), cudaMemcpyDeviceToHost, s));
       CB_CUDA(cudaMemcpyAsync(G.host_scal, G.scal.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CB_CUDA(cudaStreamSynchronize(s));
@@ -297,10 +318,7 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
 
 double device_norm(fem_problem* P, Gmres& G, const double* v, cudaStream_t s) {
   G.ensure_small(P->n_free);
-  block_dots_kernel<<<G.nchunks, 256, 0, s>>>(v, P->n_free, 1, v, P->n_free, G.partial.p, nullptr);
-  CB_LAUNCH();
-  reduce_partials_kernel<<<1, MAXV, 0, s>>>(G.partial.p, G.nchunks, 1, G.h.p, 0, nullptr);
-  CB_LAUNCH();
+  fused_dots(G, v, P->n_free, 1, const_cast<double*>(v), P->n_free, nullptr, 1, G.h.p, nullptr, s);
   CB_CUDA(cudaMemcpyAsync(G.host_scal + 4, G.h.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   CB_CUDA(cudaStreamSynchronize(s));
   return std::sqrt(G.host_scal[4]);

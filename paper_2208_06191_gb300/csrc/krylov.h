@@ -12,6 +12,7 @@ struct Gmres {
   int nchunks = 0;
   DVec<double> V, Zb, w, r, H, cs, sn, g, y, h, partial, scal;
   DVec<int> flags;
+  DVec<unsigned> ticket;
   double* host_scal = nullptr;
   int* host_flags = nullptr;
   void ensure_small(int64_t n_);
