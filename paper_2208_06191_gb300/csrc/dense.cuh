@@ -146,7 +146,7 @@ __device__ inline double2 vmask<double>(double2 v, int valid) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 gemm_nn_kernel(const GemmProb* __restrict__ probs, const T* __restrict__ A, const T* __restrict__ B,
                T* __restrict__ C, T alpha, T beta) {
   using V = typename VecT<T>::V;
@@ -232,6 +232,7 @@ gemm_nn_kernel(const GemmProb* __restrict__ probs, const T* __restrict__ A, cons
     }
   }
   T* Cb = C + p.c;
+  const bool cvec = ((p.c % W) == 0) && ((p.ldc % W) == 0);
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i) {
     const int gm = m0 + (i < W ? ty * W + i : HALF + ty * W + (i - W));
@@ -240,11 +241,22 @@ gemm_nn_kernel(const GemmProb* __restrict__ probs, const T* __restrict__ A, cons
     for (int h = 0; h < 2; ++h) {
       const int gn0 = n0 + h * HALF + tx * W;
       T* cp = Cb + (int64_t)gm * p.ldc + gn0;
+      if (cvec && gn0 + W <= p.N) {
+        T v[W];
+        if (beta != T(0)) vstore4<T>(v, *reinterpret_cast<const V*>(cp));
 #pragma unroll
-      for (int j = 0; j < W; ++j) {
-        if (gn0 + j >= p.N) break;
-        const T v = alpha * acc[i][h * W + j];
-        cp[j] = (beta == T(0)) ? v : v + beta * cp[j];
+        for (int j = 0; j < W; ++j) v[j] = (beta == T(0)) ? alpha * acc[i][h * W + j] : alpha * acc[i][h * W + j] + beta * v[j];
+        V o;
+        if constexpr (W == 4) o = V{v[0], v[1], v[2], v[3]};
+        else o = V{v[0], v[1]};
+        *reinterpret_cast<V*>(cp) = o;
+      } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          if (gn0 + j >= p.N) break;
+          const T v = alpha * acc[i][h * W + j];
+          cp[j] = (beta == T(0)) ? v : v + beta * cp[j];
+        }
       }
     }
   }
@@ -312,60 +324,74 @@ struct SweepDesc {
   int64_t offP;           // diagonal inverse (NB x NB)
 };
 
-// P = inverse of the kb x kb diagonal block of pivot step k, by in-place
-// Gauss-Jordan in shared memory in the operator precision T (FP64 for the
-// FP64 path and the coarse matrix, FP32 for FP32 local operators).
+// P = inverse of the kb x kb diagonal block of pivot step k, by Gauss-Jordan
+// in the operator precision T.  Thread c of the 64-thread CTA keeps column c
+// in registers (the pivot loop is fully unrolled so the register index is
+// static); at pivot j the owner of column j publishes it to shared memory
+// (double-buffered, so one barrier per pivot suffices) and every thread
+// updates its own column:
+//   a[j][c] <- a[j][c] / p,  a[i][c] <- a[i][c] - a[i][j] a[j][c]  (c != j),
+//   a[i][j] <- -a[i][j] / p, a[j][j] <- 1 / p.
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(SWEEP_NB)
 sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat, T* __restrict__ Pbuf,
                   int* __restrict__ status, double tol) {
   constexpr int NB = SWEEP_NB;
-  __shared__ T a[NB][NB + 1];
-  __shared__ T fcol[NB];
+  __shared__ T colj[2][NB];
   __shared__ double piv_scale;
   __shared__ int bad;
   const SweepDesc d = desc[blockIdx.x];
   const int k0 = k * NB;
   if (k0 >= d.p) return;
   const int kb = min(NB, d.p - k0);
-  const int tid = threadIdx.x;
-  const T* A = mat + d.off;
-  for (int t = tid; t < kb * kb; t += blockDim.x) {
-    int i = t / kb, j = t % kb;
-    a[i][j] = A[(int64_t)(k0 + i) * d.ld + k0 + j];
-  }
-  if (tid == 0) { bad = 0; piv_scale = 0.0; }
+  const int c = threadIdx.x;
+  const T* A = mat + d.off + (int64_t)k0 * d.ld + k0;
+  T a[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) a[i] = (i < kb && c < kb) ? A[(int64_t)i * d.ld + c] : T(0);
+  if (c == 0) { bad = 0; piv_scale = 0.0; }
   __syncthreads();
-  if (tid == 0) {
-    double sc = 0.0;
-    for (int i = 0; i < kb; ++i) sc = fmax(sc, fabs((double)a[i][i]));
-    piv_scale = sc;
+  // scale of the pivots: largest |diagonal| of the block (thread c owns a[c][c])
+  {
+    double dv = 0.0;
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if (i == c && c < kb) dv = fabs((double)a[i]);
+    for (int o = 16; o > 0; o >>= 1) dv = fmax(dv, __shfl_xor_sync(0xffffffffu, dv, o));
+    if ((c & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(&piv_scale),
+                                 __double_as_longlong(dv));  // non-negative doubles order as integers
   }
   __syncthreads();
-  for (int j = 0; j < kb; ++j) {
-    const T pv = a[j][j];
-    if (tid == 0 && (!(fabs((double)pv) > tol * piv_scale) || !isfinite((double)pv))) bad = 1;
-    const T inv = T(1) / pv;
-    if (tid < kb) fcol[tid] = a[tid][j];
-    __syncthreads();
-    // scale row j (in-place Gauss-Jordan inverse)
-    for (int c = tid; c < kb; c += blockDim.x) a[j][c] = (c == j) ? inv : a[j][c] * inv;
-    __syncthreads();
-    for (int t = tid; t < kb * kb; t += blockDim.x) {
-      int i = t / kb, c = t % kb;
-      if (i == j) continue;
-      const T f = fcol[i];
-      if (c == j) a[i][c] = -f * inv;
-      else a[i][c] -= f * a[j][c];
+  const double scale = piv_scale;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < kb) {
+      if (c == j) {
+#pragma unroll
+        for (int i = 0; i < NB; ++i) colj[j & 1][i] = a[i];
+      }
+      __syncthreads();
+      const T pv = colj[j & 1][j];
+      const T inv = T(1) / pv;
+      if (c == j) {
+        if (!(fabs((double)pv) > tol * scale) || !isfinite((double)pv)) bad = 1;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) a[i] = (i == j) ? inv : -a[i] * inv;
+      } else if (c < kb) {
+        const T t = a[j] * inv;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) a[i] = (i == j) ? t : a[i] - colj[j & 1][i] * t;
+      }
     }
-    __syncthreads();
   }
+  __syncthreads();
   T* P = Pbuf + d.offP;
-  for (int t = tid; t < kb * kb; t += blockDim.x) {
-    int i = t / kb, j = t % kb;
-    P[i * NB + j] = a[i][j];
+  if (c < kb) {
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if (i < kb) P[i * NB + c] = a[i];
   }
-  if (tid == 0 && bad) atomicOr(status, DEV_PIVOT);
+  if (c == 0 && bad) atomicOr(status, DEV_PIVOT);
 }
 
 // Builds X and Y panels and zeroes the pivot rows/columns, for indices
