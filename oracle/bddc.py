@@ -26,6 +26,11 @@ Apply z = M^-1 r:
   7. z_I = A_II^-1 (r_I - A_IGamma z_Gamma)
 Steps 2-6 are M_BDDC^-1 = R_D^T S~^-1 R_D applied to the Schur complement
 system; steps 1 and 7 are the exact outer block factors.
+
+Multilevel BDDC (Section 3.2, last paragraph; Section 7): the coarse
+problem is itself an unassembled matrix whose "elements" are the subdomains
+with their local coarse matrices; grouping those subdomains into level-2
+subdomains and applying BDDC once to it replaces S_PiPi^-1 in step 5.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -70,37 +75,109 @@ def outer_boundary_nodes(fe):
     return on
 
 
-class Classification:
-    """Interface classes (faces, edges, vertices) of an element partition."""
+class FineLevel:
+    """The fine level of BDDC: element and face matrices of the FE problem.
 
-    def __init__(self, fe, elem_part, n_parts):
-        self.n_parts = n_parts
-        part = np.asarray(elem_part, dtype=np.int64)
-        n = fe.n_nodes
-        # subdomain membership of each node (free nodes only)
+    Nodes carry 3 DoFs; Dirichlet nodes carry none.  ``elem_nodes`` and
+    ``part`` define subdomain membership and node adjacency."""
+
+    def __init__(self, fe, Ke, Kf):
+        self.fe = fe
+        self.Ke, self.Kf = Ke, Kf
+        self.n_nodes = fe.n_nodes
+        self.free = ~fe.is_dirichlet
+        self.node_to_free = fe.node_to_free
+        self.n_free = fe.n_free
+        self.elem_nodes = fe.elems
+        self.part = np.asarray(fe.prob["elem_part"], dtype=np.int64)
+        self.n_parts = int(fe.prob["n_parts"])
+        self.on_boundary = outer_boundary_nodes(fe)
+
+    def local_matrix(self, i, dof_map, n):
+        return self.fe.assemble(self.Ke, self.Kf, self.part == i, dof_map, n)
+
+
+class CoarseLevel:
+    """The coarse problem of a BDDC level seen as an unassembled matrix:
+    its nodes are the coarse nodes (a primal vertex, or an averaged class,
+    each with 3 DoFs), its "elements" are the subdomains of the finer level
+    with their local coarse matrices Phi_i^T A^(i) Phi_i, and ``part``
+    groups those subdomains into the subdomains of this level (Section 3.2,
+    multilevel BDDC)."""
+
+    def __init__(self, n_nodes, elem_nodes, elem_K, part, n_parts):
+        self.n_nodes = int(n_nodes)
+        self.free = np.ones(self.n_nodes, dtype=bool)
+        self.node_to_free = np.arange(self.n_nodes)
+        self.n_free = 3 * self.n_nodes
+        self.elem_nodes = [np.asarray(e, dtype=np.int64) for e in elem_nodes]
+        self.elem_K = elem_K
+        self.part = np.asarray(part, dtype=np.int64)
+        self.n_parts = int(n_parts)
+        self.on_boundary = None
+
+    def local_matrix(self, i, dof_map, n):
+        rows, cols, vals = [], [], []
+        for e in np.nonzero(self.part == i)[0]:
+            nodes = self.elem_nodes[e]
+            gd = (3 * nodes[:, None] + np.arange(3)).reshape(-1)
+            m = dof_map[gd]
+            K = self.elem_K[e]
+            rows.append(np.repeat(m, m.size))
+            cols.append(np.tile(m, m.size))
+            vals.append(K.reshape(-1))
+        A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(n, n))
+        return A.tocsr()
+
+
+class Classification:
+    """Interface classes (faces, edges, vertices) of a partition."""
+
+    def __init__(self, level, elem_part=None, n_parts=None):
+        if not isinstance(level, (FineLevel, CoarseLevel)):
+            # FE problem given directly: classify its elements
+            fe = level
+            level = FineLevel.__new__(FineLevel)
+            level.n_nodes = fe.n_nodes
+            level.free = ~fe.is_dirichlet
+            level.elem_nodes = fe.elems
+            level.part = np.asarray(elem_part, dtype=np.int64)
+            level.n_parts = int(n_parts)
+            level.on_boundary = outer_boundary_nodes(fe)
+        self.n_parts = level.n_parts
+        part = level.part
+        n = level.n_nodes
         memb = [set() for _ in range(n)]
-        for e in range(fe.n_el):
+        for e, nodes in enumerate(level.elem_nodes):
             p = int(part[e])
-            for a in fe.elems[e]:
+            for a in nodes:
                 memb[a].add(p)
-        self.members = [tuple(sorted(s)) if not fe.is_dirichlet[a] else ()
+        self.members = [tuple(sorted(s)) if level.free[a] else ()
                         for a, s in enumerate(memb)]
         self.count = np.array([len(s) for s in self.members])
         iface = self.count >= 2
         self.interface = iface
-        # group interface nodes by sharing set; connect through elements
         key_of = {}
         key = -np.ones(n, dtype=np.int64)
         for a in np.nonzero(iface)[0]:
             key[a] = key_of.setdefault(self.members[a], len(key_of))
-        nen = fe.n_en
-        ii = np.repeat(fe.elems, nen, axis=1).reshape(-1)
-        jj = np.tile(fe.elems, (1, nen)).reshape(-1)
+        if isinstance(level.elem_nodes, np.ndarray) and level.elem_nodes.ndim == 2:
+            en = level.elem_nodes
+            ii = np.repeat(en, en.shape[1], axis=1).reshape(-1)
+            jj = np.tile(en, (1, en.shape[1])).reshape(-1)
+        else:
+            ii, jj = [], []
+            for nodes in level.elem_nodes:
+                nodes = np.asarray(nodes)
+                ii.append(np.repeat(nodes, nodes.size))
+                jj.append(np.tile(nodes, nodes.size))
+            ii = np.concatenate(ii)
+            jj = np.concatenate(jj)
         same = (key[ii] >= 0) & (key[ii] == key[jj])
-        G = sp.coo_matrix((np.ones(same.sum()), (ii[same], jj[same])),
-                          shape=(n, n))
+        G = sp.coo_matrix((np.ones(same.sum()), (ii[same], jj[same])), shape=(n, n))
         ncomp, comp = csg.connected_components(G, directed=False)
-        on_bnd = outer_boundary_nodes(fe)
+        on_bnd = level.on_boundary
         classes = {}
         for a in np.nonzero(iface)[0]:
             classes.setdefault(int(comp[a]), []).append(int(a))
@@ -112,9 +189,9 @@ class Classification:
             elif len(nodes) == 1:
                 vertices.append(nodes[0])
             else:
-                ends = [a for a in nodes if on_bnd[a]]
+                ends = [a for a in nodes if on_bnd is not None and on_bnd[a]]
                 vertices.extend(ends)
-                rest = sorted(a for a in nodes if not on_bnd[a])
+                rest = sorted(a for a in nodes if on_bnd is None or not on_bnd[a])
                 if rest:
                     edges.append(rest)
         self.vertices = sorted(vertices)
@@ -123,14 +200,20 @@ class Classification:
 
 
 class BDDC:
-    """BDDC setup for one tangent (element and face matrices Ke, Kf)."""
+    """BDDC setup for one tangent.
 
-    def __init__(self, fe, Ke, Kf, primal="V", classification=None):
-        prob = fe.prob
-        self.fe = fe
-        part = np.asarray(prob["elem_part"], dtype=np.int64)
-        n_parts = int(prob["n_parts"])
-        cl = classification or Classification(fe, part, n_parts)
+    ``fe, Ke, Kf``: the FE problem and its element / face matrices (the fine
+    level), or a ``CoarseLevel`` as first argument (then Ke, Kf are unused).
+    ``level2``: None for the two-level method; otherwise a dict with
+    ``part`` (level-2 subdomain of every subdomain of this level),
+    ``n_parts`` and ``primal``: the coarse problem is then approximated by
+    one application of BDDC on those level-2 subdomains (multilevel BDDC,
+    Section 3.2); a nested ``level2`` entry adds a further level."""
+
+    def __init__(self, fe, Ke=None, Kf=None, primal="V", classification=None, level2=None):
+        level = fe if isinstance(fe, CoarseLevel) else FineLevel(fe, Ke, Kf)
+        self.level = level
+        cl = classification or Classification(level)
         self.cl = cl
         use_v = "V" in primal
         avg_classes = []
@@ -148,23 +231,28 @@ class BDDC:
             for a in c:
                 node_class[a] = j
         self.subs = []
-        S = np.zeros((self.n_pi, self.n_pi))
-        n2f = fe.node_to_free
-        for i in range(n_parts):
-            nodes = np.unique(fe.elems[part == i])
-            nodes = nodes[~fe.is_dirichlet[nodes]]
+        n2f = level.node_to_free
+        part = level.part
+        elem_nodes = level.elem_nodes
+        sub_nodes = [set() for _ in range(level.n_parts)]
+        for e, nodes in enumerate(elem_nodes):
+            sub_nodes[int(part[e])].update(int(a) for a in nodes)
+        Sc_list = []
+        for i in range(level.n_parts):
+            nodes = np.array(sorted(sub_nodes[i]), dtype=np.int64)
+            nodes = nodes[level.free[nodes]]
             nloc = nodes.size
-            dof_map = -np.ones(3 * fe.n_nodes, dtype=np.int64)
+            dof_map = -np.ones(3 * level.n_nodes, dtype=np.int64)
             for c in range(3):
                 dof_map[3 * nodes + c] = 3 * np.arange(nloc) + c
-            A = fe.assemble(Ke, Kf, part == i, dof_map, 3 * nloc).tocsr()
+            A = level.local_matrix(i, dof_map, 3 * nloc).tocsr()
             gdof = (3 * n2f[nodes][:, None] + np.arange(3)).reshape(-1)
             iface = cl.count[nodes] >= 2
             ldofI = (3 * np.nonzero(~iface)[0][:, None] + np.arange(3)).ravel()
             ldofG = (3 * np.nonzero(iface)[0][:, None] + np.arange(3)).ravel()
             Dg = np.repeat(1.0 / cl.count[nodes[iface]], 3)
             # primal vertex DoFs (local) and remaining DoFs r
-            is_v = np.array([use_v and a in vpos for a in nodes])
+            is_v = np.array([use_v and a in vpos for a in nodes], dtype=bool)
             ldofV = (3 * np.nonzero(is_v)[0][:, None] + np.arange(3)).ravel()
             gV = np.array([vpos[a] + c for a in nodes[is_v] for c in range(3)],
                           dtype=np.int64)
@@ -208,18 +296,32 @@ class BDDC:
                 Phi[ldofR, :] = sol[:ldofR.size]
                 gP = np.concatenate([gV, np.array(gA, dtype=np.int64)])
                 Sc = Phi.T @ (A @ Phi)
-                S[np.ix_(gP, gP)] += Sc
             else:
                 gP = np.zeros(0, dtype=np.int64)
+                Sc = np.zeros((0, 0))
+            Sc_list.append(Sc)
             AII = A[ldofI][:, ldofI].tocsc()
             sub = dict(nodes=nodes, A=A, gdof=gdof, ldofI=ldofI, ldofG=ldofG,
                        ldofR=ldofR, Dg=Dg, lu_sad=lu_sad, na=na, Phi=Phi,
-                       gP=gP,
+                       gP=gP, Sc=Sc,
                        luII=spla.splu(AII) if ldofI.size else None,
                        AGI=A[ldofG][:, ldofI], AIG=A[ldofI][:, ldofG])
             self.subs.append(sub)
-        self.S_pipi = S
-        self.n_free = fe.n_free
+        self.n_free = level.n_free
+        self.coarse = None
+        if level2 is not None and self.n_pi > 0:
+            # coarse nodes: 3 consecutive primal DoFs each (node-major)
+            clevel = CoarseLevel(self.n_pi // 3, [sub["gP"][::3] // 3 for sub in self.subs],
+                                 Sc_list, level2["part"], level2["n_parts"])
+            self.coarse = BDDC(clevel, primal=level2.get("primal", "VEF"),
+                               level2=level2.get("level2"))
+            self.S_pipi = None
+        else:
+            S = np.zeros((self.n_pi, self.n_pi))
+            for sub in self.subs:
+                if sub["gP"].size:
+                    S[np.ix_(sub["gP"], sub["gP"])] += sub["Sc"]
+            self.S_pipi = S
 
     def _local_solve(self, sub, f_loc):
         """Constrained Neumann solve with zero primal values: w_v = 0,
@@ -229,6 +331,15 @@ class BDDC:
         w = np.zeros(f_loc.size)
         w[sub["ldofR"]] = sol[:sub["ldofR"].size]
         return w
+
+    def coarse_solve(self, c):
+        """S_PiPi^-1 c (two levels), or one BDDC application on the coarse
+        problem (multilevel)."""
+        if c.size == 0:
+            return c
+        if self.coarse is not None:
+            return self.coarse.apply(c)
+        return np.linalg.solve(self.S_pipi, c)
 
     def apply(self, r):
         r = np.asarray(r, dtype=float)
@@ -243,7 +354,7 @@ class BDDC:
             else:
                 u = np.zeros(0)
             u0.append(u)
-        c = np.zeros(self.S_pipi.shape[0])
+        c = np.zeros(self.n_pi)
         ws = []
         for sub in self.subs:
             gd = sub["gdof"]
@@ -253,7 +364,7 @@ class BDDC:
             if sub["gP"].size:
                 np.add.at(c, sub["gP"], sub["Phi"].T @ f)
             ws.append(w)
-        uc = np.linalg.solve(self.S_pipi, c) if c.size else c
+        uc = self.coarse_solve(c)
         zG = np.zeros_like(r)
         for sub, w in zip(self.subs, ws):
             gd = sub["gdof"]

@@ -142,3 +142,50 @@ def test_bddc_newton_matches_direct_newton():
     d2, log2 = newton_solve(prob, make_bddc_solver("VE", tol=1e-12), tol=1e-11)
     assert np.linalg.norm(d2 - d1) <= 1e-10 * np.linalg.norm(d1)
     assert all(l["gmres_its"] > 1 for l in log2)
+
+
+def _ml_setup(nx=8, ny=8, nz=4, parts=(4, 4, 2), groups=(2, 2, 1), p=1e3, g=3e4):
+    from workloads import box_groups
+    prob = slab_problem(nx, ny, nz, parts=parts, pressure=p, gamma=g)
+    fe, K, Ke, Kf = _setup(prob, 0.0 if p == 0 else 0.005)
+    part2, n2 = box_groups(parts, groups)
+    return prob, fe, K, Ke, Kf, part2, n2
+
+
+def test_multilevel_with_one_level2_subdomain_equals_two_level():
+    # One level-2 subdomain: the level-2 BDDC solves the coarse problem
+    # exactly, so the multilevel apply must equal the two-level one.
+    prob, fe, K, Ke, Kf, part2, n2 = _ml_setup(groups=(1, 1, 1))
+    two = BDDC(fe, Ke, Kf, "VE")
+    ml = BDDC(fe, Ke, Kf, "VE", level2=dict(part=part2, n_parts=n2, primal="VEF"))
+    assert ml.coarse is not None and ml.coarse.n_pi == 0
+    r = np.random.default_rng(11).standard_normal(fe.n_free)
+    z2, zm = two.apply(r), ml.apply(r)
+    assert np.linalg.norm(zm - z2) <= 1e-10 * np.linalg.norm(z2)
+
+
+def test_multilevel_takes_at_least_the_two_level_iterations():
+    # Section 7: approximating the coarse problem by BDDC raises the
+    # iteration count relative to the exact coarse solve.
+    prob, fe, K, Ke, Kf, part2, n2 = _ml_setup()
+    b = np.random.default_rng(12).standard_normal(fe.n_free)
+    two = BDDC(fe, Ke, Kf, "VE")
+    ml = BDDC(fe, Ke, Kf, "VE", level2=dict(part=part2, n_parts=n2, primal="VEF"))
+    assert ml.coarse.n_pi > 0
+    _, i2, _ = gmres(lambda v: K @ v, b, two.apply, tol=1e-8)
+    x, im, _ = gmres(lambda v: K @ v, b, ml.apply, tol=1e-8)
+    assert im >= i2
+    assert np.linalg.norm(K @ x - b) <= 2e-8 * np.linalg.norm(b)
+
+
+def test_multilevel_symmetric_case():
+    # Symmetric tangent: the multilevel preconditioner stays symmetric and
+    # M^-1 A keeps a real spectrum bounded below by 1.
+    prob, fe, K, Ke, Kf, part2, n2 = _ml_setup(6, 6, 4, parts=(3, 3, 2), groups=(2, 2, 1), p=0.0, g=0.0)
+    ml = BDDC(fe, Ke, Kf, "VE", level2=dict(part=part2, n_parts=n2, primal="VEF"))
+    n = fe.n_free
+    Minv = np.column_stack([ml.apply(e) for e in np.eye(n)])
+    assert np.abs(Minv - Minv.T).max() <= 1e-10 * np.abs(Minv).max()
+    ev = np.linalg.eigvals(Minv @ K.toarray())
+    assert np.abs(ev.imag).max() <= 1e-8 * np.abs(ev).max()
+    assert ev.real.min() >= 1.0 - 1e-9

@@ -16,5 +16,5 @@ Conventions (they are part of the library's public input format):
 * Degrees of freedom are interleaved per node (x, y, z), Section 4 of the
   paper; a Dirichlet node has all three components clamped.
 """
-from .slab import slab_problem, slab_config, SLAB_CONFIGS  # noqa: F401
+from .slab import slab_problem, slab_config, SLAB_CONFIGS, box_groups  # noqa: F401
 from .material import default_material  # noqa: F401

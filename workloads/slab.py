@@ -119,3 +119,17 @@ def slab_config(name, **overrides):
     kw = dict(SLAB_CONFIGS[name])
     kw.update(overrides)
     return slab_problem(**kw)
+
+
+def box_groups(parts, groups):
+    """Level-2 partition of box subdomains: box (bx, by, bz) of a
+    px x py x pz box partition goes to group (bx*gx//px, by*gy//py, bz*gz//pz)
+    of a gx x gy x gz grouping.  Returns (group id per subdomain, n_groups)."""
+    px, py, pz = parts
+    gx, gy, gz = groups
+    out = []
+    for bz in range(pz):
+        for by in range(py):
+            for bx in range(px):
+                out.append((bx * gx) // px + gx * ((by * gy) // py + gy * ((bz * gz) // pz)))
+    return np.array(out, dtype=np.int32), gx * gy * gz
