@@ -176,12 +176,24 @@ typedef struct {
                         outputs of bddc_apply stay FP64, coarse solve FP64) */
   int primal;        /* OR of CBDDC_PRIMAL_* (Section 6.2: V, VE, VEF ...) */
   double pivot_tol;  /* a pivot below pivot_tol * max|diag| is an error   */
+  /* Multilevel BDDC (Section 3.2, last paragraph; Section 7).  levels = 2
+     (or 0): the coarse problem S_PiPi is inverted densely in FP64.
+     levels = 3: the coarse problem, an unassembled matrix whose elements
+     are the subdomains with their local coarse matrices, is approximated by
+     one FP64 BDDC application on n_parts2 level-2 subdomains (part2[i] is
+     the level-2 subdomain of subdomain i, host array, copied), with primal
+     space primal2; its own coarse problem is inverted densely in FP64. */
+  int levels;
+  int n_parts2;
+  const int32_t* part2;
+  int primal2;
 } bddc_options;
 
 typedef struct bddc_ctx bddc_ctx;
 
 typedef struct {
   int n_primal;                /* coarse space dimension                    */
+  int n_primal2;               /* level-2 coarse dimension (levels = 3)     */
   int precision;
   int64_t local_bytes;         /* bytes of local operators read per apply   */
   int64_t device_bytes;        /* device memory held by the context         */
@@ -263,6 +275,10 @@ typedef struct {
   double newton_rtol;  /* ||F(d)|| <= newton_rtol ||F(d^{n,0})||             */
   double gmres_rtol;   /* relative residual of each tangent solve            */
   double pivot_tol;
+  int levels;          /* as in bddc_options                                 */
+  int n_parts2;
+  const int32_t* part2;
+  int primal2;
 } solve_options;
 
 #define CBDDC_MAX_RECORDS 512

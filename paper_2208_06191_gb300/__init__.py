@@ -85,11 +85,14 @@ class _Tangent(ctypes.Structure):
 
 
 class _BddcOptions(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("primal", ctypes.c_int), ("pivot_tol", ctypes.c_double)]
+    _fields_ = [("precision", ctypes.c_int), ("primal", ctypes.c_int), ("pivot_tol", ctypes.c_double),
+                ("levels", ctypes.c_int), ("n_parts2", ctypes.c_int), ("part2", _i32p),
+                ("primal2", ctypes.c_int)]
 
 
 class _BddcInfo(ctypes.Structure):
-    _fields_ = [("n_primal", ctypes.c_int), ("precision", ctypes.c_int), ("local_bytes", ctypes.c_int64),
+    _fields_ = [("n_primal", ctypes.c_int), ("n_primal2", ctypes.c_int), ("precision", ctypes.c_int),
+                ("local_bytes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("setup_flops", ctypes.c_double)]
 
 
@@ -106,7 +109,8 @@ class _SolveOptions(ctypes.Structure):
         ("precision", ctypes.c_int), ("primal", ctypes.c_int), ("load_steps", ctypes.c_int),
         ("max_newton", ctypes.c_int), ("max_halvings", ctypes.c_int), ("restart", ctypes.c_int),
         ("max_gmres", ctypes.c_int), ("newton_rtol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
-        ("pivot_tol", ctypes.c_double),
+        ("pivot_tol", ctypes.c_double), ("levels", ctypes.c_int), ("n_parts2", ctypes.c_int),
+        ("part2", _i32p), ("primal2", ctypes.c_int),
     ]
 
 
@@ -220,11 +224,21 @@ def _ptr(t, dtype=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _part2_arg(part2):
+    if part2 is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(part2, dtype=np.int32))
+    return arr, arr.ctypes.data_as(_i32p)
+
+
 class SolveOptions:
-    """Options of the Newton-GMRES-BDDC solve (see solve_options in the header)."""
+    """Options of the Newton-GMRES-BDDC solve (see solve_options in the header).
+    Multilevel BDDC: levels=3 with part2 (level-2 subdomain of every
+    subdomain), n_parts2 and primal2."""
 
     def __init__(self, precision=FP64, primal="V", load_steps=4, max_newton=25, max_halvings=6,
-                 restart=100, max_gmres=1000, newton_rtol=1e-8, gmres_rtol=1e-8, pivot_tol=1e-13):
+                 restart=100, max_gmres=1000, newton_rtol=1e-8, gmres_rtol=1e-8, pivot_tol=1e-13,
+                 levels=2, part2=None, n_parts2=0, primal2="VEF"):
         self.precision = precision
         self.primal = primal if isinstance(primal, int) else primal_mask(primal)
         self.load_steps = load_steps
@@ -235,11 +249,16 @@ class SolveOptions:
         self.newton_rtol = newton_rtol
         self.gmres_rtol = gmres_rtol
         self.pivot_tol = pivot_tol
+        self.levels = levels
+        self.part2_arr, self._part2_ptr = _part2_arg(part2)
+        self.n_parts2 = int(n_parts2)
+        self.primal2 = primal2 if isinstance(primal2, int) else primal_mask(primal2)
 
     def c(self):
         return _SolveOptions(self.precision, self.primal, self.load_steps, self.max_newton,
                              self.max_halvings, self.restart, self.max_gmres, self.newton_rtol,
-                             self.gmres_rtol, self.pivot_tol)
+                             self.gmres_rtol, self.pivot_tol, self.levels, self.n_parts2,
+                             self._part2_ptr, self.primal2)
 
 
 def _record_dict(r):
@@ -388,11 +407,14 @@ class Problem:
 class BDDC:
     """BDDC preconditioner context (bddc_ctx) for a problem."""
 
-    def __init__(self, problem, precision=FP64, primal="V", pivot_tol=1e-13):
+    def __init__(self, problem, precision=FP64, primal="V", pivot_tol=1e-13, levels=2, part2=None,
+                 n_parts2=0, primal2="VEF"):
         self.problem = problem
         self._h = ctypes.c_void_p()
+        self._part2, p2 = _part2_arg(part2)
         self._opt = _BddcOptions(precision, primal if isinstance(primal, int) else primal_mask(primal),
-                                 pivot_tol)
+                                 pivot_tol, levels, int(n_parts2), p2,
+                                 primal2 if isinstance(primal2, int) else primal_mask(primal2))
 
     @classmethod
     def _wrap(cls, h, problem):

@@ -585,9 +585,85 @@ apply_extend_kernel(const int* __restrict__ nI, const int* __restrict__ nG,
                [&](int row, T v) { z[gdofI[oi + row]] = u0[oi + row] - (double)v; });
 }
 
+// Local coarse matrix of subdomain s (n_c x n_c, node-major: 3 DoFs per
+// coarse node) -> 3x3 contribution blocks of the coarse problem, block
+// (a, b) at cbase[s] + a * (n_c / 3) + b.
+template <typename T>
+__global__ void kc_to_blocks_kernel(const int* __restrict__ nc, const int64_t* __restrict__ offKc,
+                                    const int* __restrict__ ldPhi, const int64_t* __restrict__ cbase,
+                                    const T* __restrict__ Kc, double* __restrict__ blocks) {
+  const int s = blockIdx.y;
+  const int n = nc[s];
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  const int k = n / 3;
+  const int a = i / 3, b = j / 3;
+  blocks[(cbase[s] + (int64_t)a * k + b) * 9 + (i % 3) * 3 + (j % 3)] =
+      (double)Kc[offKc[s] + (int64_t)i * ldPhi[s] + j];
+}
+
+__global__ void or_status_kernel(const int* __restrict__ from, int* __restrict__ to) {
+  if (*from) atomicOr(to, *from);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ create
+// The coarse problem of C as an unassembled matrix (Section 3.2, multilevel
+// BDDC): nodes are the coarse nodes (3 consecutive primal DoFs each), the
+// elements are the subdomains of C with their local coarse matrices, and
+// C->part2 groups them into the level-2 subdomains.  No node is clamped.
+static void build_coarse_problem(bddc_ctx* C, fem_problem* CP) {
+  const int nsub = C->nsub;
+  const int nn = C->n_pi / 3;
+  CP->elem_type = 0;
+  CP->n_nodes = nn;
+  CP->n_el = nsub;
+  CP->n_parts = C->n_parts2;
+  CP->n_free_nodes = nn;
+  CP->n_free = 3 * (int64_t)nn;
+  CP->node_to_free.resize(nn);
+  for (int v = 0; v < nn; ++v) CP->node_to_free[v] = v;
+  std::vector<int> eptr{0}, eidx;
+  std::vector<int64_t> cbase;
+  int64_t nb = 0;
+  for (int s = 0; s < nsub; ++s) {
+    const int k = C->nc[s] / 3;
+    for (int q = 0; q < k; ++q) eidx.push_back(C->gprim_h[C->offC[s] + 3 * q] / 3);
+    eptr.push_back((int)eidx.size());
+    cbase.push_back(nb);
+    nb += (int64_t)k * k;
+  }
+  std::vector<std::vector<int>> members(nn);
+  for (int s = 0; s < nsub; ++s)
+    for (int q = eptr[s]; q < eptr[s + 1]; ++q) members[eidx[q]].push_back(C->part2[s]);
+  CP->share_count.assign(nn, 0);
+  for (int v = 0; v < nn; ++v) {
+    auto& mv = members[v];
+    std::sort(mv.begin(), mv.end());
+    mv.erase(std::unique(mv.begin(), mv.end()), mv.end());
+    CP->share_count[v] = (int)mv.size();
+  }
+  CP->subs.assign(CP->n_parts, SubHost{});
+  for (int v = 0; v < nn; ++v)
+    for (int g : members[v]) {
+      CP->subs[g].nodes.push_back(v);
+      CP->subs[g].iface.push_back(CP->share_count[v] >= 2 ? 1 : 0);
+    }
+  for (int g = 0; g < CP->n_parts; ++g)
+    CB_CHECK(!CP->subs[g].nodes.empty(), CBDDC_EINVAL, "level-2 subdomain without coarse nodes");
+  classify_interface(nn, members, CP->share_count, eptr, eidx, nullptr, CP->vertices, CP->edges,
+                     CP->faces);
+  build_local_slots(CP, eptr, eidx, C->part2, cbase);
+  CP->n_elem_blocks = nb;
+  CP->contrib.alloc((size_t)std::max<int64_t>(nb, 1) * 9);
+  CP->status.alloc(4);
+  CB_CUDA(cudaMemset(CP->status.p, 0, CP->status.bytes()));
+  CP->has_tangent = true;
+  C->d_cbase.upload(cbase);
+}
+
 void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   CB_CHECK(opt != nullptr, CBDDC_EINVAL, "null options");
   CB_CHECK(opt->precision == CBDDC_FP64 || opt->precision == CBDDC_FP32, CBDDC_EINVAL, "bad precision");
@@ -595,6 +671,15 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   C->precision = opt->precision;
   C->primal = opt->primal;
   C->pivot_tol = opt->pivot_tol > 0 ? opt->pivot_tol : 1e-13;
+  C->levels = opt->levels >= 3 ? 3 : 2;
+  CB_CHECK(opt->levels <= 3, CBDDC_EINVAL, "at most three levels are supported");
+  if (C->levels == 3) {
+    CB_CHECK(opt->part2 != nullptr && opt->n_parts2 >= 1, CBDDC_EINVAL, "multilevel BDDC needs part2");
+    C->n_parts2 = opt->n_parts2;
+    C->primal2 = opt->primal2 ? opt->primal2 : (CBDDC_PRIMAL_V | CBDDC_PRIMAL_E | CBDDC_PRIMAL_F);
+    C->part2.assign(opt->part2, opt->part2 + P->n_parts);
+    for (int g : C->part2) CB_CHECK(g >= 0 && g < C->n_parts2, CBDDC_EINVAL, "part2 out of range");
+  }
   C->esize = opt->precision == CBDDC_FP32 ? 4 : 8;
   const int nsub = P->n_parts;
   C->nsub = nsub;
@@ -837,8 +922,9 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   C->gl_SPhi.set(gSP, es);
   C->gl_Kc.set(gKc, es, true);
 
-  // coarse matrix entries
-  if (C->n_pi > 0) {
+  C->gprim_h = gprim;
+  // coarse matrix entries (two-level: dense FP64 coarse inverse)
+  if (C->n_pi > 0 && C->levels == 2) {
     std::vector<std::pair<int64_t, int>> ckv;
     for (int s = 0; s < nsub; ++s)
       for (int i = 0; i < C->nc[s]; ++i)
@@ -919,8 +1005,23 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
           2.0 * nc * nc * ng;
     lb += (int64_t)((ni * ni + 2.0 * ni * ng + nr * nr + 2.0 * ng * nc) * C->esize);
   }
-  fl += 2.0 * (double)C->n_pi * C->n_pi * C->n_pi;
-  lb += (int64_t)C->n_pi * C->n_pi * 8;
+  // multilevel: coarse problem and its BDDC context
+  if (C->levels == 3 && C->n_pi > 0) {
+    C->coarse_prob.reset(new fem_problem);
+    build_coarse_problem(C, C->coarse_prob.get());
+    bddc_options o2{};
+    o2.precision = CBDDC_FP64;
+    o2.primal = C->primal2;
+    o2.pivot_tol = C->pivot_tol;
+    o2.levels = 2;
+    C->next.reset(new bddc_ctx);
+    bddc_create(C->coarse_prob.get(), &o2, C->next.get());
+    fl += C->next->setup_flops;
+    lb += C->next->local_bytes;
+  } else {
+    fl += 2.0 * (double)C->n_pi * C->n_pi * C->n_pi;
+    lb += (int64_t)C->n_pi * C->n_pi * 8;
+  }
   C->setup_flops = fl;
   C->local_bytes = lb;
   C->apply_flops = (double)lb / (double)C->esize * 2.0;
@@ -1018,6 +1119,18 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
   if (C->n_pi > 0) {
     launch_list<T, false, false>(C->gl_SPhi, Aloc, Phi, SPhi, T(1), T(0), s);
     launch_list<T, true, false>(C->gl_Kc, Phi, SPhi, Kc, T(1), T(0), s);
+    if (C->next) {
+      // multilevel: the local coarse matrices become the element matrices of
+      // the coarse problem, which the level-2 BDDC sets up in FP64
+      fem_problem* CP = C->coarse_prob.get();
+      kc_to_blocks_kernel<T><<<dim3(cdiv((int64_t)C->maxC * C->maxC, 256), nsub), 256, 0, s>>>(
+          C->d_nc.p, C->d_offKc.p, C->d_ldPhi.p, C->d_cbase.p, Kc, CP->contrib.p);
+      CB_LAUNCH();
+      bddc_run_setup(C->next.get(), s);
+      or_status_kernel<<<1, 1, 0, s>>>(CP->status.p, status);
+      CB_LAUNCH();
+      return;
+    }
     CB_CUDA(cudaMemsetAsync(C->Sc.p, 0, C->Sc.bytes(), s));
     if (sizeof(T) == 4)
       coarse_assemble_kernel_f<<<cdiv(C->n_ce, 256), 256, 0, s>>>(
@@ -1074,9 +1187,13 @@ static void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) 
       coarse_rhs_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, C->cl.p, nch,
                                                            C->rc.p);
       CB_LAUNCH();
-      dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, C->rc.p,
-                                                                         C->uc.p);
-      CB_LAUNCH();
+      if (C->next) {
+        bddc_run_apply(C->next.get(), C->rc.p, C->uc.p, s);
+      } else {
+        dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, C->rc.p,
+                                                                           C->uc.p);
+        CB_LAUNCH();
+      }
     }
     apply_prolong_kernel<T><<<dim3(cdiv(C->maxG, AROWS), nsub), 256, 0, s>>>(
         C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, C->gprim.p, Phi,
@@ -1170,8 +1287,13 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
       coarse_rhs_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, w.cl, nch,
                                                            w.rc);
       CB_LAUNCH();
-      dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, w.rc, w.uc);
-      CB_LAUNCH();
+      if (C->next) {
+        // the level-2 context uses its own work vectors, allocated at setup
+        bddc_run_apply(C->next.get(), w.rc, w.uc, s);
+      } else {
+        dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, w.rc, w.uc);
+        CB_LAUNCH();
+      }
     }
     apply_prolong_kernel<T><<<dim3(cdiv(C->maxG, AROWS), nsub), 256, 0, s>>>(
         C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, C->gprim.p, Phi,
@@ -1229,5 +1351,6 @@ int64_t bddc_ctx::device_bytes() const {
   return (int64_t)(Aloc.bytes() + Sw.bytes() + Phi.bytes() + Y.bytes() + Zf.bytes() + Wf.bytes() +
                    G.bytes() + SPhi.bytes() + Kc.bytes() + Xp.bytes() + Yp.bytes() + Pd.bytes() + Et.bytes() +
                    Sc.bytes() + ScX.bytes() + ScY.bytes() + ScP.bytes() + u0.bytes() + hG.bytes() +
-                   gI.bytes() + wG.bytes() + cl.bytes() + rc.bytes() + uc.bytes() + yG.bytes() + gl.bytes() + xI.bytes() + zl.bytes());
+                   gI.bytes() + wG.bytes() + cl.bytes() + rc.bytes() + uc.bytes() + yG.bytes() + gl.bytes() + xI.bytes() + zl.bytes()) +
+         (next ? next->device_bytes() + coarse_prob->device_bytes() : 0);
 }

@@ -1,5 +1,7 @@
 // BDDC context (internal).
 #pragma once
+#include <memory>
+
 #include "common.h"
 #include "dense.cuh"
 #include "krylov.h"
@@ -47,6 +49,13 @@ struct bddc_ctx {
   // Krylov and Newton workspaces (allocated on first use)
   cbddc::Gmres gm;
   cbddc::DVec<double> nw_r, nw_b, nw_delta, nw_d;
+  // multilevel: the coarse problem as an unassembled matrix and its BDDC
+  std::vector<int> gprim_h;
+  int levels = 2, n_parts2 = 0, primal2 = 0;
+  std::vector<int> part2;
+  std::unique_ptr<fem_problem> coarse_prob;
+  std::unique_ptr<bddc_ctx> next;
+  cbddc::DVec<int64_t> d_cbase;  // first coarse contribution block of each subdomain
   int64_t device_bytes() const;
 };
 

@@ -92,7 +92,14 @@ static void fill_tangent(fem_problem* P, fem_tangent* K) {
 
 static void ensure_ctx(fem_problem* P, const solve_options* opt, bddc_ctx** C) {
   if (*C) return;
-  bddc_options bo{opt->precision, opt->primal, opt->pivot_tol};
+  bddc_options bo{};
+  bo.precision = opt->precision;
+  bo.primal = opt->primal;
+  bo.pivot_tol = opt->pivot_tol;
+  bo.levels = opt->levels;
+  bo.n_parts2 = opt->n_parts2;
+  bo.part2 = opt->part2;
+  bo.primal2 = opt->primal2;
   bddc_ctx* c = new bddc_ctx;
   try {
     bddc_create(P, &bo, c);
@@ -286,8 +293,9 @@ int bddc_setup(fem_problem* P, const fem_tangent* K, const bddc_options* opt, bd
       *inout = c;
     } else {
       bddc_ctx* c = *inout;
-      CB_CHECK(c->P == P && c->precision == opt->precision && c->primal == opt->primal, CBDDC_EINVAL,
-               "context was created for another problem or options");
+      CB_CHECK(c->P == P && c->precision == opt->precision && c->primal == opt->primal &&
+                   c->levels == (opt->levels >= 3 ? 3 : 2),
+               CBDDC_EINVAL, "context was created for another problem or options");
     }
     bddc_run_setup(*inout, s);
     const int st = take_status(P, s);
@@ -317,6 +325,7 @@ int bddc_get_info(const bddc_ctx* C, bddc_info* info) {
   return guard([&] {
     CB_CHECK(C && info, CBDDC_EINVAL, "null argument");
     info->n_primal = C->n_pi;
+    info->n_primal2 = C->next ? C->next->n_pi : 0;
     info->precision = C->precision;
     info->local_bytes = C->local_bytes;
     info->device_bytes = C->device_bytes();

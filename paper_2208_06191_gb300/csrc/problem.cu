@@ -60,6 +60,130 @@ void hex_face_node_list(int k, int f, int* out) {
     }
 }
 
+// Interface classes of Section 3.2 from subdomain membership: interface
+// nodes (shared by >= 2 subdomains) are grouped by their sharing set and
+// split into connected pieces (two nodes are adjacent when an element holds
+// both).  A piece shared by 2 subdomains is a face; shared by 3 or more it
+// is an edge, except that single-node pieces are vertices and, when the
+// outer boundary is known (on_bnd != null), edge nodes on it are vertices
+// too (the subdomain corners on the surface).
+void classify_interface(int nn, const std::vector<std::vector<int>>& members,
+                        const std::vector<int>& share_count, const std::vector<int>& eptr,
+                        const std::vector<int>& eidx, const std::vector<char>* on_bnd,
+                        std::vector<int>& vertices, std::vector<std::vector<int>>& edges,
+                        std::vector<std::vector<int>>& faces) {
+  std::map<std::vector<int>, int> key_of;
+  std::vector<int> key(nn, -1);
+  for (int v = 0; v < nn; ++v)
+    if (share_count[v] >= 2) {
+      auto it = key_of.find(members[v]);
+      if (it == key_of.end()) it = key_of.emplace(members[v], (int)key_of.size()).first;
+      key[v] = it->second;
+    }
+  UnionFind uf(nn);
+  const int ne = (int)eptr.size() - 1;
+  for (int e = 0; e < ne; ++e) {
+    const int* en = &eidx[eptr[e]];
+    const int k = eptr[e + 1] - eptr[e];
+    for (int a = 0; a < k; ++a) {
+      if (key[en[a]] < 0) continue;
+      for (int b = a + 1; b < k; ++b)
+        if (key[en[b]] == key[en[a]]) uf.unite(en[a], en[b]);
+    }
+  }
+  std::map<int, std::vector<int>> classes;
+  for (int v = 0; v < nn; ++v)
+    if (key[v] >= 0) classes[uf.find(v)].push_back(v);
+  vertices.clear();
+  edges.clear();
+  faces.clear();
+  for (auto& kvp : classes) {
+    std::vector<int>& nodes = kvp.second;
+    std::sort(nodes.begin(), nodes.end());
+    const int s = (int)members[nodes[0]].size();
+    if (s == 2) {
+      faces.push_back(nodes);
+    } else if (nodes.size() == 1) {
+      vertices.push_back(nodes[0]);
+    } else {
+      std::vector<int> rest;
+      for (int v : nodes) {
+        if (on_bnd && (*on_bnd)[v]) vertices.push_back(v);
+        else rest.push_back(v);
+      }
+      if (!rest.empty()) edges.push_back(rest);
+    }
+  }
+  std::sort(vertices.begin(), vertices.end());
+  std::sort(edges.begin(), edges.end());
+  std::sort(faces.begin(), faces.end());
+}
+
+// Subdomain-local slot lists for the dense local matrices.  Contributor c
+// (an element, a face, or a finer subdomain at a coarse level) has nodes
+// cidx[cptr[c]..cptr[c+1]), belongs to subdomain cpart[c] and stores its
+// 3x3 blocks (a, b) at block index cbase[c] + a * k + b (k = its node count).
+// Nodes that are not in the subdomain's node list (Dirichlet nodes) are
+// skipped.  Every distinct (subdomain, local row node, local col node)
+// becomes one slot with the list of blocks summed into it.
+void build_local_slots(fem_problem* P, const std::vector<int>& cptr, const std::vector<int>& cidx,
+                       const std::vector<int>& cpart, const std::vector<int64_t>& cbase) {
+  const int np = P->n_parts;
+  std::vector<int64_t> base(np + 1, 0);
+  for (int p = 0; p < np; ++p) {
+    const int64_t nl = (int64_t)P->subs[p].nodes.size();
+    base[p + 1] = base[p] + nl * nl;
+  }
+  std::vector<std::pair<int64_t, int>> lkv;
+  std::vector<int> loc;
+  const int nc = (int)cpart.size();
+  for (int c = 0; c < nc; ++c) {
+    const int p = cpart[c];
+    const auto& nv = P->subs[p].nodes;
+    const int64_t nl = (int64_t)nv.size();
+    const int k = cptr[c + 1] - cptr[c];
+    loc.assign(k, -1);
+    for (int a = 0; a < k; ++a) {
+      const int v = cidx[cptr[c] + a];
+      auto it = std::lower_bound(nv.begin(), nv.end(), v);
+      if (it != nv.end() && *it == v) loc[a] = (int)(it - nv.begin());
+    }
+    for (int a = 0; a < k; ++a) {
+      if (loc[a] < 0) continue;
+      for (int b = 0; b < k; ++b)
+        if (loc[b] >= 0) {
+          const int64_t blk = cbase[c] + (int64_t)a * k + b;
+          CB_CHECK(blk < INT32_MAX, CBDDC_EINVAL, "too many contribution blocks for 32-bit indices");
+          lkv.push_back({base[p] + loc[a] * nl + loc[b], (int)blk});
+        }
+    }
+  }
+  std::sort(lkv.begin(), lkv.end());
+  std::vector<int> lsub, lrow, lcol, lptr, lsrc;
+  lptr.push_back(0);
+  int p = 0;
+  for (size_t i = 0; i < lkv.size();) {
+    size_t j = i;
+    while (j < lkv.size() && lkv[j].first == lkv[i].first) ++j;
+    const int64_t key = lkv[i].first;
+    while (key >= base[p + 1]) ++p;
+    const int64_t nl = (int64_t)P->subs[p].nodes.size();
+    const int64_t off = key - base[p];
+    lsub.push_back(p);
+    lrow.push_back((int)(off / nl));
+    lcol.push_back((int)(off % nl));
+    for (size_t q = i; q < j; ++q) lsrc.push_back(lkv[q].second);
+    lptr.push_back((int)lsrc.size());
+    i = j;
+  }
+  P->n_lslots = (int64_t)lsub.size();
+  P->lslot_sub.upload(lsub);
+  P->lslot_row.upload(lrow);
+  P->lslot_col.upload(lcol);
+  P->lslot_ptr.upload(lptr);
+  P->lslot_src.upload(lsrc);
+}
+
 void build_problem(const fem_problem_desc* d, fem_problem* P) {
   CB_CHECK(d != nullptr, CBDDC_EINVAL, "null description");
   CB_CHECK(d->elem_type == CBDDC_HEX_Q1 || d->elem_type == CBDDC_HEX_Q2, CBDDC_EINVAL,
@@ -218,23 +342,6 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
 
   // interface classification
   {
-    std::map<std::vector<int>, int> key_of;
-    std::vector<int> key(nn, -1);
-    for (int v = 0; v < nn; ++v)
-      if (P->share_count[v] >= 2) {
-        auto it = key_of.find(members[v]);
-        if (it == key_of.end()) it = key_of.emplace(members[v], (int)key_of.size()).first;
-        key[v] = it->second;
-      }
-    UnionFind uf(nn);
-    for (int e = 0; e < ne; ++e) {
-      const int* en = &P->elems_h[(size_t)e * nen];
-      for (int a = 0; a < nen; ++a) {
-        if (key[en[a]] < 0) continue;
-        for (int b = a + 1; b < nen; ++b)
-          if (key[en[b]] == key[en[a]]) uf.unite(en[a], en[b]);
-      }
-    }
     // outer boundary: element faces (by corner nodes) used by one element
     std::vector<char> on_bnd(nn, 0);
     {
@@ -269,99 +376,28 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
         i = j;
       }
     }
-    std::map<int, std::vector<int>> classes;
-    for (int v = 0; v < nn; ++v)
-      if (key[v] >= 0) classes[uf.find(v)].push_back(v);
-    P->vertices.clear(); P->edges.clear(); P->faces.clear();
-    for (auto& kvp : classes) {
-      std::vector<int>& nodes = kvp.second;
-      std::sort(nodes.begin(), nodes.end());
-      int s = (int)members[nodes[0]].size();
-      if (s == 2) {
-        P->faces.push_back(nodes);
-      } else if (nodes.size() == 1) {
-        P->vertices.push_back(nodes[0]);
-      } else {
-        std::vector<int> rest;
-        for (int v : nodes) {
-          if (on_bnd[v]) P->vertices.push_back(v);
-          else rest.push_back(v);
-        }
-        if (!rest.empty()) P->edges.push_back(rest);
-      }
-    }
-    std::sort(P->vertices.begin(), P->vertices.end());
-    std::sort(P->edges.begin(), P->edges.end());
-    std::sort(P->faces.begin(), P->faces.end());
+    std::vector<int> eptr(ne + 1), eidx(P->elems_h.begin(), P->elems_h.end());
+    for (int e = 0; e <= ne; ++e) eptr[e] = e * nen;
+    classify_interface(nn, members, P->share_count, eptr, eidx, &on_bnd, P->vertices, P->edges, P->faces);
   }
 
-  // subdomain-local slots: (sub, local row node, local col node) pairs
+  // subdomain-local slots: elements then pressure faces as contributors
   {
-    std::vector<int64_t> base(P->n_parts + 1, 0);
-    for (int p = 0; p < P->n_parts; ++p) {
-      int64_t nl = (int64_t)P->subs[p].nodes.size();
-      base[p + 1] = base[p] + nl * nl;
-    }
-    auto lidx = [&](int p, int v) -> int {
-      const auto& nv = P->subs[p].nodes;
-      return (int)(std::lower_bound(nv.begin(), nv.end(), v) - nv.begin());
-    };
-    std::vector<std::pair<int64_t, int>> lkv;
-    lkv.reserve(P->n_elem_blocks + P->n_face_blocks);
-    std::vector<int> loc(nen);
+    std::vector<int> cptr{0}, cidx, cpart;
+    std::vector<int64_t> cbase;
     for (int e = 0; e < ne; ++e) {
-      int p = P->part_h[e];
-      int64_t nl = (int64_t)P->subs[p].nodes.size();
-      for (int a = 0; a < nen; ++a) {
-        int v = P->elems_h[(size_t)e * nen + a];
-        loc[a] = is_dir[v] ? -1 : lidx(p, v);
-      }
-      for (int a = 0; a < nen; ++a) {
-        if (loc[a] < 0) continue;
-        for (int b = 0; b < nen; ++b)
-          if (loc[b] >= 0)
-            lkv.push_back({base[p] + loc[a] * nl + loc[b], (int)((int64_t)e * nen * nen + a * nen + b)});
-      }
+      for (int a = 0; a < nen; ++a) cidx.push_back(P->elems_h[(size_t)e * nen + a]);
+      cptr.push_back((int)cidx.size());
+      cpart.push_back(P->part_h[e]);
+      cbase.push_back((int64_t)e * nen * nen);
     }
     for (int f = 0; f < P->n_faces; ++f) {
-      int p = P->part_h[face_elem[f]];
-      int64_t nl = (int64_t)P->subs[p].nodes.size();
-      for (int a = 0; a < nfn; ++a) {
-        int v = face_nodes[(size_t)f * nfn + a];
-        loc[a] = is_dir[v] ? -1 : lidx(p, v);
-      }
-      for (int a = 0; a < nfn; ++a) {
-        if (loc[a] < 0) continue;
-        for (int b = 0; b < nfn; ++b)
-          if (loc[b] >= 0)
-            lkv.push_back({base[p] + loc[a] * nl + loc[b],
-                           (int)(P->n_elem_blocks + (int64_t)f * nfn * nfn + a * nfn + b)});
-      }
+      for (int a = 0; a < nfn; ++a) cidx.push_back(face_nodes[(size_t)f * nfn + a]);
+      cptr.push_back((int)cidx.size());
+      cpart.push_back(P->part_h[face_elem[f]]);
+      cbase.push_back(P->n_elem_blocks + (int64_t)f * nfn * nfn);
     }
-    std::sort(lkv.begin(), lkv.end());
-    std::vector<int> lsub, lrow, lcol, lptr, lsrc;
-    lptr.push_back(0);
-    int p = 0;
-    for (size_t i = 0; i < lkv.size();) {
-      size_t j = i;
-      while (j < lkv.size() && lkv[j].first == lkv[i].first) ++j;
-      int64_t key = lkv[i].first;
-      while (key >= base[p + 1]) ++p;
-      int64_t nl = (int64_t)P->subs[p].nodes.size();
-      int64_t off = key - base[p];
-      lsub.push_back(p);
-      lrow.push_back((int)(off / nl));
-      lcol.push_back((int)(off % nl));
-      for (size_t q = i; q < j; ++q) lsrc.push_back(lkv[q].second);
-      lptr.push_back((int)lsrc.size());
-      i = j;
-    }
-    P->n_lslots = (int64_t)lsub.size();
-    P->lslot_sub.upload(lsub);
-    P->lslot_row.upload(lrow);
-    P->lslot_col.upload(lcol);
-    P->lslot_ptr.upload(lptr);
-    P->lslot_src.upload(lsrc);
+    build_local_slots(P, cptr, cidx, cpart, cbase);
   }
 
   // uploads

@@ -251,3 +251,65 @@ def test_full_size_slab_residual_and_apply_sampled():
         pc.apply(_dev(-r_ref), z)
         z_ref = ref.apply(-r_ref)
         assert np.linalg.norm(_host(z) - z_ref) <= tol * np.linalg.norm(z_ref)
+
+
+# ------------------------------------------------------------- multilevel
+
+def _ml_pair(parts=(4, 4, 2), groups=(2, 2, 1), precision=None, primal="VE"):
+    from workloads import box_groups
+    prob = slab_problem(8, 8, 4, order=1, parts=parts, jitter=0.15, pressure=1e3, gamma=3e4)
+    fe = FEProblem(prob)
+    d = smooth_displacement(fe, seed=21)
+    K, (Ke, Kf) = fe.tangent(d, 0.8)
+    part2, n2 = box_groups(parts, groups)
+    ref = OracleBDDC(fe, Ke, Kf, primal, level2=dict(part=part2, n_parts=n2, primal="VEF"))
+    P = pkg.Problem(prob)
+    P.assemble_tangent(_dev(d), 0.8)
+    pc = pkg.BDDC(P, precision=precision if precision is not None else pkg.FP64, primal=primal,
+                  levels=3, part2=part2, n_parts2=n2, primal2="VEF").setup()
+    return fe, K, ref, P, pc
+
+
+@pytest.mark.parametrize("precision,tol", [(pkg.FP64, 1e-9), (pkg.FP32, 1e-3)])
+def test_multilevel_apply_parity(precision, tol):
+    fe, K, ref, P, pc = _ml_pair(precision=precision)
+    info = pc.info()
+    assert info["n_primal"] == ref.n_pi and info["n_primal2"] == ref.coarse.n_pi > 0
+    r = np.random.default_rng(31).standard_normal(fe.n_free)
+    z = torch.empty(fe.n_free, dtype=torch.float64, device="cuda")
+    pc.apply(_dev(r), z)
+    z_ref = ref.apply(r)
+    assert np.linalg.norm(_host(z) - z_ref) <= tol * np.linalg.norm(z_ref)
+
+
+def test_multilevel_with_one_group_equals_two_level_on_gpu():
+    from workloads import box_groups
+    prob = slab_problem(8, 8, 4, order=1, parts=(4, 4, 2), pressure=1e3, gamma=3e4)
+    fe = FEProblem(prob)
+    d = smooth_displacement(fe, seed=22)
+    P = pkg.Problem(prob)
+    P.assemble_tangent(_dev(d), 0.7)
+    part2, n2 = box_groups((4, 4, 2), (1, 1, 1))
+    two = pkg.BDDC(P, precision=pkg.FP64, primal="VE").setup()
+    ml = pkg.BDDC(P, precision=pkg.FP64, primal="VE", levels=3, part2=part2, n_parts2=n2).setup()
+    r = _dev(np.random.default_rng(32).standard_normal(fe.n_free))
+    z2 = torch.empty_like(r)
+    zm = torch.empty_like(r)
+    two.apply(r, z2)
+    ml.apply(r, zm)
+    torch.cuda.synchronize()
+    assert float(torch.linalg.vector_norm(zm - z2)) <= 1e-10 * float(torch.linalg.vector_norm(z2))
+
+
+def test_multilevel_newton_solve_fp32():
+    from workloads import box_groups
+    prob = slab_problem(8, 8, 8, order=1, parts=(4, 4, 4), pressure=1e3, gamma=3e4, load_steps=4)
+    P = pkg.Problem(prob)
+    part2, n2 = box_groups((4, 4, 4), (2, 2, 2))
+    d2, rep2 = P.solve(pkg.SolveOptions(precision=pkg.FP32, primal="VE"))
+    dm, repm = P.solve(pkg.SolveOptions(precision=pkg.FP32, primal="VE", levels=3, part2=part2,
+                                        n_parts2=n2, primal2="VEF"))
+    assert repm["status"] == 0 and repm["load_steps_done"] == 4
+    assert repm["final_rel_residual"] <= 1e-8
+    assert repm["total_gmres_its"] >= rep2["total_gmres_its"]
+    assert float(torch.linalg.vector_norm(dm - d2)) <= 1e-6 * float(torch.linalg.vector_norm(d2))
