@@ -38,8 +38,9 @@ class FEProblem:
         self.node_to_free[self.free_nodes] = np.arange(self.free_nodes.size)
         self.n_free = 3 * self.free_nodes.size
         # volume quadrature
-        pts, wts = el.hex_volume_rule(self.k)
-        N, dN = el.hex_shape(self.k, pts)
+        et = prob["elem_type"]
+        pts, wts = el.volume_rule(et)
+        N, dN = el.shape(et, pts)
         Xe = self.coords[self.elems]                       # (ne, nen, 3)
         J0 = np.einsum("eai,qaj->eqij", Xe, dN)           # dX_i/dxi_j
         self.detJ0 = np.linalg.det(J0)
@@ -49,16 +50,23 @@ class FEProblem:
         self.dNdX = np.einsum("qaj,eqji->eqai", dN, invJ0)
         self.wdet = wts[None, :] * self.detJ0
         Xq = np.einsum("qa,eai->eqi", N, Xe)
-        self.R = mat.fiber_frame(prob["fibers"], Xq)       # (ne, nq, 3, 3)
+        fib = prob["fibers"]
+        if fib["kind"] == "nodal":
+            # nodal directions interpolated to the quadrature points
+            fq = np.einsum("qa,eai->eqi", N, np.asarray(fib["f"], dtype=float)[self.elems])
+            nq = np.einsum("qa,eai->eqi", N, np.asarray(fib["n"], dtype=float)[self.elems])
+            self.R = mat.nodal_fiber_frame(fq, nq)
+        else:
+            self.R = mat.fiber_frame(fib, Xq)              # (ne, nq, 3, 3)
         # pressure faces: volume shape data at face quadrature points
         self.faces = []
         for e, f in np.asarray(prob["pressure_faces"], dtype=np.int64):
-            fp, fw, es, et = el.hex_face_rule(self.k, int(f))
-            Nf, dNf = el.hex_shape(self.k, fp)
+            fp, fw, es, et_ = el.face_rule(et, int(f))
+            Nf, dNf = el.shape(et, fp)
             J0f = np.einsum("ai,qaj->qij", Xe[e], dNf)
             dNdXf = np.einsum("qaj,qji->qai", dNf, np.linalg.inv(J0f))
             Xs = J0f @ es
-            Xt = J0f @ et
+            Xt = J0f @ et_
             Aref = np.cross(Xs, Xt)                        # N dA / (ds dt)
             self.faces.append((int(e), Nf, dNdXf, Aref, fw))
 

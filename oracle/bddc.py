@@ -38,40 +38,20 @@ import scipy.sparse.csgraph as csg
 import scipy.sparse.linalg as spla
 
 
-def hex_corner_faces(k):
-    """Corner-node local indices of the 6 faces of a hexahedron of order k
-    (used only to find the outer boundary)."""
-    m = k + 1
-
-    def idx(a, b, c):
-        return a + m * (b + m * c)
-    K = k
-    return [
-        [idx(0, 0, 0), idx(0, K, 0), idx(0, K, K), idx(0, 0, K)],
-        [idx(K, 0, 0), idx(K, K, 0), idx(K, K, K), idx(K, 0, K)],
-        [idx(0, 0, 0), idx(K, 0, 0), idx(K, 0, K), idx(0, 0, K)],
-        [idx(0, K, 0), idx(K, K, 0), idx(K, K, K), idx(0, K, K)],
-        [idx(0, 0, 0), idx(K, 0, 0), idx(K, K, 0), idx(0, K, 0)],
-        [idx(0, 0, K), idx(K, 0, K), idx(K, K, K), idx(0, K, K)],
-    ]
-
-
 def outer_boundary_nodes(fe):
     """Nodes lying on element faces that belong to one element only."""
-    from .elements import hex_face_nodes
-    k = fe.k
-    corners = hex_corner_faces(k)
+    from .elements import corner_faces, face_nodes
+    et = fe.prob["elem_type"]
     keys = {}
-    for f, cn in enumerate(corners):
+    for f, cn in enumerate(corner_faces(et)):
         fk = np.sort(fe.elems[:, cn], axis=1)
         for e in range(fe.n_el):
-            t = tuple(fk[e])
-            keys.setdefault(t, []).append((e, f))
+            keys.setdefault(tuple(fk[e]), []).append((e, f))
     on = np.zeros(fe.n_nodes, dtype=bool)
     for lst in keys.values():
         if len(lst) == 1:
             e, f = lst[0]
-            on[fe.elems[e, hex_face_nodes(k, f)]] = True
+            on[fe.elems[e, face_nodes(et, f)]] = True
     return on
 
 

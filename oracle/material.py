@@ -139,6 +139,18 @@ def slab_helix_frame(z, z0, z1, alpha0, alpha1):
     return R
 
 
+def nodal_fiber_frame(f, n):
+    """Fibre frame from interpolated nodal directions (the left-ventricle
+    workloads): f normalised, n made orthogonal to f by one Gram-Schmidt
+    step and normalised, s = n x f so that (f, s, n) is right-handed.
+    Returns R with columns f, s, n, shape (..., 3, 3)."""
+    f = f / np.linalg.norm(f, axis=-1, keepdims=True)
+    n = n - np.sum(n * f, axis=-1, keepdims=True) * f
+    n = n / np.linalg.norm(n, axis=-1, keepdims=True)
+    s = np.cross(n, f)
+    return np.stack([f, s, n], axis=-1)
+
+
 def fiber_frame(spec, X):
     """Fibre frame at reference points X (..., 3) from the analytic spec."""
     if spec["kind"] == "slab_helix":
