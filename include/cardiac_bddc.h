@@ -59,7 +59,10 @@ enum {
 /* Element types (Section 2, "Space discretization"). */
 enum {
   CBDDC_HEX_Q1 = 1, /* 8-node trilinear hexahedron, 2x2x2 Gauss points  */
-  CBDDC_HEX_Q2 = 2  /* 27-node triquadratic hexahedron, 3x3x3 points   */
+  CBDDC_HEX_Q2 = 2, /* 27-node triquadratic hexahedron, 3x3x3 points   */
+  CBDDC_TET_P1 = 3, /* 4-node linear tetrahedron, centroid rule         */
+  CBDDC_TET_P2 = 4  /* 10-node quadratic tetrahedron, 4-point rule of
+                       degree 2; faces: centroid / 3-point rule          */
 };
 
 /* Analytic fibre fields, evaluated at quadrature points. */
@@ -67,7 +70,12 @@ enum {
   /* f = (cos a, sin a, 0), s = (-sin a, cos a, 0), n = e_z, with
      a = p[2] + (p[3] - p[2]) (Z - p[0]) / (p[1] - p[0]) and Z the
      reference height; p = fiber_params. */
-  CBDDC_FIBER_SLAB_HELIX = 1
+  CBDDC_FIBER_SLAB_HELIX = 1,
+  /* Nodal directions fiber_nodal[node] = (f_x, f_y, f_z, n_x, n_y, n_z),
+     interpolated with the shape functions to each quadrature point; there
+     f is normalised, n is made orthogonal to f and normalised, and
+     s = n x f. */
+  CBDDC_FIBER_NODAL = 2
 };
 
 /*
@@ -77,9 +85,14 @@ enum {
  * Hexahedron local numbering is lexicographic: local node a+(k+1)(b+(k+1)c)
  * sits at reference point (-1+2a/k, -1+2b/k, -1+2c/k), k = element order.
  * Local faces: 0 = xi-, 1 = xi+, 2 = eta-, 3 = eta+, 4 = zeta-, 5 = zeta+.
+ *
+ * Tetrahedron: vertices 0..3 at (0,0,0), (1,0,0), (0,1,0), (0,0,1); P2 adds
+ * the midpoints of edges (0,1), (1,2), (0,2), (0,3), (1,3), (2,3) as local
+ * nodes 4..9.  Local face f is the face opposite vertex f.  Elements must
+ * be positively oriented (det of the reference Jacobian > 0).
  */
 typedef struct {
-  int elem_type;               /* CBDDC_HEX_Q1 or CBDDC_HEX_Q2              */
+  int elem_type;               /* CBDDC_HEX_* or CBDDC_TET_*                */
   int n_nodes;
   const double* coords;        /* [n_nodes][3] reference coordinates        */
   int n_elems;
@@ -98,6 +111,8 @@ typedef struct {
   double material[8];
   double pressure;             /* p at load factor 1 (Pa)                   */
   double gamma;                /* activation gamma at load factor 1 (Pa)    */
+  const double* fiber_nodal;   /* [n_nodes][6] for CBDDC_FIBER_NODAL, else
+                                  ignored (may be NULL)                     */
 } fem_problem_desc;
 
 typedef struct fem_problem fem_problem;

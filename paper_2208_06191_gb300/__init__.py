@@ -23,8 +23,8 @@ __all__ = [
 ]
 
 OK, EINVAL, ECUDA, EPIVOT, EINVERTED, ENOCONV, ETIMEOUT, ENOMEM = range(8)
-HEX_Q1, HEX_Q2 = 1, 2
-FIBER_SLAB_HELIX = 1
+HEX_Q1, HEX_Q2, TET_P1, TET_P2 = 1, 2, 3, 4
+FIBER_SLAB_HELIX, FIBER_NODAL = 1, 2
 FP64, FP32 = 0, 1
 PRIMAL_V, PRIMAL_E, PRIMAL_F = 1, 2, 4
 MAX_RECORDS = 512
@@ -66,7 +66,7 @@ class _Desc(ctypes.Structure):
         ("n_pressure_faces", ctypes.c_int), ("pressure_faces", _i32p),
         ("fiber_kind", ctypes.c_int), ("fiber_params", ctypes.c_double * 8),
         ("material", ctypes.c_double * 8), ("pressure", ctypes.c_double),
-        ("gamma", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("fiber_nodal", _dp),
     ]
 
 
@@ -279,9 +279,9 @@ class Problem:
 
         coords = np.ascontiguousarray(np.asarray(prob["coords"], dtype=np.float64))
         self._keep.append(coords)
-        et = {"Q1": HEX_Q1, "Q2": HEX_Q2}[prob["elem_type"]]
+        et = {"Q1": HEX_Q1, "Q2": HEX_Q2, "P1": TET_P1, "P2": TET_P2}[prob["elem_type"]]
         fib = prob["fibers"]
-        if fib["kind"] != "slab_helix":
+        if fib["kind"] not in ("slab_helix", "nodal"):
             raise ValueError("unsupported fibre field %r" % fib["kind"])
         mat = prob["material"]
         d = _Desc()
@@ -297,9 +297,18 @@ class Problem:
         pf = np.asarray(prob["pressure_faces"], dtype=np.int32).reshape(-1, 2)
         d.n_pressure_faces = pf.shape[0]
         d.pressure_faces = i32(pf)
-        d.fiber_kind = FIBER_SLAB_HELIX
-        for i, v in enumerate([fib["z0"], fib["z1"], fib["alpha0"], fib["alpha1"]]):
-            d.fiber_params[i] = float(v)
+        if fib["kind"] == "slab_helix":
+            d.fiber_kind = FIBER_SLAB_HELIX
+            for i, v in enumerate([fib["z0"], fib["z1"], fib["alpha0"], fib["alpha1"]]):
+                d.fiber_params[i] = float(v)
+        else:
+            d.fiber_kind = FIBER_NODAL
+            fn = np.ascontiguousarray(np.hstack([np.asarray(fib["f"], dtype=np.float64),
+                                                 np.asarray(fib["n"], dtype=np.float64)]))
+            if fn.shape != (coords.shape[0], 6):
+                raise ValueError("nodal fibres must have one (f, n) pair per node")
+            self._keep.append(fn)
+            d.fiber_nodal = fn.ctypes.data_as(_dp)
         for i, k in enumerate(["C", "bff", "bss", "bnn", "bfs", "bfn", "bsn", "B"]):
             d.material[i] = float(mat[k])
         d.pressure = float(prob["pressure"])

@@ -107,6 +107,7 @@ struct SubHost {
 struct fem_problem {
   // description
   int elem_type = 0, order = 1, n_en = 8, n_qp = 8, n_fn = 4, n_fqp = 4;
+  bool tet = false;                         // tetrahedra (else hexahedra)
   int n_nodes = 0, n_el = 0, n_parts = 0, n_faces = 0;
   int64_t n_free_nodes = 0, n_free = 0, nnzb = 0;
   int fiber_kind = 0;
@@ -123,6 +124,7 @@ struct fem_problem {
   std::vector<std::vector<int>> edges, faces;  // classes (node lists)
   // device data
   cbddc::DVec<double> coords;               // n_nodes*3
+  cbddc::DVec<double> fib_nodal;            // n_nodes*6 (f, n) for nodal fibres
   cbddc::DVec<int> elems;                   // n_el*n_en
   cbddc::DVec<int> face_nodes;              // n_faces*n_fn (outward order)
   cbddc::DVec<int> free_nodes;              // n_free_nodes -> node id

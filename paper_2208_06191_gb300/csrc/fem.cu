@@ -26,7 +26,108 @@ __constant__ double c_dL[2][3][3];
 __constant__ double c_w[2][3];
 __constant__ double c_x[2][3];
 
+// Tetrahedra (index o = order - 1): volume rule points q, shape values
+// c_tN[o][q][a] and reference gradients c_tdN[o][q][a][j]; triangle faces:
+// values c_fN[o][q][a] and parametric derivatives c_fds / c_fdt.
+__constant__ double c_tN[2][4][10];
+__constant__ double c_tdN[2][4][10][3];
+__constant__ double c_tw[2][4];
+__constant__ double c_fN[2][3][6];
+__constant__ double c_fds[2][3][6];
+__constant__ double c_fdt[2][3][6];
+__constant__ double c_fw[2][3];
+
+namespace {
+
+// P1/P2 shape functions of the reference tetrahedron at xi (barycentric
+// L0 = 1 - x - y - z, L1..3 = x, y, z; P2 vertices L(2L - 1), edge
+// midpoints 4 L_a L_b on edges (0,1), (1,2), (0,2), (0,3), (1,3), (2,3)).
+void tet_shape_host(int k, const double xi[3], double* N, double (*dN)[3]) {
+  const double L[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
+  const double dL[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  if (k == 1) {
+    for (int a = 0; a < 4; ++a) {
+      N[a] = L[a];
+      for (int j = 0; j < 3; ++j) dN[a][j] = dL[a][j];
+    }
+    return;
+  }
+  static const int ed[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
+  for (int a = 0; a < 4; ++a) {
+    N[a] = L[a] * (2.0 * L[a] - 1.0);
+    for (int j = 0; j < 3; ++j) dN[a][j] = (4.0 * L[a] - 1.0) * dL[a][j];
+  }
+  for (int m = 0; m < 6; ++m) {
+    const int a = ed[m][0], b = ed[m][1];
+    N[4 + m] = 4.0 * L[a] * L[b];
+    for (int j = 0; j < 3; ++j) dN[4 + m][j] = 4.0 * (L[b] * dL[a][j] + L[a] * dL[b][j]);
+  }
+}
+
+// P1/P2 shape functions of the reference triangle in the face parameters
+// (s, t): vertices (0,0), (1,0), (0,1), then midpoints of (0,1), (1,2), (0,2).
+void tri_shape_host(int k, double s, double t, double* N, double* ds, double* dt) {
+  const double L[3] = {1.0 - s - t, s, t};
+  const double dLs[3] = {-1, 1, 0}, dLt[3] = {-1, 0, 1};
+  if (k == 1) {
+    for (int a = 0; a < 3; ++a) { N[a] = L[a]; ds[a] = dLs[a]; dt[a] = dLt[a]; }
+    return;
+  }
+  static const int ed[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+  for (int a = 0; a < 3; ++a) {
+    N[a] = L[a] * (2.0 * L[a] - 1.0);
+    ds[a] = (4.0 * L[a] - 1.0) * dLs[a];
+    dt[a] = (4.0 * L[a] - 1.0) * dLt[a];
+  }
+  for (int m = 0; m < 3; ++m) {
+    const int a = ed[m][0], b = ed[m][1];
+    N[3 + m] = 4.0 * L[a] * L[b];
+    ds[3 + m] = 4.0 * (L[b] * dLs[a] + L[a] * dLs[b]);
+    dt[3 + m] = 4.0 * (L[b] * dLt[a] + L[a] * dLt[b]);
+  }
+}
+
+void init_tet_tables() {
+  double tN[2][4][10] = {}, tdN[2][4][10][3] = {}, tw[2][4] = {};
+  double fN[2][3][6] = {}, fds[2][3][6] = {}, fdt[2][3][6] = {}, fw[2][3] = {};
+  // P1: centroid, weight 1/6 (volume of the reference tetrahedron)
+  {
+    const double xi[3] = {0.25, 0.25, 0.25};
+    tet_shape_host(1, xi, tN[0][0], tdN[0][0]);
+    tw[0][0] = 1.0 / 6.0;
+  }
+  // P2: symmetric 4-point rule of degree 2, barycentric (a, b, b, b)
+  {
+    const double a = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, b = (5.0 - std::sqrt(5.0)) / 20.0;
+    for (int q = 0; q < 4; ++q) {
+      double bary[4] = {b, b, b, b};
+      bary[q] = a;
+      const double xi[3] = {bary[1], bary[2], bary[3]};
+      tet_shape_host(2, xi, tN[1][q], tdN[1][q]);
+      tw[1][q] = 1.0 / 24.0;
+    }
+  }
+  // triangle rules: centroid (weight 1/2) and the 3-point rule of degree 2
+  tri_shape_host(1, 1.0 / 3.0, 1.0 / 3.0, fN[0][0], fds[0][0], fdt[0][0]);
+  fw[0][0] = 0.5;
+  const double st[3][2] = {{1.0 / 6.0, 1.0 / 6.0}, {2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}};
+  for (int q = 0; q < 3; ++q) {
+    tri_shape_host(2, st[q][0], st[q][1], fN[1][q], fds[1][q], fdt[1][q]);
+    fw[1][q] = 1.0 / 6.0;
+  }
+  CB_CUDA(cudaMemcpyToSymbol(c_tN, tN, sizeof(tN)));
+  CB_CUDA(cudaMemcpyToSymbol(c_tdN, tdN, sizeof(tdN)));
+  CB_CUDA(cudaMemcpyToSymbol(c_tw, tw, sizeof(tw)));
+  CB_CUDA(cudaMemcpyToSymbol(c_fN, fN, sizeof(fN)));
+  CB_CUDA(cudaMemcpyToSymbol(c_fds, fds, sizeof(fds)));
+  CB_CUDA(cudaMemcpyToSymbol(c_fdt, fdt, sizeof(fdt)));
+  CB_CUDA(cudaMemcpyToSymbol(c_fw, fw, sizeof(fw)));
+}
+
+}  // namespace
+
 void init_shape_tables(int /*order*/) {
+  init_tet_tables();
   double L[2][3][3] = {}, dL[2][3][3] = {}, w[2][3] = {}, x[2][3] = {};
   for (int o = 1; o <= 2; ++o) {
     const int m = o + 1;
@@ -66,6 +167,7 @@ struct MatParams {
   double C, W[3][3], B;
   double fz0, fz1, fa0, fa1;  // slab helix fibre field
   double gamma, pressure;
+  int nodal;                  // fibres from interpolated nodal (f, n)
 };
 
 __device__ inline double det3(const double A[3][3]) {
@@ -101,6 +203,19 @@ __device__ inline void fibre_frame(const MatParams& m, const double X[3], double
   R[0][0] = c;   R[0][1] = -s;  R[0][2] = 0.0;
   R[1][0] = s;   R[1][1] = c;   R[1][2] = 0.0;
   R[2][0] = 0.0; R[2][1] = 0.0; R[2][2] = 1.0;
+}
+
+// Fibre frame from interpolated nodal directions: f normalised, n made
+// orthogonal to f and normalised, s = n x f; columns (f, s, n).
+__device__ inline void frame_from_fn(const double fv[3], const double nv[3], double R[3][3]) {
+  const double fl = 1.0 / sqrt(fv[0] * fv[0] + fv[1] * fv[1] + fv[2] * fv[2]);
+  const double f[3] = {fv[0] * fl, fv[1] * fl, fv[2] * fl};
+  const double nf = nv[0] * f[0] + nv[1] * f[1] + nv[2] * f[2];
+  double n[3] = {nv[0] - nf * f[0], nv[1] - nf * f[1], nv[2] - nf * f[2]};
+  const double nl = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  n[0] *= nl; n[1] *= nl; n[2] *= nl;
+  const double sv[3] = {n[1] * f[2] - n[2] * f[1], n[2] * f[0] - n[0] * f[2], n[0] * f[1] - n[1] * f[0]};
+  for (int i = 0; i < 3; ++i) { R[i][0] = f[i]; R[i][1] = sv[i]; R[i][2] = n[i]; }
 }
 
 // Stress P (row-major 3x3) and, if A != nullptr, the tangent
@@ -213,7 +328,8 @@ __global__ void scatter_free_kernel(const double* __restrict__ d, const int* __r
 template <int K, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 element_kernel(MatParams mp, const double* __restrict__ coords, const int* __restrict__ elems,
-               const double* __restrict__ d_full, double* __restrict__ rcontrib,
+               const double* __restrict__ fib, const double* __restrict__ d_full,
+               double* __restrict__ rcontrib,
                double* __restrict__ contrib, int* __restrict__ status, int want_tangent) {
   constexpr int M = K + 1, NEN = M * M * M, NQ = NEN;
   constexpr int O = K - 1;
@@ -238,7 +354,7 @@ element_kernel(MatParams mp, const double* __restrict__ coords, const int* __res
   for (int q = tid; q < NQ; q += THREADS) {
     const int qx = q % M, qy = (q / M) % M, qz = q / (M * M);
     double J0[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    double Xq[3] = {0, 0, 0};
+    double Xq[3] = {0, 0, 0}, fq[3] = {0, 0, 0}, nq[3] = {0, 0, 0};
     for (int a = 0; a < NEN; ++a) {
       const int ax = a % M, ay = (a / M) % M, az = a / (M * M);
       const double lx = c_L[O][qx][ax], ly = c_L[O][qy][ay], lz = c_L[O][qz][az];
@@ -248,6 +364,10 @@ element_kernel(MatParams mp, const double* __restrict__ coords, const int* __res
       for (int i = 0; i < 3; ++i) {
         Xq[i] += n * X[a][i];
         for (int j = 0; j < 3; ++j) J0[i][j] += X[a][i] * dn[j];
+      }
+      if (mp.nodal) {
+        const double* fa = fib + (int64_t)elems[(int64_t)e * NEN + a] * 6;
+        for (int i = 0; i < 3; ++i) { fq[i] += n * fa[i]; nq[i] += n * fa[3 + i]; }
       }
       G[q][a][0] = dn[0];
       G[q][a][1] = dn[1];
@@ -268,7 +388,8 @@ element_kernel(MatParams mp, const double* __restrict__ coords, const int* __res
         for (int j = 0; j < 3; ++j) F[i][j] += U[a][i] * gx[j];
     }
     double R[3][3];
-    fibre_frame(mp, Xq, R);
+    if (mp.nodal) frame_from_fn(fq, nq, R);
+    else fibre_frame(mp, Xq, R);
     if (!(det0 > 0.0) || !material_point(mp, F, R, Pq[q], want_tangent ? Aq[q] : nullptr)) {
       bad = 1;
       for (int i = 0; i < 9; ++i) Pq[q][i] = 0.0;
@@ -319,6 +440,178 @@ element_kernel(MatParams mp, const double* __restrict__ coords, const int* __res
   for (int j = 0; j < PER; ++j) {
     const int t = tid + j * THREADS;
     if (t < NE) contrib[(int64_t)e * NE + t] = acc[j];
+  }
+}
+
+
+// Tetrahedra, TET_THREADS material points per CTA (EPB = TET_THREADS / NQ
+// elements).  Phase 1: one thread per quadrature point computes the
+// geometry, F, the fibre frame and the material point, and stores
+// w detJ0 P and w detJ0 dP/dF in shared memory (stride 81 per point keeps
+// the 8-byte accesses conflict-free).  Phase 2: one thread per residual
+// entry (e, a, i).  Phase 3: one thread per (e, a, i, k) row of the element
+// matrix, K[a][b][i][k] = sum_q sum_L (sum_J G_aJ A_iJkL) G_bL for all b.
+constexpr int TET_THREADS = 32;
+
+template <int K>
+__global__ void __launch_bounds__(TET_THREADS)
+tet_element_kernel(MatParams mp, const double* __restrict__ coords, const int* __restrict__ elems,
+                   const double* __restrict__ fib, const double* __restrict__ d_full,
+                   double* __restrict__ rcontrib, double* __restrict__ contrib,
+                   int* __restrict__ status, int want_tangent, int n_el) {
+  constexpr int NEN = K == 1 ? 4 : 10, NQ = K == 1 ? 1 : 4, O = K - 1;
+  constexpr int EPB = TET_THREADS / NQ;
+  __shared__ double As[TET_THREADS * 81];
+  __shared__ double Ps[TET_THREADS * 9];
+  __shared__ double Gs[TET_THREADS][NEN][3];
+  __shared__ double Xs[EPB][NEN][3], Us[EPB][NEN][3];
+  __shared__ int Ns[EPB][NEN];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int ne_here = (int)min((int64_t)EPB, (int64_t)n_el - e0);
+  if (tid == 0) bad = 0;
+  for (int t = tid; t < ne_here * NEN; t += TET_THREADS) Ns[t / NEN][t % NEN] = elems[e0 * NEN + t];
+  __syncthreads();
+  for (int t = tid; t < ne_here * NEN * 3; t += TET_THREADS) {
+    const int el = t / (NEN * 3), a = (t / 3) % NEN, c = t % 3;
+    const int node = Ns[el][a];
+    Xs[el][a][c] = coords[(int64_t)node * 3 + c];
+    Us[el][a][c] = d_full[(int64_t)node * 3 + c];
+  }
+  __syncthreads();
+  {
+    const int p = tid, el = p / NQ, q = p % NQ;
+    double* A = &As[p * 81];
+    double* P = &Ps[p * 9];
+    bool ok = el < ne_here;
+    if (ok) {
+      double J0[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      double fq[3] = {0, 0, 0}, nq[3] = {0, 0, 0}, Xq[3] = {0, 0, 0};
+      for (int a = 0; a < NEN; ++a) {
+        const double n = c_tN[O][q][a];
+        for (int i = 0; i < 3; ++i) {
+          Xq[i] += n * Xs[el][a][i];
+          for (int j = 0; j < 3; ++j) J0[i][j] += Xs[el][a][i] * c_tdN[O][q][a][j];
+        }
+        if (mp.nodal) {
+          const double* fa = fib + (int64_t)Ns[el][a] * 6;
+          for (int i = 0; i < 3; ++i) { fq[i] += n * fa[i]; nq[i] += n * fa[3 + i]; }
+        }
+      }
+      double J0i[3][3];
+      const double det0 = inv3(J0, J0i);
+      double F[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+      for (int a = 0; a < NEN; ++a) {
+        double gx[3];
+        for (int i = 0; i < 3; ++i)
+          gx[i] = c_tdN[O][q][a][0] * J0i[0][i] + c_tdN[O][q][a][1] * J0i[1][i] +
+                  c_tdN[O][q][a][2] * J0i[2][i];
+        for (int i = 0; i < 3; ++i) {
+          Gs[p][a][i] = gx[i];
+          for (int j = 0; j < 3; ++j) F[i][j] += Us[el][a][i] * gx[j];
+        }
+      }
+      double R[3][3];
+      if (mp.nodal) frame_from_fn(fq, nq, R);
+      else fibre_frame(mp, Xq, R);
+      ok = det0 > 0.0 && material_point(mp, F, R, P, want_tangent ? A : nullptr);
+      if (ok) {
+        const double wd = c_tw[O][q] * det0;
+        for (int i = 0; i < 9; ++i) P[i] *= wd;
+        if (want_tangent)
+          for (int i = 0; i < 81; ++i) A[i] *= wd;
+      } else {
+        bad = 1;
+      }
+    }
+    if (!ok) {
+      for (int i = 0; i < 9; ++i) P[i] = 0.0;
+      for (int i = 0; i < 81; ++i) A[i] = 0.0;
+      for (int a = 0; a < NEN; ++a) Gs[p][a][0] = Gs[p][a][1] = Gs[p][a][2] = 0.0;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && bad) atomicOr(status, DEV_INVERTED);
+  for (int t = tid; t < ne_here * NEN * 3; t += TET_THREADS) {
+    const int el = t / (NEN * 3), a = (t / 3) % NEN, i = t % 3;
+    double r = 0.0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int p = el * NQ + q;
+      r += Ps[p * 9 + i * 3 + 0] * Gs[p][a][0] + Ps[p * 9 + i * 3 + 1] * Gs[p][a][1] +
+           Ps[p * 9 + i * 3 + 2] * Gs[p][a][2];
+    }
+    rcontrib[((e0 + el) * NEN + a) * 3 + i] = r;
+  }
+  if (!want_tangent) return;
+  for (int t = tid; t < ne_here * NEN * 9; t += TET_THREADS) {
+    const int el = t / (NEN * 9), a = (t / 9) % NEN, i = (t % 9) / 3, k = t % 3;
+    double acc[NEN];
+#pragma unroll
+    for (int b = 0; b < NEN; ++b) acc[b] = 0.0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int p = el * NQ + q;
+      const double* A = &As[p * 81 + i * 27 + k * 3];
+      const double g0 = Gs[p][a][0], g1 = Gs[p][a][1], g2 = Gs[p][a][2];
+      const double T0 = g0 * A[0] + g1 * A[9] + g2 * A[18];
+      const double T1 = g0 * A[1] + g1 * A[10] + g2 * A[19];
+      const double T2 = g0 * A[2] + g1 * A[11] + g2 * A[20];
+#pragma unroll
+      for (int b = 0; b < NEN; ++b) acc[b] += T0 * Gs[p][b][0] + T1 * Gs[p][b][1] + T2 * Gs[p][b][2];
+    }
+    double* out = contrib + ((e0 + el) * NEN * NEN + (int64_t)a * NEN) * 9 + i * 3 + k;
+#pragma unroll
+    for (int b = 0; b < NEN; ++b) out[b * 9] = acc[b];
+  }
+}
+
+// Follower pressure on one triangular face per CTA (same integrand as the
+// quadrilateral faces, with the triangle rules).
+template <int K, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+tri_face_kernel(double pressure, const double* __restrict__ coords, const int* __restrict__ face_nodes,
+                const double* __restrict__ d_full, double* __restrict__ rcontrib,
+                double* __restrict__ contrib, int want_tangent) {
+  constexpr int NFN = K == 1 ? 3 : 6, NQ = K == 1 ? 1 : 3, O = K - 1;
+  __shared__ double x[NFN][3];
+  __shared__ double xs[NQ][3], xt[NQ][3];
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < NFN * 3; t += THREADS) {
+    int a = t / 3, c = t % 3;
+    int node = face_nodes[(int64_t)f * NFN + a];
+    x[a][c] = coords[(int64_t)node * 3 + c] + d_full[(int64_t)node * 3 + c];
+  }
+  __syncthreads();
+  for (int q = tid; q < NQ; q += THREADS) {
+    double s[3] = {0, 0, 0}, t3[3] = {0, 0, 0};
+    for (int a = 0; a < NFN; ++a)
+      for (int i = 0; i < 3; ++i) { s[i] += c_fds[O][q][a] * x[a][i]; t3[i] += c_fdt[O][q][a] * x[a][i]; }
+    for (int i = 0; i < 3; ++i) { xs[q][i] = s[i]; xt[q][i] = t3[i]; }
+  }
+  __syncthreads();
+  for (int t = tid; t < NFN * 3; t += THREADS) {
+    const int a = t / 3, i = t % 3;
+    const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+    double r = 0.0;
+    for (int q = 0; q < NQ; ++q)
+      r += c_fw[O][q] * c_fN[O][q][a] * (xs[q][i1] * xt[q][i2] - xs[q][i2] * xt[q][i1]);
+    rcontrib[((int64_t)f * NFN + a) * 3 + i] = pressure * r;
+  }
+  if (!want_tangent) return;
+  constexpr int NE = NFN * NFN * 9;
+  for (int t = tid; t < NE; t += THREADS) {
+    const int a = t / (NFN * 9), b = (t / 9) % NFN, i = (t % 9) / 3, k = t % 3;
+    double v = 0.0;
+    if (i != k) {
+      const int l = 3 - i - k;
+      const double eps = ((k - i + 3) % 3 == 1) ? 1.0 : -1.0;  // eps_ikl
+      for (int q = 0; q < NQ; ++q)
+        v += c_fw[O][q] * c_fN[O][q][a] * (c_fds[O][q][b] * eps * xt[q][l] - c_fdt[O][q][b] * eps * xs[q][l]);
+    }
+    contrib[(int64_t)f * NE + t] = pressure * v;
   }
 }
 
@@ -427,6 +720,7 @@ MatParams make_params(const fem_problem* P, double lam) {
   m.fz0 = P->fiber[0]; m.fz1 = P->fiber[1]; m.fa0 = P->fiber[2]; m.fa1 = P->fiber[3];
   m.gamma = lam * P->gamma;
   m.pressure = lam * P->pressure;
+  m.nodal = P->fiber_kind == CBDDC_FIBER_NODAL ? 1 : 0;
   return m;
 }
 
@@ -440,12 +734,25 @@ void assemble(fem_problem* P, const double* d, double lam, double* residual, boo
   double* fr = P->rcontrib.p + P->n_elem_vec * 3;
   const int wt = want_tangent ? 1 : 0;
   timer_begin(CBDDC_TIMER_ELEMENT, s);
-  if (P->order == 1)
-    element_kernel<1, 64><<<P->n_el, 64, 0, s>>>(mp, P->coords.p, P->elems.p, P->d_full.p,
+  const double* fib = P->fib_nodal.p;
+  if (P->tet) {
+    const int epb = TET_THREADS / P->n_qp;
+    const int grid = (int)cdiv(P->n_el, epb);
+    if (P->order == 1)
+      tet_element_kernel<1><<<grid, TET_THREADS, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
+                                                         P->rcontrib.p, P->contrib.p, P->status.p, wt,
+                                                         P->n_el);
+    else
+      tet_element_kernel<2><<<grid, TET_THREADS, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
+                                                         P->rcontrib.p, P->contrib.p, P->status.p, wt,
+                                                         P->n_el);
+  } else if (P->order == 1) {
+    element_kernel<1, 64><<<P->n_el, 64, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
                                                   P->rcontrib.p, P->contrib.p, P->status.p, wt);
-  else
-    element_kernel<2, 256><<<P->n_el, 256, 0, s>>>(mp, P->coords.p, P->elems.p, P->d_full.p,
+  } else {
+    element_kernel<2, 256><<<P->n_el, 256, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
                                                     P->rcontrib.p, P->contrib.p, P->status.p, wt);
+  }
   CB_LAUNCH();
   {
     // algorithmic work of the element kernel: the two-stage contraction
@@ -456,7 +763,15 @@ void assemble(fem_problem* P, const double* d, double lam, double* residual, boo
     const double by = 8.0 * P->n_el * (want_tangent ? ne * ne * 9.0 : 0.0) + 8.0 * P->n_el * ne * 3.0;
     timer_end(CBDDC_TIMER_ELEMENT, s, fl, by);
   }
-  if (P->n_faces) {
+  if (P->n_faces && P->tet) {
+    if (P->order == 1)
+      tri_face_kernel<1, 32><<<P->n_faces, 32, 0, s>>>(mp.pressure, P->coords.p, P->face_nodes.p,
+                                                       P->d_full.p, fr, fc, wt);
+    else
+      tri_face_kernel<2, 64><<<P->n_faces, 64, 0, s>>>(mp.pressure, P->coords.p, P->face_nodes.p,
+                                                       P->d_full.p, fr, fc, wt);
+    CB_LAUNCH();
+  } else if (P->n_faces) {
     if (P->order == 1)
       face_kernel<1, 64><<<P->n_faces, 64, 0, s>>>(mp.pressure, P->coords.p, P->face_nodes.p,
                                                     P->d_full.p, fr, fc, wt);

@@ -60,6 +60,28 @@ void hex_face_node_list(int k, int f, int* out) {
     }
 }
 
+// Local node indices of face f (opposite vertex f) of a tetrahedron of
+// order k: the three vertices (o, s-end, t-end) with (x_s - x_o) x
+// (x_t - x_o) pointing out of the element, then for P2 the midpoints of
+// (o, s-end), (s-end, t-end), (o, t-end).
+void tet_face_node_list(int k, int f, int* out) {
+  static const int ost[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+  static const int edge_of[4][4] = {{-1, 4, 6, 7}, {4, -1, 5, 8}, {6, 5, -1, 9}, {7, 8, 9, -1}};
+  const int o = ost[f][0], a = ost[f][1], b = ost[f][2];
+  out[0] = o; out[1] = a; out[2] = b;
+  if (k == 2) {
+    out[3] = edge_of[o][a];
+    out[4] = edge_of[a][b];
+    out[5] = edge_of[o][b];
+  }
+}
+
+// Face node list of either element family.
+void face_node_list(bool tet, int k, int f, int* out) {
+  if (tet) tet_face_node_list(k, f, out);
+  else hex_face_node_list(k, f, out);
+}
+
 // Interface classes of Section 3.2 from subdomain membership: interface
 // nodes (shared by >= 2 subdomains) are grouped by their sharing set and
 // split into connected pieces (two nodes are adjacent when an element holds
@@ -186,20 +208,34 @@ void build_local_slots(fem_problem* P, const std::vector<int>& cptr, const std::
 
 void build_problem(const fem_problem_desc* d, fem_problem* P) {
   CB_CHECK(d != nullptr, CBDDC_EINVAL, "null description");
-  CB_CHECK(d->elem_type == CBDDC_HEX_Q1 || d->elem_type == CBDDC_HEX_Q2, CBDDC_EINVAL,
+  CB_CHECK(d->elem_type >= CBDDC_HEX_Q1 && d->elem_type <= CBDDC_TET_P2, CBDDC_EINVAL,
            "unsupported element type");
   CB_CHECK(d->n_nodes > 0 && d->n_elems > 0 && d->coords && d->elems && d->elem_part,
            CBDDC_EINVAL, "empty mesh");
   CB_CHECK(d->n_parts >= 1, CBDDC_EINVAL, "n_parts must be >= 1");
-  CB_CHECK(d->fiber_kind == CBDDC_FIBER_SLAB_HELIX, CBDDC_EINVAL, "unsupported fibre kind");
-  CB_CHECK(d->fiber_params[1] != d->fiber_params[0], CBDDC_EINVAL, "degenerate fibre range");
+  CB_CHECK(d->fiber_kind == CBDDC_FIBER_SLAB_HELIX || d->fiber_kind == CBDDC_FIBER_NODAL,
+           CBDDC_EINVAL, "unsupported fibre kind");
+  if (d->fiber_kind == CBDDC_FIBER_SLAB_HELIX)
+    CB_CHECK(d->fiber_params[1] != d->fiber_params[0], CBDDC_EINVAL, "degenerate fibre range");
+  else
+    CB_CHECK(d->fiber_nodal != nullptr, CBDDC_EINVAL, "nodal fibre field missing");
   P->elem_type = d->elem_type;
-  P->order = d->elem_type == CBDDC_HEX_Q1 ? 1 : 2;
+  P->tet = d->elem_type == CBDDC_TET_P1 || d->elem_type == CBDDC_TET_P2;
+  P->order = (d->elem_type == CBDDC_HEX_Q1 || d->elem_type == CBDDC_TET_P1) ? 1 : 2;
   const int k = P->order, m = k + 1;
-  P->n_en = m * m * m;
-  P->n_qp = P->n_en;   // (k+1)^3 Gauss points
-  P->n_fn = m * m;
-  P->n_fqp = m * m;
+  const bool tet = P->tet;
+  if (tet) {
+    P->n_en = k == 1 ? 4 : 10;
+    P->n_qp = k == 1 ? 1 : 4;
+    P->n_fn = k == 1 ? 3 : 6;
+    P->n_fqp = k == 1 ? 1 : 3;
+  } else {
+    P->n_en = m * m * m;
+    P->n_qp = P->n_en;   // (k+1)^3 Gauss points
+    P->n_fn = m * m;
+    P->n_fqp = m * m;
+  }
+  const int n_lfaces = tet ? 4 : 6;
   P->n_nodes = d->n_nodes;
   P->n_el = d->n_elems;
   P->n_parts = d->n_parts;
@@ -238,9 +274,9 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
   std::vector<int> face_elem(P->n_faces);
   for (int f = 0; f < P->n_faces; ++f) {
     int e = d->pressure_faces[2 * f], lf = d->pressure_faces[2 * f + 1];
-    CB_CHECK(e >= 0 && e < ne && lf >= 0 && lf < 6, CBDDC_EINVAL, "bad pressure face");
+    CB_CHECK(e >= 0 && e < ne && lf >= 0 && lf < n_lfaces, CBDDC_EINVAL, "bad pressure face");
     int loc[9];
-    hex_face_node_list(k, lf, loc);
+    face_node_list(tet, k, lf, loc);
     for (int a = 0; a < nfn; ++a) face_nodes[(size_t)f * nfn + a] = P->elems_h[(size_t)e * nen + loc[a]];
     face_elem[f] = e;
   }
@@ -346,31 +382,36 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
     std::vector<char> on_bnd(nn, 0);
     {
       std::vector<std::pair<std::array<int, 4>, int64_t>> fk;
-      fk.reserve((size_t)ne * 6);
+      fk.reserve((size_t)ne * n_lfaces);
       const int c0 = 0, cK = k;
       auto idx = [m](int a, int b, int c) { return a + m * (b + m * c); };
-      const int corner[6][4] = {
+      const int hcorner[6][4] = {
           {idx(c0, c0, c0), idx(c0, cK, c0), idx(c0, cK, cK), idx(c0, c0, cK)},
           {idx(cK, c0, c0), idx(cK, cK, c0), idx(cK, cK, cK), idx(cK, c0, cK)},
           {idx(c0, c0, c0), idx(cK, c0, c0), idx(cK, c0, cK), idx(c0, c0, cK)},
           {idx(c0, cK, c0), idx(cK, cK, c0), idx(cK, cK, cK), idx(c0, cK, cK)},
           {idx(c0, c0, c0), idx(cK, c0, c0), idx(cK, cK, c0), idx(c0, cK, c0)},
           {idx(c0, c0, cK), idx(cK, c0, cK), idx(cK, cK, cK), idx(c0, cK, cK)}};
+      // tetrahedron face f: the three vertices other than f (4th key -1)
+      const int tcorner[4][4] = {{1, 2, 3, -1}, {0, 2, 3, -1}, {0, 1, 3, -1}, {0, 1, 2, -1}};
       for (int e = 0; e < ne; ++e)
-        for (int f = 0; f < 6; ++f) {
+        for (int f = 0; f < n_lfaces; ++f) {
           std::array<int, 4> c;
-          for (int q = 0; q < 4; ++q) c[q] = P->elems_h[(size_t)e * nen + corner[f][q]];
+          for (int q = 0; q < 4; ++q) {
+            const int lc = tet ? tcorner[f][q] : hcorner[f][q];
+            c[q] = lc < 0 ? -1 : P->elems_h[(size_t)e * nen + lc];
+          }
           std::sort(c.begin(), c.end());
-          fk.push_back({c, (int64_t)e * 6 + f});
+          fk.push_back({c, (int64_t)e * n_lfaces + f});
         }
       std::sort(fk.begin(), fk.end());
       for (size_t i = 0; i < fk.size();) {
         size_t j = i;
         while (j < fk.size() && fk[j].first == fk[i].first) ++j;
         if (j - i == 1) {
-          int e = (int)(fk[i].second / 6), f = (int)(fk[i].second % 6);
+          int e = (int)(fk[i].second / n_lfaces), f = (int)(fk[i].second % n_lfaces);
           int loc[9];
-          hex_face_node_list(k, f, loc);
+          face_node_list(tet, k, f, loc);
           for (int a = 0; a < nfn; ++a) on_bnd[P->elems_h[(size_t)e * nen + loc[a]]] = 1;
         }
         i = j;
@@ -403,6 +444,15 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
   // uploads
   std::vector<double> coords(d->coords, d->coords + (size_t)nn * 3);
   P->coords.upload(coords);
+  if (P->fiber_kind == CBDDC_FIBER_NODAL) {
+    std::vector<double> fn(d->fiber_nodal, d->fiber_nodal + (size_t)nn * 6);
+    for (int v = 0; v < nn; ++v) {
+      const double* q = &fn[(size_t)v * 6];
+      CB_CHECK(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] > 0.0 && q[3] * q[3] + q[4] * q[4] + q[5] * q[5] > 0.0,
+               CBDDC_EINVAL, "zero nodal fibre direction");
+    }
+    P->fib_nodal.upload(fn);
+  }
   P->elems.upload(P->elems_h);
   P->face_nodes.upload(face_nodes);
   P->free_nodes.upload(free_nodes);
@@ -426,7 +476,7 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
 }  // namespace cbddc
 
 int64_t fem_problem::device_bytes() const {
-  return (int64_t)(coords.bytes() + elems.bytes() + face_nodes.bytes() + free_nodes.bytes() +
+  return (int64_t)(coords.bytes() + fib_nodal.bytes() + elems.bytes() + face_nodes.bytes() + free_nodes.bytes() +
                    d_full.bytes() + contrib.bytes() + rcontrib.bytes() + bsr_row_ptr.bytes() +
                    bsr_col.bytes() + bsr_vals.bytes() + slot_ptr.bytes() + slot_src.bytes() +
                    res_ptr.bytes() + res_src.bytes() + lslot_sub.bytes() + lslot_row.bytes() +
