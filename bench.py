@@ -36,8 +36,31 @@ if ROOT not in sys.path:
 METRIC = "Newton-step BDDC-GMRES solve time, FP32-local vs FP64, at 1e-8 rel residual"
 UNIT = "ms/Newton step"
 WORKLOAD = "slab48_q1"
-WORKLOAD_DESC = ("48x48x12 Q1 hex slab [0,4]x[0,4]x[0,1], 64 box subdomains (4x4x4), primal VE, "
-                 "n_free=86436, follower pressure 1 kPa + activation 30 kPa, 4 load steps")
+
+# name -> (description, problem builder, BDDC levels, level-2 groups, load
+# steps whose Newton states are replayed (None: all), FP64 steps timed)
+WORKLOADS = {
+    "slab48_q1": ("48x48x12 Q1 hex slab [0,4]x[0,4]x[0,1], 64 box subdomains (4x4x4), primal VE, "
+                  "n_free=86436, follower pressure 1 kPa + activation 30 kPa, 4 load steps",
+                  lambda: __import__("workloads").slab_config("slab48_q1"), 2, None, None, 3),
+    "slab24_q2": ("24x24x6 Q2 hex slab [0,4]x[0,4]x[0,1], 64 box subdomains (8x4x2), primal VEF, "
+                  "n_free=86436, follower pressure 1 kPa + activation 30 kPa, 4 load steps",
+                  lambda: __import__("workloads").slab_config("slab24_q2"), 2, None, None, 3),
+    "lv_p1": ("left-ventricle shell, P1 tets, ~1.0M free DoFs, 512 uneven subdomains (+-30%), "
+              "primal VEF, two-level (dense FP64 coarse), endocardial pressure 2 kPa + activation "
+              "15 kPa over 8 load steps; Newton states of the first load step",
+              lambda: __import__("workloads").lv_config("lv_p1"), 2, None, 1, 1),
+    "lv_p1_ml": ("left-ventricle shell, P1 tets, ~1.0M free DoFs, 512 uneven subdomains (+-30%) "
+                 "nested in 16 level-2 subdomains, three-level BDDC, primal VEF/VEF, pressure 2 kPa "
+                 "+ activation 15 kPa over 8 load steps; Newton states of the first load step",
+                 lambda: __import__("workloads").lv_config("lv_p1", n_parts2=16), 3, 16, 1, 1),
+    "lv_p2": ("left-ventricle shell, P2 tets, ~3.0M free DoFs, 4096 uneven subdomains (2048 "
+              "surface patches x 2 slabs) nested in 64 level-2 subdomains, three-level BDDC, "
+              "primal VEF/VEF, FP64 coarsest solve, pressure 2 kPa + activation 15 kPa over 8 "
+              "load steps; Newton states of the first load step",
+              lambda: __import__("workloads").lv_config("lv_p2"), 3, 64, 1, 1),
+}
+WORKLOAD_DESC = WORKLOADS[WORKLOAD][0]
 
 
 def _parse():
@@ -49,6 +72,8 @@ def _parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-budget-s", type=float, default=150.0)
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--max-gmres", type=int, default=1000)
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
                     help="kernels: one BDDC setup and a few applies and SpMVs of the workload "
                          "(a short program for profiler captures)")
@@ -218,24 +243,30 @@ def run_ours(args, world, rank, local):
     import torch
 
     import paper_2208_06191_gb300 as pkg
-    from workloads import slab_config
 
     if world == 1:
         torch.cuda.set_device(local)
     pkg.build()
     pkg.load_library()
-    prob = slab_config(WORKLOAD)
+    desc, build_prob, levels, _groups, n_load_rec, fp64_default = WORKLOADS[args.workload]
+    prob = build_prob()
     P = pkg.Problem(prob)
     n = P.n_free
-    opts32 = pkg.SolveOptions(precision=pkg.FP32, primal=prob["primal"])
-    opts64 = pkg.SolveOptions(precision=pkg.FP64, primal=prob["primal"])
+    ml = {}
+    if levels == 3:
+        ml = dict(levels=3, part2=prob["part2"], n_parts2=prob["n_parts2"], primal2="VEF")
+    opts32 = pkg.SolveOptions(precision=pkg.FP32, primal=prob["primal"], max_gmres=args.max_gmres,
+                              precision2=pkg.FP32, **ml)
+    opts64 = pkg.SolveOptions(precision=pkg.FP64, primal=prob["primal"], max_gmres=args.max_gmres,
+                              precision2=pkg.FP64, **ml)
 
-    # untimed: Newton states of a full FP32 solve
+    # untimed: Newton states of a full FP32 solve (or of its first load steps)
     states = []
     d = torch.zeros(n, dtype=torch.float64, device="cuda")
     r = torch.empty_like(d)
     ctx32 = None
-    for k in range(1, prob["load_steps"] + 1):
+    last = prob["load_steps"] if n_load_rec is None else n_load_rec
+    for k in range(1, last + 1):
         lam = k / prob["load_steps"]
         P.residual(d, lam, r)
         r0 = float(torch.linalg.vector_norm(r))
@@ -301,7 +332,7 @@ def run_ours(args, world, rank, local):
     # ---- FP64 local operators
     ctx64 = run_steps(1, opts64, None)
     recs64 = []
-    K64 = max(1, min(K, args.fp64_steps))
+    K64 = max(1, min(K, args.fp64_steps if args.workload == WORKLOAD else fp64_default))
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
@@ -351,9 +382,10 @@ def run_ours(args, world, rank, local):
         "ms_per_step": ms32, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
         "config": {
-            "workload": WORKLOAD_DESC, "newton_states": ns, "parallelism": "replicas",
+            "workload": desc, "workload_name": args.workload, "newton_states": ns,
+            "n_free": n, "parallelism": "replicas",
             "precision": {"local_operators": "f32", "assembly": "f64", "gmres": "f64",
-                          "coarse": "f64"},
+                          "coarse": "f64" if levels == 2 else "level-2 f32, coarsest f64"},
             "l2": "inputs larger than L2 (dense local operators ~1.1 GB read per BDDC apply)",
         },
         "fp64": {"ms_per_step": ms64, "steps": K64,
@@ -372,7 +404,10 @@ def run_ours(args, world, rank, local):
     }
     if clk:
         line["clocks"] = clk
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if args.workload != WORKLOAD:
+        line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "not run: reported for the default workload only"}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             s, its = _oracle_step_seconds(timeout=900)
             line["cpu_baseline"] = {
@@ -391,16 +426,20 @@ def run_kernels(args):
     import torch
 
     import paper_2208_06191_gb300 as pkg
-    from workloads import slab_config
 
     pkg.build()
     pkg.load_library()
-    prob = slab_config(WORKLOAD)
+    _desc, build_prob, levels, _groups, _n, _f = WORKLOADS[args.workload]
+    prob = build_prob()
     P = pkg.Problem(prob)
     d = torch.zeros(P.n_free, dtype=torch.float64, device="cuda")
     r = torch.empty_like(d)
     P.assemble_tangent(d, 1.0 / prob["load_steps"], r)
-    pc = pkg.BDDC(P, precision=pkg.FP32, primal=prob["primal"]).setup()
+    ml = {}
+    if levels == 3:
+        ml = dict(levels=3, part2=prob["part2"], n_parts2=prob["n_parts2"], primal2="VEF",
+                  precision2=pkg.FP32)
+    pc = pkg.BDDC(P, precision=pkg.FP32, primal=prob["primal"], **ml).setup()
     z = torch.empty_like(d)
     y = torch.empty_like(d)
     for _ in range(3):

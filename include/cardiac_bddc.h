@@ -195,13 +195,17 @@ typedef struct {
      (or 0): the coarse problem S_PiPi is inverted densely in FP64.
      levels = 3: the coarse problem, an unassembled matrix whose elements
      are the subdomains with their local coarse matrices, is approximated by
-     one FP64 BDDC application on n_parts2 level-2 subdomains (part2[i] is
-     the level-2 subdomain of subdomain i, host array, copied), with primal
-     space primal2; its own coarse problem is inverted densely in FP64. */
+     one BDDC application on n_parts2 level-2 subdomains (part2[i] is the
+     level-2 subdomain of subdomain i, host array, copied), with primal
+     space primal2 and local operators in precision2 (CBDDC_FP64, the
+     zero default, or CBDDC_FP32); its own (coarsest) problem is inverted
+     densely in FP64.  A subdomain may carry at most 512 primal
+     constraints. */
   int levels;
   int n_parts2;
   const int32_t* part2;
   int primal2;
+  int precision2;
 } bddc_options;
 
 typedef struct bddc_ctx bddc_ctx;
@@ -294,6 +298,7 @@ typedef struct {
   int n_parts2;
   const int32_t* part2;
   int primal2;
+  int precision2;
 } solve_options;
 
 #define CBDDC_MAX_RECORDS 512

@@ -273,51 +273,6 @@ __global__ void cons_g_kernel(const int* __restrict__ na, const int64_t* __restr
   G[offG[s] + (int64_t)q * ldG[s] + q2] = (T)(acc * cw[gq]);
 }
 
-// In-place inverse of each small n_a x n_a block (FP64 Gauss-Jordan).
-template <typename T>
-__global__ void small_inverse_kernel(const int* __restrict__ na, const int64_t* __restrict__ offG,
-                                     const int* __restrict__ ldG, T* __restrict__ G,
-                                     int* __restrict__ status, double tol) {
-  extern __shared__ double sm[];
-  const int s = blockIdx.x;
-  const int n = na[s];
-  if (n == 0) return;
-  double* a = sm;                 // n x (n+1)
-  double* fcol = sm + n * (n + 1);
-  __shared__ double scale;
-  __shared__ int bad;
-  const int tid = threadIdx.x;
-  T* g = G + offG[s];
-  const int ld = ldG[s];
-  for (int t = tid; t < n * n; t += blockDim.x) a[(t / n) * (n + 1) + t % n] = (double)g[(int64_t)(t / n) * ld + t % n];
-  if (tid == 0) { bad = 0; scale = 0.0; }
-  __syncthreads();
-  if (tid == 0) {
-    double m = 0.0;
-    for (int i = 0; i < n; ++i) m = fmax(m, fabs(a[i * (n + 1) + i]));
-    scale = m;
-  }
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    const double pv = a[j * (n + 1) + j];
-    if (tid == 0 && (!(fabs(pv) > tol * scale) || !isfinite(pv))) bad = 1;
-    const double inv = 1.0 / pv;
-    for (int i = tid; i < n; i += blockDim.x) fcol[i] = a[i * (n + 1) + j];
-    __syncthreads();
-    for (int c = tid; c < n; c += blockDim.x) a[j * (n + 1) + c] = (c == j) ? inv : a[j * (n + 1) + c] * inv;
-    __syncthreads();
-    for (int t = tid; t < n * n; t += blockDim.x) {
-      const int i = t / n, c = t % n;
-      if (i == j) continue;
-      if (c == j) a[i * (n + 1) + c] = -fcol[i] * inv;
-      else a[i * (n + 1) + c] -= fcol[i] * a[j * (n + 1) + c];
-    }
-    __syncthreads();
-  }
-  for (int t = tid; t < n * n; t += blockDim.x) g[(int64_t)(t / n) * ld + t % n] = (T)a[(t / n) * (n + 1) + t % n];
-  if (tid == 0 && bad) atomicOr(status, DEV_PIVOT);
-}
-
 // Phi[0:nr, 0:nv] = -Sw[0:nr, nr:nG] ; Phi[nr:nG, :] = [I 0]
 template <typename T>
 __global__ void phi_vertex_kernel(const int* __restrict__ nG, const int* __restrict__ nr,
@@ -359,6 +314,7 @@ __global__ void coarse_assemble_kernel_d(const int* __restrict__ key, const int*
 
 // ------------------------------------------------------------ apply kernels
 constexpr int AROWS = 32;  // rows per CTA in the batched GEMVs (8 warps x 4)
+constexpr int NC_MAX = 512;  // primal constraints per subdomain
 
 // xI = r[gdof of the interior DoFs], packed per subdomain.
 __global__ void gather_kernel(const int* __restrict__ idx, int64_t n, const double* __restrict__ x,
@@ -450,9 +406,9 @@ apply_local_kernel(const int* __restrict__ nG, const int* __restrict__ nr,
 }
 
 // Partial coarse restriction Phi^T g_i over one chunk of PHIT_ROWS interface
-// rows: clp[(offC[s] + c) * nchunk + chunk] (FP64 accumulation, n_c <= 128).
-// Chunks past the subdomain's rows write zeros, so the coarse gather can sum
-// every chunk of every entry in a fixed order.
+// rows: clp[(offC[s] + c) * nchunk + chunk] (FP64 accumulation), columns in
+// blocks of 128.  Chunks past the subdomain's rows write zeros, so the
+// coarse gather can sum every chunk of every entry in a fixed order.
 constexpr int PHIT_ROWS = 128;
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -466,27 +422,30 @@ apply_phit_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
   const int ng = nG[s], ncs = nc[s];
   if (ncs == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double acc[4] = {0, 0, 0, 0};
   const T* P0 = Phi + offPhi[s];
   const int ld = ldPhi[s];
   const int64_t og = offGam[s];
   const int r0 = chunk * PHIT_ROWS, r1 = min(ng, r0 + PHIT_ROWS);
-  for (int j = r0 + warp; j < r1; j += 8) {
-    const double gj = gl[og + j];
-    const T* row = P0 + (int64_t)j * ld;
+  for (int cb = 0; cb < ncs; cb += 128) {
+    double acc[4] = {0, 0, 0, 0};
+    for (int j = r0 + warp; j < r1; j += 8) {
+      const double gj = gl[og + j];
+      const T* row = P0 + (int64_t)j * ld + cb;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int c = lane + 32 * t;
-      if (c < ncs) acc[t] += (double)row[c] * gj;
+      for (int t = 0; t < 4; ++t) {
+        const int c = lane + 32 * t;
+        if (cb + c < ncs) acc[t] += (double)row[c] * gj;
+      }
     }
-  }
+    __syncthreads();  // red is reused across column blocks
 #pragma unroll
-  for (int t = 0; t < 4; ++t) red[warp][lane + 32 * t] = acc[t];
-  __syncthreads();
-  for (int c = threadIdx.x; c < ncs; c += blockDim.x) {
-    double v = 0.0;
-    for (int w = 0; w < 8; ++w) v += red[w][c];
-    clp[(offC[s] + c) * nchunk + chunk] = v;
+    for (int t = 0; t < 4; ++t) red[warp][lane + 32 * t] = acc[t];
+    __syncthreads();
+    for (int c = threadIdx.x; c < 128 && cb + c < ncs; c += blockDim.x) {
+      double v = 0.0;
+      for (int w = 0; w < 8; ++w) v += red[w][c];
+      clp[(offC[s] + cb + c) * nchunk + chunk] = v;
+    }
   }
 }
 
@@ -524,7 +483,7 @@ apply_prolong_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
                      const int* __restrict__ gprim, const T* __restrict__ Phi,
                      const double* __restrict__ uc, const double* __restrict__ wG,
                      const double* __restrict__ Dg, double* __restrict__ yG) {
-  __shared__ double ucl[128];
+  __shared__ double ucl[NC_MAX];
   const int s = blockIdx.y;
   const int ng = nG[s], ncs = nc[s];
   const int r0 = blockIdx.x * AROWS;
@@ -677,6 +636,9 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     CB_CHECK(opt->part2 != nullptr && opt->n_parts2 >= 1, CBDDC_EINVAL, "multilevel BDDC needs part2");
     C->n_parts2 = opt->n_parts2;
     C->primal2 = opt->primal2 ? opt->primal2 : (CBDDC_PRIMAL_V | CBDDC_PRIMAL_E | CBDDC_PRIMAL_F);
+    CB_CHECK(opt->precision2 == CBDDC_FP64 || opt->precision2 == CBDDC_FP32, CBDDC_EINVAL,
+             "bad precision2");
+    C->precision2 = opt->precision2;
     C->part2.assign(opt->part2, opt->part2 + P->n_parts);
     for (int g : C->part2) CB_CHECK(g >= 0 && g < C->n_parts2, CBDDC_EINVAL, "part2 out of range");
   }
@@ -763,7 +725,7 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     }
     C->na[s] = 3 * (int)cls.size();
     C->nc[s] = C->nv[s] + C->na[s];
-    CB_CHECK(C->nc[s] <= 128, CBDDC_EINVAL, "more than 128 primal constraints in one subdomain");
+    CB_CHECK(C->nc[s] <= NC_MAX, CBDDC_EINVAL, "more than 512 primal constraints in one subdomain");
     for (int l : Gv)
       for (int c = 0; c < 3; ++c) gprim.push_back(3 * vert_pos[sub.nodes[l]] + c);
     for (int j : cls)
@@ -867,17 +829,24 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   // Interior elimination: sweep of the A_II block alone (A_II^-1 in place),
   // then E = A_II^-1 A_IG and S = A_GG - A_GI E as two large-K GEMMs; E is
   // copied over A_IG afterwards (A_IG is not needed once S is formed).
-  std::vector<SweepDesc> sw1(nsub), sw2(nsub);
+  // The constraint matrix G = C S_rr^-1 C^T (n_a x n_a) is inverted by a
+  // third sweep; its panels fit the same X / Y buffers (n_a <= n_s rows,
+  // ld_G <= ld_A columns).
+  std::vector<SweepDesc> sw1(nsub), sw2(nsub), swg(nsub);
   for (int s = 0; s < nsub; ++s) {
     sw1[s] = SweepDesc{C->nI[s], C->nI[s], C->ldA[s], C->nI[s], C->offA[s], C->offX[s], C->offYp[s],
                        C->offP[s]};
     sw2[s] = SweepDesc{C->nG[s], C->nG[s], C->ldS[s], C->nr[s], C->offS[s], C->offX[s], C->offYp[s],
                        C->offP[s]};
+    swg[s] = SweepDesc{C->na[s], C->na[s], C->ldG[s], C->na[s], C->offG[s], C->offX[s], C->offYp[s],
+                       C->offP[s]};
     C->steps1 = std::max(C->steps1, (int)cdiv(C->nI[s], NB));
     C->steps2 = std::max(C->steps2, (int)cdiv(C->nr[s], NB));
+    C->stepsg = std::max(C->stepsg, (int)cdiv(C->na[s], NB));
   }
   C->sw1.upload(sw1);
   C->sw2.upload(sw2);
+  C->swg.upload(swg);
   auto sweep_gemms = [NB, es](const std::vector<SweepDesc>& sw, int steps, std::vector<GemmList>& out) {
     const int nmat = (int)sw.size();
     out.clear();
@@ -894,6 +863,7 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   };
   sweep_gemms(sw1, C->steps1, C->gl_sw1);
   sweep_gemms(sw2, C->steps2, C->gl_sw2);
+  sweep_gemms(swg, C->stepsg, C->gl_swg);
   std::vector<GemmProb> gE, gS, gW, gT, gPA, gSP, gKc;
   for (int s = 0; s < nsub; ++s) {
     const int cI = (int)round_up(C->nI[s], 4);
@@ -1010,7 +980,9 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     C->coarse_prob.reset(new fem_problem);
     build_coarse_problem(C, C->coarse_prob.get());
     bddc_options o2{};
-    o2.precision = CBDDC_FP64;
+    // level-2 local operators in precision2; the coarsest problem (level
+    // 2's own coarse matrix) is always FP64
+    o2.precision = C->precision2;
     o2.primal = C->primal2;
     o2.pivot_tol = C->pivot_tol;
     o2.levels = 2;
@@ -1100,12 +1072,7 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
         C->d_na.p, C->d_offCon.p, C->cons_ptr.p, C->cons_idx.p, C->cons_w.p, C->d_offY.p, C->d_ldY.p,
         C->d_offG.p, C->d_ldG.p, Y, G);
     CB_LAUNCH();
-    const size_t smem = (size_t)C->maxA * (C->maxA + 2) * sizeof(double);
-    if (smem > 48 * 1024)
-      CB_CUDA(cudaFuncSetAttribute(small_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-    small_inverse_kernel<T><<<nsub, 256, smem, s>>>(C->d_na.p, C->d_offG.p, C->d_ldG.p, G, status, tol);
-    CB_LAUNCH();
+    run_sweep<T>(C->swg, nsub, C->gl_swg, C->maxA, C->maxA, G, Xp, Yp, Pd, status, tol, s);
     launch_list<T, false, false>(C->gl_W, G, Zf, Wf, T(1), T(0), s);
     launch_list<T, false, false>(C->gl_T, Y, Wf, Sw, T(-1), T(1), s);
     launch_list<T, false, false>(C->gl_PhiA, Y, G, Phi, T(1), T(0), s);

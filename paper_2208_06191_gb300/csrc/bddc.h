@@ -39,9 +39,9 @@ struct bddc_ctx {
   // apply work vectors
   cbddc::DVec<double> u0, hG, gI, wG, cl, rc, uc, yG, xI, zl;
   // sweep descriptors and GEMM problem lists
-  cbddc::DVec<cbddc::SweepDesc> sw1, sw2, swc;
-  int steps1 = 0, steps2 = 0, stepsc = 0;
-  std::vector<cbddc::GemmList> gl_sw1, gl_sw2, gl_swc;
+  cbddc::DVec<cbddc::SweepDesc> sw1, sw2, swg, swc;
+  int steps1 = 0, steps2 = 0, stepsg = 0, stepsc = 0;
+  std::vector<cbddc::GemmList> gl_sw1, gl_sw2, gl_swg, gl_swc;
   cbddc::GemmList gl_E, gl_S, gl_W, gl_T, gl_PhiA, gl_SPhi, gl_Kc;
   cbddc::DVec<double> gl;                  // scaled interface restriction
   double setup_flops = 0.0, apply_flops = 0.0;
@@ -51,7 +51,7 @@ struct bddc_ctx {
   cbddc::DVec<double> nw_r, nw_b, nw_delta, nw_d;
   // multilevel: the coarse problem as an unassembled matrix and its BDDC
   std::vector<int> gprim_h;
-  int levels = 2, n_parts2 = 0, primal2 = 0;
+  int levels = 2, n_parts2 = 0, primal2 = 0, precision2 = CBDDC_FP64;
   std::vector<int> part2;
   std::unique_ptr<fem_problem> coarse_prob;
   std::unique_ptr<bddc_ctx> next;

@@ -25,6 +25,8 @@ struct Timer {
   int kernel_class = 0;
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
+  int depth = 0;      // nesting of begin/end of the timed class (multilevel apply)
+  bool open = false;  // the outermost begin recorded an event
   int64_t launches = 0;
   double flops = 0.0, bytes = 0.0;
   static constexpr size_t kMax = 65536;
@@ -33,19 +35,28 @@ struct Timer {
 
 bool timer_active(int kernel_class) { return g_timer.kernel_class == kernel_class && kernel_class != 0; }
 
+// Only the outermost begin/end pair of the timed class is recorded: the
+// multilevel apply runs the level-2 apply inside the level-1 one, and its
+// work is already counted in the outer call's flops and bytes.
 void timer_begin(int kernel_class, cudaStream_t s) {
-  if (!timer_active(kernel_class) || g_timer.used + 2 > Timer::kMax) return;
+  if (!timer_active(kernel_class)) return;
+  if (g_timer.depth++ > 0) return;
+  g_timer.open = false;
+  if (g_timer.used + 2 > Timer::kMax) return;
   while (g_timer.pool.size() < g_timer.used + 2) {
     cudaEvent_t e;
     CB_CUDA(cudaEventCreate(&e));
     g_timer.pool.push_back(e);
   }
   CB_CUDA(cudaEventRecord(g_timer.pool[g_timer.used], s));
+  g_timer.open = true;
 }
 
 void timer_end(int kernel_class, cudaStream_t s, double flops, double bytes) {
-  if (!timer_active(kernel_class) || g_timer.used + 2 > Timer::kMax) return;
+  if (!timer_active(kernel_class) || g_timer.depth == 0) return;
+  if (--g_timer.depth > 0 || !g_timer.open) return;
   CB_CUDA(cudaEventRecord(g_timer.pool[g_timer.used + 1], s));
+  g_timer.open = false;
   g_timer.used += 2;
   g_timer.launches += 1;
   g_timer.flops += flops;
@@ -100,6 +111,7 @@ static void ensure_ctx(fem_problem* P, const solve_options* opt, bddc_ctx** C) {
   bo.n_parts2 = opt->n_parts2;
   bo.part2 = opt->part2;
   bo.primal2 = opt->primal2;
+  bo.precision2 = opt->precision2;
   bddc_ctx* c = new bddc_ctx;
   try {
     bddc_create(P, &bo, c);
@@ -466,6 +478,8 @@ int cbddc_timer_start(int kernel_class) {
     CB_CHECK(kernel_class >= 0 && kernel_class <= CBDDC_TIMER_SPMV, CBDDC_EINVAL, "bad kernel class");
     g_timer.kernel_class = kernel_class;
     g_timer.used = 0;
+    g_timer.depth = 0;
+    g_timer.open = false;
     g_timer.launches = 0;
     g_timer.flops = g_timer.bytes = 0.0;
   });
@@ -486,6 +500,8 @@ int cbddc_timer_stop(double* total_ms, int64_t* launches, double* flops, double*
     if (bytes) *bytes = g_timer.bytes;
     g_timer.kernel_class = 0;
     g_timer.used = 0;
+    g_timer.depth = 0;
+    g_timer.open = false;
   });
 }
 

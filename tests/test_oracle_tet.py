@@ -13,6 +13,7 @@ from oracle import material as mat
 from oracle.assembly import FEProblem
 from oracle.bddc import outer_boundary_nodes
 from workloads import lv_problem
+from workloads.lv import ring_sizes
 
 
 def _tet_monomial(a, b, c):
@@ -137,12 +138,13 @@ def test_lv_pressure_resultant(k):
     # endocardium and the base opening enclose the cavity, so the integral
     # of the outward tissue normal over the endocardium equals the area of
     # the (polygonal) opening times e_z.
-    p, nth, a = 1.7e3, 10, 0.025
-    prob = _small_lv(k, gamma=0.0, pressure=p, ntheta=nth, a_endo=a)
+    p, nth, nu, a = 1.7e3, 16, 5, 0.025
+    prob = _small_lv(k, gamma=0.0, pressure=p, ntheta=nth, nu=nu, a_endo=a)
     prob["dirichlet_nodes"] = np.zeros(0, dtype=np.int32)
     fe = FEProblem(prob)
     r = fe.residual(np.zeros(fe.n_free), 1.0).reshape(-1, 3)
-    area = 0.5 * nth * a * a * np.sin(2 * np.pi / nth)
+    nb = ring_sizes(nth, nu)[-1]                          # nodes on the base ring
+    area = 0.5 * nb * a * a * np.sin(2 * np.pi / nb)
     assert np.allclose(r.sum(0), [0.0, 0.0, p * area], rtol=1e-12, atol=1e-12)
 
 
