@@ -60,6 +60,17 @@ WORKLOADS = {
               "load steps; Newton states of the first load step",
               lambda: __import__("workloads").lv_config("lv_p2"), 3, 64, 1, 1),
 }
+# reduced ventricles (same generator, 5 x 64 x 32 rings, 64 subdomains) for
+# profiler captures that must stay a few GB on the device
+WORKLOADS["lv_p1_small"] = ("left-ventricle shell, P1 tets, 5 x 64 x 32 rings, 64 subdomains",
+                            lambda: __import__("workloads").lv_problem(
+                                nt=5, ntheta=64, nu=32, order=1, n_parts=64, load_steps=8,
+                                gamma=0.25 * 6.0e4), 2, None, 1, 1)
+WORKLOADS["lv_p2_small"] = ("left-ventricle shell, P2 tets, 5 x 64 x 32 rings, 128 subdomains "
+                            "(64 patches x 2 slabs) in 8 level-2 subdomains",
+                            lambda: __import__("workloads").lv_problem(
+                                nt=5, ntheta=64, nu=32, order=2, n_parts=128, n_parts2=8,
+                                n_layers=2, load_steps=8, gamma=0.25 * 6.0e4), 3, 8, 1, 1)
 WORKLOAD_DESC = WORKLOADS[WORKLOAD][0]
 
 
@@ -318,7 +329,7 @@ def run_ours(args, world, rank, local):
     # region, so the timed numbers carry no extra events)
     kernels = {}
     for name, cls in (("bddc_apply", pkg.TIMER_APPLY), ("bsr_spmv", pkg.TIMER_SPMV),
-                      ("element_kernel", pkg.TIMER_ELEMENT)):
+                      ("element_kernel", pkg.TIMER_ELEMENT), ("gmres_orth", pkg.TIMER_ORTH)):
         pkg.timer_start(cls)
         ctx32 = run_steps(2, opts32, ctx32)
         t = pkg.timer_stop()

@@ -356,7 +356,9 @@ enum {
   CBDDC_TIMER_SWEEP_GEMM = 1, /* trailing updates of the Gauss-Jordan sweeps */
   CBDDC_TIMER_ELEMENT = 2,    /* element residual/tangent kernel              */
   CBDDC_TIMER_APPLY = 3,      /* one whole BDDC apply (all its launches)      */
-  CBDDC_TIMER_SPMV = 4        /* BSR SpMV                                     */
+  CBDDC_TIMER_SPMV = 4,       /* BSR SpMV                                     */
+  CBDDC_TIMER_ORTH = 5        /* one GMRES orthogonalisation (CGS2, Givens,
+                                 normalisation)                               */
 };
 
 /* Starts recording CUDA events around every launch of the given class, on

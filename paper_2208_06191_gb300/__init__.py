@@ -37,7 +37,7 @@ EXPORTED_SYMBOLS = [
     "cbddc_kernel_launches", "cbddc_timer_start", "cbddc_timer_stop",
     "cbddc_last_error",
 ]
-TIMER_OFF, TIMER_SWEEP_GEMM, TIMER_ELEMENT, TIMER_APPLY, TIMER_SPMV = range(5)
+TIMER_OFF, TIMER_SWEEP_GEMM, TIMER_ELEMENT, TIMER_APPLY, TIMER_SPMV, TIMER_ORTH = range(6)
 
 
 def primal_mask(spec):

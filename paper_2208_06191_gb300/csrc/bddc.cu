@@ -314,6 +314,7 @@ __global__ void coarse_assemble_kernel_d(const int* __restrict__ key, const int*
 
 // ------------------------------------------------------------ apply kernels
 constexpr int AROWS = 32;  // rows per CTA in the batched GEMVs (8 warps x 4)
+constexpr int PHIT_ROWS = 128;  // interface rows per CTA of the coarse restriction
 constexpr int NC_MAX = 512;  // primal constraints per subdomain
 
 // xI = r[gdof of the interior DoFs], packed per subdomain.
@@ -326,14 +327,16 @@ __global__ void gather_kernel(const int* __restrict__ idx, int64_t n, const doub
 // u0 = A_II^-1 r_I (rows of the A_II^-1 block), 64 rows per CTA.
 template <typename T>
 __global__ void __launch_bounds__(256)
-apply_interior_kernel(const int* __restrict__ nI, const int64_t* __restrict__ offA,
-                      const int* __restrict__ ldA, const int64_t* __restrict__ offI,
-                      const T* __restrict__ Aloc, const double* __restrict__ xI, double* __restrict__ u0) {
+apply_interior_kernel(const int2* __restrict__ items, const int* __restrict__ nI,
+                      const int64_t* __restrict__ offA, const int* __restrict__ ldA,
+                      const int64_t* __restrict__ offI, const T* __restrict__ Aloc,
+                      const double* __restrict__ xI, double* __restrict__ u0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* xs = reinterpret_cast<T*>(smraw);
-  const int s = blockIdx.y;
+  const int2 it = items[blockIdx.x];
+  const int s = it.x;
   const int ni = nI[s];
-  const int rb = blockIdx.x * GROWS * GGROUPS;
+  const int rb = it.y * GROWS * GGROUPS;
   if (rb >= ni) return;
   load_x<T>(xs, xI + offI[s], ni);
   double* out = u0 + offI[s];
@@ -344,15 +347,16 @@ apply_interior_kernel(const int* __restrict__ nI, const int64_t* __restrict__ of
 // hG = -A_GI u0 (the interface part of the interior correction).
 template <typename T>
 __global__ void __launch_bounds__(256)
-apply_gi_kernel(const int* __restrict__ nI, const int* __restrict__ nG, const int64_t* __restrict__ offA,
-                const int* __restrict__ ldA, const int64_t* __restrict__ offI,
-                const int64_t* __restrict__ offGam, const T* __restrict__ Aloc,
-                const double* __restrict__ u0, double* __restrict__ hG) {
+apply_gi_kernel(const int2* __restrict__ items, const int* __restrict__ nI, const int* __restrict__ nG,
+                const int64_t* __restrict__ offA, const int* __restrict__ ldA,
+                const int64_t* __restrict__ offI, const int64_t* __restrict__ offGam,
+                const T* __restrict__ Aloc, const double* __restrict__ u0, double* __restrict__ hG) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* xs = reinterpret_cast<T*>(smraw);
-  const int s = blockIdx.y;
+  const int2 it = items[blockIdx.x];
+  const int s = it.x;
   const int ni = nI[s], ng = nG[s];
-  const int rb = blockIdx.x * GROWS * GGROUPS;
+  const int rb = it.y * GROWS * GGROUPS;
   if (rb >= ng) return;
   const int re = min(ng, rb + GROWS * GGROUPS);
   double* out = hG + offGam[s];
@@ -385,15 +389,16 @@ __global__ void restrict_kernel(const int* __restrict__ gam_if, const double* __
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-apply_local_kernel(const int* __restrict__ nG, const int* __restrict__ nr,
+apply_local_kernel(const int2* __restrict__ items, const int* __restrict__ nG, const int* __restrict__ nr,
                    const int64_t* __restrict__ offS, const int* __restrict__ ldS,
                    const int64_t* __restrict__ offGam, const T* __restrict__ Sw,
                    const double* __restrict__ gl, double* __restrict__ wG) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* xs = reinterpret_cast<T*>(smraw);
-  const int s = blockIdx.y;
+  const int2 it = items[blockIdx.x];
+  const int s = it.x;
   const int ng = nG[s], nrs = nr[s];
-  const int rb = blockIdx.x * GROWS * GGROUPS;
+  const int rb = it.y * GROWS * GGROUPS;
   if (rb >= ng) return;
   const int64_t og = offGam[s];
   const int re = min(ng, rb + GROWS * GGROUPS);
@@ -407,18 +412,18 @@ apply_local_kernel(const int* __restrict__ nG, const int* __restrict__ nr,
 
 // Partial coarse restriction Phi^T g_i over one chunk of PHIT_ROWS interface
 // rows: clp[(offC[s] + c) * nchunk + chunk] (FP64 accumulation), columns in
-// blocks of 128.  Chunks past the subdomain's rows write zeros, so the
-// coarse gather can sum every chunk of every entry in a fixed order.
-constexpr int PHIT_ROWS = 128;
+// blocks of 128.  Only the subdomain's own chunks exist (work items); the
+// coarse gather sums each entry's chunks in order.
 template <typename T>
 __global__ void __launch_bounds__(256)
-apply_phit_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
+apply_phit_kernel(const int2* __restrict__ items, const int* __restrict__ nG, const int* __restrict__ nc,
                   const int64_t* __restrict__ offPhi, const int* __restrict__ ldPhi,
                   const int64_t* __restrict__ offGam, const int64_t* __restrict__ offC,
                   const T* __restrict__ Phi, const double* __restrict__ gl, double* __restrict__ clp,
                   int nchunk) {
   __shared__ double red[8][128];
-  const int s = blockIdx.y, chunk = blockIdx.x;
+  const int2 it = items[blockIdx.x];
+  const int s = it.x, chunk = it.y;
   const int ng = nG[s], ncs = nc[s];
   if (ncs == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -427,19 +432,22 @@ apply_phit_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
   const int64_t og = offGam[s];
   const int r0 = chunk * PHIT_ROWS, r1 = min(ng, r0 + PHIT_ROWS);
   for (int cb = 0; cb < ncs; cb += 128) {
-    double acc[4] = {0, 0, 0, 0};
+    // products and the chunk's partial sums in the operator precision (FP64
+    // issue is the scarce resource on this part); chunks are summed in FP64
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 4
     for (int j = r0 + warp; j < r1; j += 8) {
-      const double gj = gl[og + j];
+      const T gj = (T)gl[og + j];
       const T* row = P0 + (int64_t)j * ld + cb;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int c = lane + 32 * t;
-        if (cb + c < ncs) acc[t] += (double)row[c] * gj;
+        if (cb + c < ncs) acc[t] += row[c] * gj;
       }
     }
     __syncthreads();  // red is reused across column blocks
 #pragma unroll
-    for (int t = 0; t < 4; ++t) red[warp][lane + 32 * t] = acc[t];
+    for (int t = 0; t < 4; ++t) red[warp][lane + 32 * t] = (double)acc[t];
     __syncthreads();
     for (int c = threadIdx.x; c < 128 && cb + c < ncs; c += blockDim.x) {
       double v = 0.0;
@@ -449,15 +457,18 @@ apply_phit_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
   }
 }
 
-// rc[p] = sum over the listed local primal entries of all their chunks.
+// rc[p] = sum over the listed local primal entries of all their chunks
+// (cnch[q]: chunks of the subdomain that owns local entry q).
 __global__ void coarse_rhs_kernel(const int* __restrict__ ptr, const int* __restrict__ src, int n,
-                                  const double* __restrict__ clp, int nchunk, double* __restrict__ rc) {
+                                  const double* __restrict__ clp, int nchunk,
+                                  const int* __restrict__ cnch, double* __restrict__ rc) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n) return;
   double v = 0.0;
   for (int j = ptr[m]; j < ptr[m + 1]; ++j) {
     const double* q = clp + (int64_t)src[j] * nchunk;
-    for (int c = 0; c < nchunk; ++c) v += q[c];
+    const int nc = cnch[src[j]];
+    for (int c = 0; c < nc; ++c) v += q[c];
   }
   rc[m] = v;
 }
@@ -477,32 +488,34 @@ __global__ void dense_gemv_kernel(const double* __restrict__ A, int n, const dou
 // y_i = D_i (w_i + Phi_i R_Pi u_c); 8 lanes per interface row.
 template <typename T>
 __global__ void __launch_bounds__(256)
-apply_prolong_kernel(const int* __restrict__ nG, const int* __restrict__ nc,
+apply_prolong_kernel(const int2* __restrict__ items, const int* __restrict__ nG, const int* __restrict__ nc,
                      const int64_t* __restrict__ offPhi, const int* __restrict__ ldPhi,
                      const int64_t* __restrict__ offGam, const int64_t* __restrict__ offC,
                      const int* __restrict__ gprim, const T* __restrict__ Phi,
                      const double* __restrict__ uc, const double* __restrict__ wG,
                      const double* __restrict__ Dg, double* __restrict__ yG) {
-  __shared__ double ucl[NC_MAX];
-  const int s = blockIdx.y;
+  __shared__ T ucl[NC_MAX];
+  const int2 it = items[blockIdx.x];
+  const int s = it.x;
   const int ng = nG[s], ncs = nc[s];
-  const int r0 = blockIdx.x * AROWS;
+  const int r0 = it.y * AROWS;
   if (r0 >= ng) return;
-  for (int c = threadIdx.x; c < ncs; c += blockDim.x) ucl[c] = uc[gprim[offC[s] + c]];
+  for (int c = threadIdx.x; c < ncs; c += blockDim.x) ucl[c] = (T)uc[gprim[offC[s] + c]];
   __syncthreads();
   const int sub = threadIdx.x & 7, grp = threadIdx.x >> 3;  // 32 groups of 8 lanes
   const int row = r0 + grp;
-  double acc = 0.0;
+  T acc = T(0);  // operator precision, as in the other local products
   if (row < ng) {
     const T* pr = Phi + offPhi[s] + (int64_t)row * ldPhi[s];
-    for (int c = sub; c < ncs; c += 8) acc += (double)pr[c] * ucl[c];
+#pragma unroll 4
+    for (int c = sub; c < ncs; c += 8) acc += pr[c] * ucl[c];
   }
   acc += __shfl_xor_sync(0xffffffffu, acc, 4);
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
   acc += __shfl_xor_sync(0xffffffffu, acc, 1);
   if (row < ng && sub == 0) {
     const int64_t og = offGam[s];
-    yG[og + row] = Dg[og + row] * (wG[og + row] + acc);
+    yG[og + row] = Dg[og + row] * (wG[og + row] + (double)acc);
   }
 }
 
@@ -521,16 +534,17 @@ __global__ void average_kernel(const int* __restrict__ if_dof, const int* __rest
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-apply_extend_kernel(const int* __restrict__ nI, const int* __restrict__ nG,
+apply_extend_kernel(const int2* __restrict__ items, const int* __restrict__ nI, const int* __restrict__ nG,
                     const int64_t* __restrict__ offA, const int* __restrict__ ldA,
                     const int64_t* __restrict__ offI, const int64_t* __restrict__ offGam,
                     const int* __restrict__ gdofI, const T* __restrict__ Aloc,
                     const double* __restrict__ zl, const double* __restrict__ u0, double* __restrict__ z) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* xs = reinterpret_cast<T*>(smraw);
-  const int s = blockIdx.y;
+  const int2 it = items[blockIdx.x];
+  const int s = it.x;
   const int ni = nI[s], ng = nG[s];
-  const int rb = blockIdx.x * GROWS * GGROUPS;
+  const int rb = it.y * GROWS * GGROUPS;
   if (rb >= ni) return;
   const int re = min(ni, rb + GROWS * GGROUPS);
   const int64_t oi = offI[s];
@@ -938,6 +952,28 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     }
   }
 
+  // work items (subdomain, row block) of the batched apply kernels: only
+  // blocks that exist, so many small subdomains of uneven size cost no
+  // empty CTAs
+  {
+    std::vector<int2> iI, iG, iP, iR;
+    std::vector<int> cn(std::max<int64_t>(C->totC, 1), 0);
+    for (int s = 0; s < nsub; ++s) {
+      for (int b = 0; b < (int)cdiv(C->nI[s], GROWS * GGROUPS); ++b) iI.push_back(make_int2(s, b));
+      for (int b = 0; b < (int)cdiv(C->nG[s], GROWS * GGROUPS); ++b) iG.push_back(make_int2(s, b));
+      for (int b = 0; b < (int)cdiv(C->nG[s], AROWS); ++b) iR.push_back(make_int2(s, b));
+      if (C->nc[s] > 0) {
+        const int nch_s = (int)cdiv(C->nG[s], PHIT_ROWS);
+        for (int b = 0; b < nch_s; ++b) iP.push_back(make_int2(s, b));
+        for (int c = 0; c < C->nc[s]; ++c) cn[C->offC[s] + c] = nch_s;
+      }
+    }
+    C->n_itI = (int)iI.size(); C->n_itG = (int)iG.size();
+    C->n_itP = (int)iP.size(); C->n_itR = (int)iR.size();
+    C->itI.upload(iI); C->itG.upload(iG); C->itP.upload(iP); C->itR.upload(iR);
+    C->cnch.upload(cn);
+  }
+
   // device copies of sizes and maps
   C->d_nI.upload(C->nI); C->d_nG.upload(C->nG); C->d_nr.upload(C->nr); C->d_nv.upload(C->nv);
   C->d_na.upload(C->na); C->d_nc.upload(C->nc); C->d_ns.upload(C->ns);
@@ -1127,13 +1163,17 @@ static void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) 
   const size_t smI = (size_t)round_up(std::max(C->maxI, 4), 4) * sizeof(T);
   gather_kernel<<<cdiv(std::max<int64_t>(C->totI, 1), 256), 256, 0, s>>>(C->gdofI.p, C->totI, r, C->xI.p);
   CB_LAUNCH();
-  apply_interior_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), GROWS * GGROUPS), nsub), 256, smI, s>>>(
-      C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, Aloc, C->xI.p, C->u0.p);
-  CB_LAUNCH();
-  if (C->maxG > 0) {
-    apply_gi_kernel<T><<<dim3(cdiv(C->maxG, GROWS * GGROUPS), nsub), 256, smI, s>>>(
-        C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, Aloc, C->u0.p, C->hG.p);
+  if (C->n_itI > 0) {
+    apply_interior_kernel<T><<<C->n_itI, 256, smI, s>>>(
+        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, Aloc, C->xI.p, C->u0.p);
     CB_LAUNCH();
+  }
+  if (C->maxG > 0) {
+    if (C->n_itG > 0) {
+      apply_gi_kernel<T><<<C->n_itG, 256, smI, s>>>(
+          C->itG.p, C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, Aloc, C->u0.p, C->hG.p);
+      CB_LAUNCH();
+    }
   }
   if (C->n_if > 0) {
     assemble_g_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
@@ -1141,18 +1181,22 @@ static void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) 
     CB_LAUNCH();
     restrict_kernel<<<cdiv(C->totG, 256), 256, 0, s>>>(C->gam_if.p, C->Dg.p, C->totG, C->gI.p, gl);
     CB_LAUNCH();
-    apply_local_kernel<T><<<dim3(cdiv(C->maxG, GROWS * GGROUPS), nsub), 256,
-                            (size_t)round_up(std::max(C->maxR, 4), 4) * sizeof(T), s>>>(
-        C->d_nG.p, C->d_nr.p, C->d_offS.p, C->d_ldS.p, C->d_offGam.p, Sw, gl, C->wG.p);
-    CB_LAUNCH();
+    if (C->n_itG > 0) {
+      apply_local_kernel<T><<<C->n_itG, 256,
+                              (size_t)round_up(std::max(C->maxR, 4), 4) * sizeof(T), s>>>(
+          C->itG.p, C->d_nG.p, C->d_nr.p, C->d_offS.p, C->d_ldS.p, C->d_offGam.p, Sw, gl, C->wG.p);
+      CB_LAUNCH();
+    }
     if (C->n_pi > 0) {
       const int nch = (int)cdiv(C->maxG, PHIT_ROWS);
-      apply_phit_kernel<T><<<dim3(nch, nsub), 256, 0, s>>>(C->d_nG.p, C->d_nc.p, C->d_offPhi.p,
-                                                          C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, Phi,
-                                                          gl, C->cl.p, nch);
-      CB_LAUNCH();
+      if (C->n_itP > 0) {
+        apply_phit_kernel<T><<<C->n_itP, 256, 0, s>>>(C->itP.p, C->d_nG.p, C->d_nc.p, C->d_offPhi.p,
+                                                            C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, Phi,
+                                                            gl, C->cl.p, nch);
+        CB_LAUNCH();
+      }
       coarse_rhs_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, C->cl.p, nch,
-                                                           C->rc.p);
+                                                           C->cnch.p, C->rc.p);
       CB_LAUNCH();
       if (C->next) {
         bddc_run_apply(C->next.get(), C->rc.p, C->uc.p, s);
@@ -1162,19 +1206,23 @@ static void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) 
         CB_LAUNCH();
       }
     }
-    apply_prolong_kernel<T><<<dim3(cdiv(C->maxG, AROWS), nsub), 256, 0, s>>>(
-        C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, C->gprim.p, Phi,
-        C->uc.p, C->wG.p, C->Dg.p, C->yG.p);
-    CB_LAUNCH();
+    if (C->n_itR > 0) {
+      apply_prolong_kernel<T><<<C->n_itR, 256, 0, s>>>(
+          C->itR.p, C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, C->gprim.p, Phi,
+          C->uc.p, C->wG.p, C->Dg.p, C->yG.p);
+      CB_LAUNCH();
+    }
     average_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
                                                      C->yG.p, z, C->zl.p);
     CB_LAUNCH();
   }
-  apply_extend_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), GROWS * GGROUPS), nsub), 256,
-                           (size_t)round_up(std::max(C->maxG, 4), 4) * sizeof(T), s>>>(
-      C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, Aloc,
-      C->zl.p, C->u0.p, z);
-  CB_LAUNCH();
+  if (C->n_itI > 0) {
+    apply_extend_kernel<T><<<C->n_itI, 256,
+                             (size_t)round_up(std::max(C->maxG, 4), 4) * sizeof(T), s>>>(
+        C->itI.p, C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p,
+        Aloc, C->zl.p, C->u0.p, z);
+    CB_LAUNCH();
+  }
 }
 
 void bddc_run_apply(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
@@ -1227,13 +1275,17 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
   const size_t smI = (size_t)round_up(std::max(C->maxI, 4), 4) * sizeof(T);
   gather_kernel<<<cdiv(std::max<int64_t>(C->totI, 1), 256), 256, 0, s>>>(C->gdofI.p, C->totI, r, w.xI);
   CB_LAUNCH();
-  apply_interior_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), GROWS * GGROUPS), nsub), 256, smI, s>>>(
-      C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, Aloc, w.xI, w.u0);
-  CB_LAUNCH();
-  if (C->maxG > 0) {
-    apply_gi_kernel<T><<<dim3(cdiv(C->maxG, GROWS * GGROUPS), nsub), 256, smI, s>>>(
-        C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, Aloc, w.u0, w.hG);
+  if (C->n_itI > 0) {
+    apply_interior_kernel<T><<<C->n_itI, 256, smI, s>>>(
+        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, Aloc, w.xI, w.u0);
     CB_LAUNCH();
+  }
+  if (C->maxG > 0) {
+    if (C->n_itG > 0) {
+      apply_gi_kernel<T><<<C->n_itG, 256, smI, s>>>(
+          C->itG.p, C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, Aloc, w.u0, w.hG);
+      CB_LAUNCH();
+    }
   }
   if (C->n_if > 0) {
     assemble_g_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
@@ -1241,18 +1293,22 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
     CB_LAUNCH();
     restrict_kernel<<<cdiv(C->totG, 256), 256, 0, s>>>(C->gam_if.p, C->Dg.p, C->totG, w.gI, w.gl);
     CB_LAUNCH();
-    apply_local_kernel<T><<<dim3(cdiv(C->maxG, GROWS * GGROUPS), nsub), 256,
-                            (size_t)round_up(std::max(C->maxR, 4), 4) * sizeof(T), s>>>(
-        C->d_nG.p, C->d_nr.p, C->d_offS.p, C->d_ldS.p, C->d_offGam.p, Sw, w.gl, w.wG);
-    CB_LAUNCH();
+    if (C->n_itG > 0) {
+      apply_local_kernel<T><<<C->n_itG, 256,
+                              (size_t)round_up(std::max(C->maxR, 4), 4) * sizeof(T), s>>>(
+          C->itG.p, C->d_nG.p, C->d_nr.p, C->d_offS.p, C->d_ldS.p, C->d_offGam.p, Sw, w.gl, w.wG);
+      CB_LAUNCH();
+    }
     if (C->n_pi > 0) {
       const int nch = (int)cdiv(C->maxG, PHIT_ROWS);
-      apply_phit_kernel<T><<<dim3(nch, nsub), 256, 0, s>>>(C->d_nG.p, C->d_nc.p, C->d_offPhi.p,
-                                                          C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, Phi,
-                                                          w.gl, w.cl, nch);
-      CB_LAUNCH();
+      if (C->n_itP > 0) {
+        apply_phit_kernel<T><<<C->n_itP, 256, 0, s>>>(C->itP.p, C->d_nG.p, C->d_nc.p, C->d_offPhi.p,
+                                                            C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, Phi,
+                                                            w.gl, w.cl, nch);
+        CB_LAUNCH();
+      }
       coarse_rhs_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, w.cl, nch,
-                                                           w.rc);
+                                                           C->cnch.p, w.rc);
       CB_LAUNCH();
       if (C->next) {
         // the level-2 context uses its own work vectors, allocated at setup
@@ -1262,19 +1318,23 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
         CB_LAUNCH();
       }
     }
-    apply_prolong_kernel<T><<<dim3(cdiv(C->maxG, AROWS), nsub), 256, 0, s>>>(
-        C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, C->gprim.p, Phi,
-        w.uc, w.wG, C->Dg.p, w.yG);
-    CB_LAUNCH();
+    if (C->n_itR > 0) {
+      apply_prolong_kernel<T><<<C->n_itR, 256, 0, s>>>(
+          C->itR.p, C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, C->gprim.p, Phi,
+          w.uc, w.wG, C->Dg.p, w.yG);
+      CB_LAUNCH();
+    }
     average_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
                                                      w.yG, z, w.zl);
     CB_LAUNCH();
   }
-  apply_extend_kernel<T><<<dim3(cdiv(std::max(C->maxI, 1), GROWS * GGROUPS), nsub), 256,
-                           (size_t)round_up(std::max(C->maxG, 4), 4) * sizeof(T), s>>>(
-      C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p, Aloc,
-      w.zl, w.u0, z);
-  CB_LAUNCH();
+  if (C->n_itI > 0) {
+    apply_extend_kernel<T><<<C->n_itI, 256,
+                             (size_t)round_up(std::max(C->maxG, 4), 4) * sizeof(T), s>>>(
+        C->itI.p, C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p,
+        Aloc, w.zl, w.u0, z);
+    CB_LAUNCH();
+  }
 }
 
 }  // namespace

@@ -36,6 +36,10 @@ struct bddc_ctx {
   cbddc::DVec<int> ce_key, ce_ptr, ce_src; // coarse matrix entries
   int64_t n_ce = 0;
   cbddc::DVec<double> Sc, ScX, ScY, ScP;   // coarse matrix (inverted in place)
+  // work items {subdomain, row block} of the batched apply kernels
+  cbddc::DVec<int2> itI, itG, itP, itR;
+  int n_itI = 0, n_itG = 0, n_itP = 0, n_itR = 0;
+  cbddc::DVec<int> cnch;                   // coarse-restriction chunks per local primal entry
   // apply work vectors
   cbddc::DVec<double> u0, hG, gI, wG, cl, rc, uc, yG, xI, zl;
   // sweep descriptors and GEMM problem lists

@@ -475,7 +475,7 @@ uint64_t cbddc_kernel_launches(void) { return g_launches.load(); }
 
 int cbddc_timer_start(int kernel_class) {
   return guard([&] {
-    CB_CHECK(kernel_class >= 0 && kernel_class <= CBDDC_TIMER_SPMV, CBDDC_EINVAL, "bad kernel class");
+    CB_CHECK(kernel_class >= 0 && kernel_class <= CBDDC_TIMER_ORTH, CBDDC_EINVAL, "bad kernel class");
     g_timer.kernel_class = kernel_class;
     g_timer.used = 0;
     g_timer.depth = 0;

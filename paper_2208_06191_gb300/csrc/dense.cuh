@@ -32,18 +32,22 @@ template <typename T> struct GemmCfg;
 template <> struct GemmCfg<float> { static constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8; };
 template <> struct GemmCfg<double> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
 
-// C = alpha op(A) op(B) + beta C for every problem; grid (tilesN, tilesM, nprob).
+// C = alpha op(A) op(B) + beta C for every problem; one CTA per output
+// tile, the tiles listed as {problem, tile row, tile column} (only tiles
+// that exist, so problems of uneven size launch no empty CTAs).
 // Row-major storage; op(A) = A^T reads A as K x M, op(B) = B^T reads B as N x K.
-// A problem with K == 0 leaves C untouched (callers use beta = 1 there).
+// A problem with K == 0 has no tiles and leaves C untouched (callers use
+// beta = 1 there).
 template <typename T, bool TA, bool TB>
 __global__ void __launch_bounds__((GemmCfg<T>::BM / GemmCfg<T>::TM) * (GemmCfg<T>::BN / GemmCfg<T>::TN))
-gemm_grouped_kernel(const GemmProb* __restrict__ probs, const T* __restrict__ A,
+gemm_grouped_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ probs, const T* __restrict__ A,
                     const T* __restrict__ B, T* __restrict__ C, T alpha, T beta) {
   constexpr int BM = GemmCfg<T>::BM, BN = GemmCfg<T>::BN, BK = GemmCfg<T>::BK;
   constexpr int TM = GemmCfg<T>::TM, TN = GemmCfg<T>::TN;
   constexpr int NT = (BM / TM) * (BN / TN);
-  const GemmProb p = probs[blockIdx.z];
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int4 tl = tiles[blockIdx.x];
+  const GemmProb p = probs[tl.x];
+  const int m0 = tl.y * BM, n0 = tl.z * BN;
   if (m0 >= p.M || n0 >= p.N || p.K <= 0) return;
   __shared__ T As[BK][BM + 4];
   __shared__ T Bs[BK][BN + 4];
@@ -147,14 +151,15 @@ __device__ inline double2 vmask<double>(double2 v, int valid) {
 
 template <typename T>
 __global__ void __launch_bounds__(256, 2)
-gemm_nn_kernel(const GemmProb* __restrict__ probs, const T* __restrict__ A, const T* __restrict__ B,
-               T* __restrict__ C, T alpha, T beta) {
+gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ probs, const T* __restrict__ A,
+               const T* __restrict__ B, T* __restrict__ C, T alpha, T beta) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
   constexpr int BM = 32 * W, BN = 32 * W, BK = 8;
   constexpr int HALF = BM / 2;
-  const GemmProb p = probs[blockIdx.z];
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int4 tl = tiles[blockIdx.x];
+  const GemmProb p = probs[tl.x];
+  const int m0 = tl.y * BM, n0 = tl.z * BN;
   if (m0 >= p.M || n0 >= p.N || p.K <= 0) return;
   __shared__ __align__(16) T As[2][BK][BM + 4];
   __shared__ __align__(16) T Bs[2][BK][BN + 4];
@@ -262,54 +267,61 @@ gemm_nn_kernel(const GemmProb* __restrict__ probs, const T* __restrict__ A, cons
   }
 }
 
-// A list of grouped GEMM problems with its host-side totals.
+// Output tile edge of both GEMM kernels: 128 for FP32, 64 for FP64.
+inline int gemm_tile(size_t esize) { return esize == 4 ? 128 : 64; }
+static_assert(GemmCfg<float>::BM == 128 && GemmCfg<float>::BN == 128 && 32 * VecT<float>::W == 128, "tile");
+static_assert(GemmCfg<double>::BM == 64 && GemmCfg<double>::BN == 64 && 32 * VecT<double>::W == 64, "tile");
+
+// A list of grouped GEMM problems with its output tiles and host-side totals.
 struct GemmList {
   DVec<GemmProb> d;
-  int n = 0, maxM = 0, maxN = 0;
+  DVec<int4> tiles;  // {problem, tile row, tile column, 0}
+  int n = 0, ntiles = 0;
   double flops = 0.0, bytes = 0.0;
   bool fast = true;  // every problem meets the vector-load alignment
   void set(const std::vector<GemmProb>& v, size_t esize, bool ta = false) {
     n = (int)v.size();
-    maxM = maxN = 0;
     flops = bytes = 0.0;
     const int w = (int)(16 / esize);
+    const int tile = gemm_tile(esize);
     fast = !ta;
-    for (const GemmProb& q : v) {
+    std::vector<int4> t;
+    for (int i = 0; i < n; ++i) {
+      const GemmProb& q = v[i];
       if (q.M <= 0 || q.N <= 0 || q.K <= 0) continue;
-      maxM = std::max(maxM, q.M);
-      maxN = std::max(maxN, q.N);
       flops += 2.0 * q.M * q.N * q.K;
       bytes += (double)esize * (2.0 * q.M * q.N + (double)q.K * (q.M + q.N));
       if (q.a % w || q.b % w || q.lda % w || q.ldb % w) fast = false;
+      for (int tm = 0; tm < (int)cdiv(q.M, tile); ++tm)
+        for (int tn = 0; tn < (int)cdiv(q.N, tile); ++tn) t.push_back(make_int4(i, tm, tn, 0));
     }
+    ntiles = (int)t.size();
     d.upload(v);
+    tiles.upload(t);
   }
 };
 
 template <typename T, bool TA, bool TB>
-void launch_gemm(const GemmProb* probs, int nprob, int maxM, int maxN, const T* A, const T* B, T* C,
+void launch_gemm(const int4* tiles, int ntiles, const GemmProb* probs, const T* A, const T* B, T* C,
                  T alpha, T beta, cudaStream_t s, bool fast = false) {
-  if (nprob == 0 || maxM <= 0 || maxN <= 0) return;
+  if (ntiles == 0) return;
   if (!TA && !TB && fast) {
-    constexpr int BMf = 32 * VecT<T>::W;
-    dim3 grid(cdiv(maxN, BMf), cdiv(maxM, BMf), nprob);
-    gemm_nn_kernel<T><<<grid, 256, 0, s>>>(probs, A, B, C, alpha, beta);
+    gemm_nn_kernel<T><<<ntiles, 256, 0, s>>>(tiles, probs, A, B, C, alpha, beta);
     CB_LAUNCH();
     return;
   }
   constexpr int BM = GemmCfg<T>::BM, BN = GemmCfg<T>::BN;
   constexpr int NT = (BM / GemmCfg<T>::TM) * (BN / GemmCfg<T>::TN);
-  dim3 grid(cdiv(maxN, BN), cdiv(maxM, BM), nprob);
-  gemm_grouped_kernel<T, TA, TB><<<grid, NT, 0, s>>>(probs, A, B, C, alpha, beta);
+  gemm_grouped_kernel<T, TA, TB><<<ntiles, NT, 0, s>>>(tiles, probs, A, B, C, alpha, beta);
   CB_LAUNCH();
 }
 
 // Launch of a whole list (timed as a setup GEMM when the timer follows them).
 template <typename T, bool TA, bool TB>
 void launch_list(const GemmList& g, const T* A, const T* B, T* C, T alpha, T beta, cudaStream_t s) {
-  if (g.n == 0 || g.maxM == 0) return;
+  if (g.ntiles == 0) return;
   timer_begin(CBDDC_TIMER_SWEEP_GEMM, s);
-  launch_gemm<T, TA, TB>(g.d.p, g.n, g.maxM, g.maxN, A, B, C, alpha, beta, s, g.fast);
+  launch_gemm<T, TA, TB>(g.tiles.p, g.ntiles, g.d.p, A, B, C, alpha, beta, s, g.fast);
   timer_end(CBDDC_TIMER_SWEEP_GEMM, s, g.flops, g.bytes);
 }
 

@@ -16,7 +16,7 @@ namespace cbddc {
 
 namespace {
 
-constexpr int DOT_ROWS = 512;   // rows per CTA in the block dot products
+constexpr int DOT_THREADS = 256;
 constexpr int MAXV = 128;       // maximum Krylov vectors per dot launch
 
 __device__ inline double wsum(double v) {
@@ -24,12 +24,15 @@ __device__ inline double wsum(double v) {
   return v;
 }
 
-// Block dot products with a last-block reduction: every CTA writes the
-// partial sums of its DOT_ROWS rows to partial[blockIdx][j]; the CTA that
-// finishes last (atomic ticket) sums them over all CTAs in CTA order, so the
-// result does not depend on scheduling.  Optionally the rows of w are first
-// updated, w -= V hin, which fuses the second Gram-Schmidt pass (or the
-// final update) with the next reduction.
+// Block dot products with a last-block reduction.  Each CTA owns a tile of
+// 256 * RPT consecutive rows: it first forms its rows of w (optionally
+// w -= V hin, which fuses the update of one Gram-Schmidt pass with the dots
+// of the next), keeps them in shared memory, then every warp takes whole
+// columns of V and reads the tile's rows of that column with all 32 lanes
+// (coalesced, 8 * RPT independent loads per lane), so the reduction costs
+// one warp sum per column and CTA.  The CTA that finishes last (atomic
+// ticket) sums the per-CTA partials in CTA order, so results do not depend
+// on scheduling.
 struct DotArgs {
   const double* V;      // nvec columns of length n, stride ldv
   int64_t ldv;
@@ -44,64 +47,99 @@ struct DotArgs {
   const int* done;      // skip everything once GMRES has converged
 };
 
-__device__ inline void last_block_sum(const DotArgs& a, int nout, bool& is_last) {
+__device__ inline void last_block_sum(const DotArgs& a, int nout) {
   __shared__ bool last;
+  __shared__ double half[MAXV];
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
   __syncthreads();
-  is_last = last;
   if (!last) return;
-  for (int j = threadIdx.x; j < nout; j += blockDim.x) {
-    double sum = 0.0;
-    for (unsigned c = 0; c < gridDim.x; ++c) sum += __ldcg(a.partial + (int64_t)c * MAXV + j);
-    a.out[j] = sum;
+  // two threads per output: CTAs [0, G/2) and [G/2, G), four accumulators
+  // each in a fixed order, then the halves added in a fixed order
+  const int j = threadIdx.x & (MAXV - 1), side = threadIdx.x >> 7;
+  const unsigned G = gridDim.x, mid = G / 2;
+  const unsigned c0 = side ? mid : 0u, c1 = side ? G : mid;
+  double s4[4] = {0.0, 0.0, 0.0, 0.0};
+  if (j < nout) {
+    unsigned c = c0;
+    for (; c + 4 <= c1; c += 4) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s4[q] += __ldcg(a.partial + (int64_t)(c + q) * MAXV + j);
+    }
+    for (; c < c1; ++c) s4[0] += __ldcg(a.partial + (int64_t)c * MAXV + j);
   }
+  const double sum = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+  if (side == 1 && j < nout) half[j] = sum;
+  __syncthreads();
+  if (side == 0 && j < nout) a.out[j] = sum + half[j];
   if (threadIdx.x == 0) *a.ticket = 0u;
   __threadfence();
 }
 
-__global__ void __launch_bounds__(256) fused_dots_kernel(DotArgs a) {
+template <int RPT>
+__global__ void __launch_bounds__(DOT_THREADS) fused_dots_kernel(DotArgs a) {
   if (a.done && *a.done) return;
-  __shared__ double red[8][MAXV];
+  constexpr int TILE = DOT_THREADS * RPT;
+  __shared__ double ws[TILE];
   __shared__ double hs[MAXV];
-  const int64_t r0 = (int64_t)blockIdx.x * DOT_ROWS;
+  __shared__ double red[DOT_THREADS / 32];
+  const int64_t r0 = (int64_t)blockIdx.x * TILE;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int R = DOT_ROWS / 256;
-  double wv[R];
-  if (a.hin) {
-    for (int j = tid; j < a.nvec; j += 256) hs[j] = a.hin[j];
-    __syncthreads();
-  }
+  const int rows = (int)min((int64_t)TILE, a.n - r0);
+  // rows of w (updated when hin is given)
+  double x[RPT];
 #pragma unroll
-  for (int t = 0; t < R; ++t) {
-    const int64_t row = r0 + tid + 256 * t;
-    double x = row < a.n ? a.w[row] : 0.0;
-    if (a.hin && row < a.n) {
-      for (int j = 0; j < a.nvec; ++j) x -= a.V[(int64_t)j * a.ldv + row] * hs[j];
-      a.w[row] = x;
+  for (int t = 0; t < RPT; ++t) {
+    const int q = tid + DOT_THREADS * t;
+    x[t] = q < rows ? a.w[r0 + q] : 0.0;
+  }
+  if (a.hin) {
+    for (int j = tid; j < a.nvec; j += DOT_THREADS) hs[j] = a.hin[j];
+    __syncthreads();
+    for (int j = 0; j < a.nvec; ++j) {
+      const double hj = hs[j];
+      const double* Vj = a.V + (int64_t)j * a.ldv + r0;
+#pragma unroll
+      for (int t = 0; t < RPT; ++t) {
+        const int q = tid + DOT_THREADS * t;
+        if (q < rows) x[t] -= Vj[q] * hj;
+      }
     }
-    wv[t] = x;
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+      const int q = tid + DOT_THREADS * t;
+      if (q < rows) a.w[r0 + q] = x[t];
+    }
   }
   const int nout = a.self_norm ? 1 : a.nvec;
-  for (int j = 0; j < nout; ++j) {
+  if (a.self_norm) {
     double acc = 0.0;
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      const int64_t row = r0 + tid + 256 * t;
-      if (row < a.n) acc += (a.self_norm ? wv[t] : a.V[(int64_t)j * a.ldv + row]) * wv[t];
-    }
+    for (int t = 0; t < RPT; ++t) acc += x[t] * x[t];
     acc = wsum(acc);
-    if (lane == 0) red[warp][j] = acc;
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double sm = 0.0;
+      for (int q = 0; q < DOT_THREADS / 32; ++q) sm += red[q];
+      a.partial[(int64_t)blockIdx.x * MAXV] = sm;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) ws[tid + DOT_THREADS * t] = x[t];
+    __syncthreads();
+    for (int j = warp; j < a.nvec; j += DOT_THREADS / 32) {
+      const double* Vj = a.V + (int64_t)j * a.ldv + r0;
+      double acc = 0.0;
+#pragma unroll 8
+      for (int q = lane; q < TILE; q += 32)
+        if (q < rows) acc += Vj[q] * ws[q];
+      acc = wsum(acc);
+      if (lane == 0) a.partial[(int64_t)blockIdx.x * MAXV + j] = acc;
+    }
   }
-  __syncthreads();
-  for (int j = tid; j < nout; j += 256) {
-    double sm = 0.0;
-    for (int q = 0; q < 8; ++q) sm += red[q][j];
-    a.partial[(int64_t)blockIdx.x * MAXV + j] = sm;
-  }
-  bool last;
-  last_block_sum(a, nout, last);
+  last_block_sum(a, nout);
 }
 
 // Column j of the Hessenberg matrix from h1 + h2 (the two CGS passes) and
@@ -192,8 +230,8 @@ __global__ void cycle_start_kernel(const double* __restrict__ rn2, double* __res
 }  // namespace
 
 void Gmres::ensure_small(int64_t n_) {
-  if (partial.p && nchunks == (int)cdiv(n_, DOT_ROWS)) return;
-  nchunks = (int)cdiv(n_, DOT_ROWS);
+  if (partial.p && nchunks == (int)cdiv(n_, DOT_THREADS)) return;
+  nchunks = (int)cdiv(n_, DOT_THREADS);   // CTAs at one row per thread (the most)
   partial.alloc((size_t)nchunks * MAXV);
   ticket.alloc(1);
   CB_CUDA(cudaMemset(ticket.p, 0, sizeof(unsigned)));
@@ -231,7 +269,20 @@ Gmres::~Gmres() {
 static void fused_dots(Gmres& G, const double* V, int64_t ldv, int nvec, double* w, int64_t n,
                        const double* hin, int self_norm, double* out, const int* done, cudaStream_t s) {
   DotArgs a{V, ldv, nvec, w, n, hin, self_norm, G.partial.p, G.ticket.p, out, done};
-  fused_dots_kernel<<<(unsigned)cdiv(n, DOT_ROWS), 256, 0, s>>>(a);
+  // rows per thread: the largest of 16, 8, 4, 2, 1 that still gives two
+  // CTAs per SM (fewer CTAs also shorten the last CTA's reduction)
+  const int64_t sms2 = 2 * 152;
+  if (n >= 16 * DOT_THREADS * sms2) {
+    fused_dots_kernel<16><<<(unsigned)cdiv(n, 16 * DOT_THREADS), DOT_THREADS, 0, s>>>(a);
+  } else if (n >= 8 * DOT_THREADS * sms2) {
+    fused_dots_kernel<8><<<(unsigned)cdiv(n, 8 * DOT_THREADS), DOT_THREADS, 0, s>>>(a);
+  } else if (n >= 4 * DOT_THREADS * sms2) {
+    fused_dots_kernel<4><<<(unsigned)cdiv(n, 4 * DOT_THREADS), DOT_THREADS, 0, s>>>(a);
+  } else if (n >= 2 * DOT_THREADS * sms2) {
+    fused_dots_kernel<2><<<(unsigned)cdiv(n, 2 * DOT_THREADS), DOT_THREADS, 0, s>>>(a);
+  } else {
+    fused_dots_kernel<1><<<(unsigned)cdiv(n, DOT_THREADS), DOT_THREADS, 0, s>>>(a);
+  }
   CB_LAUNCH();
 }
 
@@ -280,6 +331,7 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
       double* h1 = G.h.p;
       double* h2 = G.h.p + MAXV;
       double* wn2 = G.h.p + 2 * MAXV;
+      timer_begin(CBDDC_TIMER_ORTH, s);
       fused_dots(G, G.V.p, n, j + 1, G.w.p, n, nullptr, 0, h1, done, s);
       fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h1, 0, h2, done, s);
       fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h2, 1, wn2, done, s);
@@ -288,6 +340,10 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
       CB_LAUNCH();
       scale_kernel<<<nb, 256, 0, s>>>(G.w.p, G.V.p + (int64_t)(j + 1) * n, n, G.scal.p, 1, done);
       CB_LAUNCH();
+      // algorithmic traffic: V read three times (dots, update + dots,
+      // update), w read 3x / written 2x, v_{j+1} written
+      timer_end(CBDDC_TIMER_ORTH, s, 6.0 * (j + 1) * (double)n,
+                8.0 * (double)n * (3.0 * (j + 1) + 6.0));
       CB_CUDA(cudaMemcpyAsync(hflags, done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
       CB_CUDA(cudaStreamSynchronize(s));
       ++total;
