@@ -1041,7 +1041,7 @@ static void run_sweep(const DVec<SweepDesc>& desc, int nmat, const std::vector<G
                       int maxRows, int maxCols, T* mat, T* X, T* Y, T* Pbuf, int* status, double tol,
                       cudaStream_t s) {
   for (int k = 0; k < (int)lists.size(); ++k) {
-    sweep_diag_kernel<T><<<nmat, SWEEP_NB, 0, s>>>(desc.p, k, mat, Pbuf, status, tol);
+    sweep_diag_kernel<T><<<nmat, DIAG_THREADS, 0, s>>>(desc.p, k, mat, Pbuf, status, tol);
     CB_LAUNCH();
     dim3 grid(cdiv(std::max(maxRows, maxCols), 64), nmat);
     sweep_panel_kernel<T><<<grid, 256, 0, s>>>(desc.p, k, mat, Pbuf, X, Y);

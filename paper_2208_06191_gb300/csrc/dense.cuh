@@ -155,8 +155,12 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
                const T* __restrict__ B, T* __restrict__ C, T alpha, T beta) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
-  constexpr int BM = 32 * W, BN = 32 * W, BK = 8;
+  constexpr int BM = 32 * W, BN = 32 * W, BK = 16;
   constexpr int HALF = BM / 2;
+  // each thread moves two vectors of A (rows am, am + BM/2) and two of B
+  // (rows bk, bk + 8) per BK step; the next step's four vectors are in
+  // flight while the current step's FMAs run
+  static_assert(BM * BK == 2 * 256 * W && BK * BN == 2 * 256 * W, "two vectors per thread");
   const int4 tl = tiles[blockIdx.x];
   const GemmProb p = probs[tl.x];
   const int m0 = tl.y * BM, n0 = tl.z * BN;
@@ -165,54 +169,59 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
   __shared__ __align__(16) T Bs[2][BK][BN + 4];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  // global load coordinates (one vector of A and one of B per thread)
+  // global load coordinates
   const int am = tid / (BK / W), ak = (tid % (BK / W)) * W;
   const int bk = tid / (BN / W), bn = (tid % (BN / W)) * W;
   const T* Ab = A + p.a + (int64_t)(m0 + am) * p.lda + ak;
   const T* Bb = B + p.b + (int64_t)bk * p.ldb + n0 + bn;
-  const bool a_row = (m0 + am) < p.M;
   const int b_col_valid = p.N - (n0 + bn);
-  auto load_a = [&](int k0) -> V {
+  auto load_a = [&](int k0, int h) -> V {
     V v;
     const int valid = p.K - (k0 + ak);
-    if (a_row && valid > 0) {
-      v = *reinterpret_cast<const V*>(Ab + k0);
+    if ((m0 + am + h * HALF) < p.M && valid > 0) {
+      v = *reinterpret_cast<const V*>(Ab + (int64_t)h * HALF * p.lda + k0);
       v = vmask<T>(v, valid);
     } else {
       v = vmask<T>(V{}, 0);
     }
     return v;
   };
-  auto load_b = [&](int k0) -> V {
+  auto load_b = [&](int k0, int h) -> V {
     V v;
-    if ((k0 + bk) < p.K && b_col_valid > 0) {
-      v = *reinterpret_cast<const V*>(Bb + (int64_t)k0 * p.ldb);
+    if ((k0 + bk + 8 * h) < p.K && b_col_valid > 0) {
+      v = *reinterpret_cast<const V*>(Bb + (int64_t)(k0 + 8 * h) * p.ldb);
       v = vmask<T>(v, b_col_valid);
     } else {
       v = vmask<T>(V{}, 0);
     }
     return v;
   };
+  auto stage = [&](int b, const V* ra, const V* rb) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      T tmp[W];
+      vstore4<T>(tmp, ra[h]);
+#pragma unroll
+      for (int q = 0; q < W; ++q) As[b][ak + q][am + h * HALF] = tmp[q];
+      *reinterpret_cast<V*>(&Bs[b][bk + 8 * h][bn]) = rb[h];
+    }
+  };
   T acc[2 * W][2 * W];
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i)
 #pragma unroll
     for (int j = 0; j < 2 * W; ++j) acc[i][j] = T(0);
-  V ra = load_a(0), rb = load_b(0);
+  V ra[2] = {load_a(0, 0), load_a(0, 1)}, rb[2] = {load_b(0, 0), load_b(0, 1)};
   int buf = 0;
-  {
-    T tmp[W];
-    vstore4<T>(tmp, ra);
-#pragma unroll
-    for (int q = 0; q < W; ++q) As[0][ak + q][am] = tmp[q];
-    *reinterpret_cast<V*>(&Bs[0][bk][bn]) = rb;
-  }
+  stage(0, ra, rb);
   __syncthreads();
   for (int k0 = 0; k0 < p.K; k0 += BK) {
     const bool more = (k0 + BK) < p.K;
     if (more) {
-      ra = load_a(k0 + BK);
-      rb = load_b(k0 + BK);
+      ra[0] = load_a(k0 + BK, 0);
+      ra[1] = load_a(k0 + BK, 1);
+      rb[0] = load_b(k0 + BK, 0);
+      rb[1] = load_b(k0 + BK, 1);
     }
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
@@ -227,11 +236,7 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
         for (int j = 0; j < 2 * W; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     if (more) {
-      T tmp[W];
-      vstore4<T>(tmp, ra);
-#pragma unroll
-      for (int q = 0; q < W; ++q) As[buf ^ 1][ak + q][am] = tmp[q];
-      *reinterpret_cast<V*>(&Bs[buf ^ 1][bk][bn]) = rb;
+      stage(buf ^ 1, ra, rb);
       __syncthreads();
       buf ^= 1;
     }
@@ -337,85 +342,86 @@ struct SweepDesc {
 };
 
 // P = inverse of the kb x kb diagonal block of pivot step k, by Gauss-Jordan
-// in the operator precision T.  Thread c of the 64-thread CTA keeps column c
-// in registers (the pivot loop is fully unrolled so the register index is
-// static); at pivot j the owner of column j publishes it to shared memory
-// (double-buffered, so one barrier per pivot suffices) and every thread
-// updates its own column:
-//   a[j][c] <- a[j][c] / p,  a[i][c] <- a[i][c] - a[i][j] a[j][c]  (c != j),
+// in the operator precision T on a shared-memory copy of the block.
+// Thread (c, g) = (tid % 64, tid / 64) owns rows [16 g, 16 g + 16) of
+// column c, so the 256 threads keep all four SM sub-partitions busy (the
+// FP64 case of the coarse matrix needs every FP64 unit).  At pivot j each
+// thread first reads the pivot-row entry of its column and the column-j
+// entries of its rows, then, after a barrier, updates its entries:
+//   a[j][c] <- a[j][c] / p,  a[i][c] <- a[i][c] - a[i][j] a[j][c] / p (c != j),
 //   a[i][j] <- -a[i][j] / p, a[j][j] <- 1 / p.
+constexpr int DIAG_THREADS = 256;
 template <typename T>
-__global__ void __launch_bounds__(SWEEP_NB)
+__global__ void __launch_bounds__(DIAG_THREADS)
 sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat, T* __restrict__ Pbuf,
                   int* __restrict__ status, double tol) {
   constexpr int NB = SWEEP_NB;
-  __shared__ T colj[2][NB];
+  constexpr int RG = NB / (DIAG_THREADS / NB);  // rows per thread
+  __shared__ T a[NB][NB + 1];
   __shared__ double piv_scale;
   __shared__ int bad;
   const SweepDesc d = desc[blockIdx.x];
   const int k0 = k * NB;
   if (k0 >= d.p) return;
   const int kb = min(NB, d.p - k0);
-  const int c = threadIdx.x;
+  const int tid = threadIdx.x;
+  const int c = tid % NB, r0 = (tid / NB) * RG;
   const T* A = mat + d.off + (int64_t)k0 * d.ld + k0;
-  T a[NB];
-#pragma unroll
-  for (int i = 0; i < NB; ++i) a[i] = (i < kb && c < kb) ? A[(int64_t)i * d.ld + c] : T(0);
-  if (c == 0) { bad = 0; piv_scale = 0.0; }
+  for (int t = tid; t < NB * NB; t += DIAG_THREADS) {
+    const int i = t / NB, cc = t % NB;
+    a[i][cc] = (i < kb && cc < kb) ? A[(int64_t)i * d.ld + cc] : T(0);
+  }
+  if (tid == 0) bad = 0;
   __syncthreads();
-  // scale of the pivots: largest |diagonal| of the block (thread c owns a[c][c])
-  {
+  // scale of the pivots: largest |diagonal| of the block
+  if (tid < 32) {
     double dv = 0.0;
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-      if (i == c && c < kb) dv = fabs((double)a[i]);
+    for (int i = tid; i < kb; i += 32) dv = fmax(dv, fabs((double)a[i][i]));
     for (int o = 16; o > 0; o >>= 1) dv = fmax(dv, __shfl_xor_sync(0xffffffffu, dv, o));
-    if ((c & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(&piv_scale),
-                                 __double_as_longlong(dv));  // non-negative doubles order as integers
+    if (tid == 0) piv_scale = dv;
   }
   __syncthreads();
   const double scale = piv_scale;
+  for (int j = 0; j < kb; ++j) {
+    const T pv = a[j][j];
+    const T rowv = a[j][c];
+    T cj[RG];
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    if (j < kb) {
+    for (int q = 0; q < RG; ++q) cj[q] = a[r0 + q][j];
+    __syncthreads();
+    const T inv = T(1) / pv;
+    if (c < kb) {
       if (c == j) {
 #pragma unroll
-        for (int i = 0; i < NB; ++i) colj[j & 1][i] = a[i];
-      }
-      __syncthreads();
-      const T pv = colj[j & 1][j];
-      const T inv = T(1) / pv;
-      if (c == j) {
-        if (!(fabs((double)pv) > tol * scale) || !isfinite((double)pv)) bad = 1;
+        for (int q = 0; q < RG; ++q) a[r0 + q][c] = (r0 + q == j) ? inv : -cj[q] * inv;
+      } else {
+        const T t = rowv * inv;
 #pragma unroll
-        for (int i = 0; i < NB; ++i) a[i] = (i == j) ? inv : -a[i] * inv;
-      } else if (c < kb) {
-        const T t = a[j] * inv;
-#pragma unroll
-        for (int i = 0; i < NB; ++i) a[i] = (i == j) ? t : a[i] - colj[j & 1][i] * t;
+        for (int q = 0; q < RG; ++q) a[r0 + q][c] = (r0 + q == j) ? t : a[r0 + q][c] - cj[q] * t;
       }
     }
+    if (tid == 0 && (!(fabs((double)pv) > tol * scale) || !isfinite((double)pv))) bad = 1;
+    __syncthreads();
   }
-  __syncthreads();
   T* P = Pbuf + d.offP;
-  if (c < kb) {
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-      if (i < kb) P[i * NB + c] = a[i];
-  }
-  if (c == 0 && bad) atomicOr(status, DEV_PIVOT);
+  for (int t = tid; t < kb * kb; t += DIAG_THREADS) P[(t / kb) * NB + t % kb] = a[t / kb][t % kb];
+  if (tid == 0 && bad) atomicOr(status, DEV_PIVOT);
 }
 
 // Builds X and Y panels and zeroes the pivot rows/columns, for indices
 // [blockIdx.x*64, +64) of each matrix (as columns for Y, as rows for X).
 // Reads and writes of different CTAs touch disjoint entries: the Y part
 // reads pivot rows outside the pivot columns, the X part reads pivot
-// columns outside the pivot rows.
+// columns outside the pivot rows (the pivot block itself is read only into
+// Y entries that are replaced by P).  Each thread forms a 4 x 4 block of Y
+// (16 independent FMA chains) and gathers its 16 X entries before storing,
+// so that loads are in flight together.
 template <typename T>
 __global__ void __launch_bounds__(256)
 sweep_panel_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat,
                    const T* __restrict__ Pbuf, T* __restrict__ Xbuf, T* __restrict__ Ybuf) {
-  constexpr int NB = SWEEP_NB, CH = 64;
+  constexpr int NB = SWEEP_NB, CH = 64, PER = NB * CH / 256;
+  static_assert(NB == 64 && CH == 64, "4 x 4 register tiles over 256 threads");
   __shared__ T Ps[NB][NB + 1];
   __shared__ T col[NB][CH + 1];
   const SweepDesc d = desc[blockIdx.y];
@@ -431,40 +437,68 @@ sweep_panel_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ ma
   const T* P = Pbuf + d.offP;
   T* X = Xbuf + d.offX;
   T* Y = Ybuf + d.offY;
-  for (int t = tid; t < kb * kb; t += blockDim.x) Ps[t / kb][t % kb] = P[(t / kb) * NB + t % kb];
-  // pivot rows restricted to this column chunk
-  for (int t = tid; t < kb * cn; t += blockDim.x) {
-    int r = t / cn, c = t % cn;
-    col[r][c] = A[(int64_t)(k0 + r) * d.ld + c0 + c];
-  }
-  __syncthreads();
-  // Y[r, j] = sum_t P[r][t] A[k0+t, j]  (j outside kk),  Y[:, kk] = P
-  for (int t = tid; t < kb * cn; t += blockDim.x) {
-    int r = t / cn, c = t % cn;
-    const int j = c0 + c;
-    T v;
-    if (j >= k0 && j < k0 + kb) {
-      v = Ps[r][j - k0];
-    } else {
-      T s = T(0);
-      for (int q = 0; q < kb; ++q) s = fma(Ps[r][q], col[q][c], s);
-      v = s;
+  if (cn > 0) {
+    for (int t = tid; t < NB * NB; t += 256) {
+      const int r = t / NB, q = t % NB;
+      Ps[r][q] = (r < kb && q < kb) ? P[r * NB + q] : T(0);
     }
-    Y[(int64_t)r * d.ld + j] = v;
-    A[(int64_t)(k0 + r) * d.ld + j] = T(0);
+    // pivot rows restricted to this column chunk (zero outside kb x cn)
+    for (int t = tid; t < NB * CH; t += 256) {
+      const int r = t / CH, c = t % CH;
+      col[r][c] = (r < kb && c < cn) ? A[(int64_t)(k0 + r) * d.ld + c0 + c] : T(0);
+    }
   }
   // X[i, :] = A[i, kk] (i outside kk), X[kk] = -I ; then A[i, kk] = 0
-  for (int t = tid; t < rn * kb; t += blockDim.x) {
-    int r = t / kb, q = t % kb;
-    const int i = c0 + r;
-    T v;
-    if (i >= k0 && i < k0 + kb) {
-      v = (i - k0 == q) ? T(-1) : T(0);
-    } else {
-      v = A[(int64_t)i * d.ld + k0 + q];
+  if (rn > 0) {
+    T xv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int t = tid + 256 * u, r = t / NB, q = t % NB, i = c0 + r;
+      xv[u] = (r < rn && q < kb && !(i >= k0 && i < k0 + kb)) ? A[(int64_t)i * d.ld + k0 + q] : T(0);
     }
-    X[(int64_t)i * NB + q] = v;
-    A[(int64_t)i * d.ld + k0 + q] = T(0);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int t = tid + 256 * u, r = t / NB, q = t % NB, i = c0 + r;
+      if (r < rn && q < kb) {
+        const bool piv = i >= k0 && i < k0 + kb;
+        X[(int64_t)i * NB + q] = piv ? ((i - k0 == q) ? T(-1) : T(0)) : xv[u];
+        A[(int64_t)i * d.ld + k0 + q] = T(0);
+      }
+    }
+  }
+  if (cn == 0) return;
+  __syncthreads();
+  // Y[r, j] = sum_q P[r][q] A[k0+q, j]  (j outside kk),  Y[:, kk] = P
+  const int ty = tid / 16, tx = tid % 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int q = 0; q < kb; ++q) {
+    T pr[4], cc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) pr[i] = Ps[4 * ty + i][q];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cc[j] = col[q][4 * tx + j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(pr[i], cc[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = 4 * ty + i;
+    if (r >= kb) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = 4 * tx + j;
+      if (c >= cn) continue;
+      const int jg = c0 + c;
+      const T v = (jg >= k0 && jg < k0 + kb) ? Ps[r][jg - k0] : acc[i][j];
+      Y[(int64_t)r * d.ld + jg] = v;
+      A[(int64_t)(k0 + r) * d.ld + jg] = T(0);
+    }
   }
 }
 
