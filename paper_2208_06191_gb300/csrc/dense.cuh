@@ -155,12 +155,14 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
                const T* __restrict__ B, T* __restrict__ C, T alpha, T beta) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
-  constexpr int BM = 32 * W, BN = 32 * W, BK = 16;
+  // K slice: 8 for FP32 (register budget of the 8 x 8 micro-tile), 16 for
+  // FP64; each thread moves NV vectors of A (rows am + h * AR) and of B
+  // (rows bk + 8 h) per slice, the next slice's loads in flight while the
+  // current slice's FMAs run
+  constexpr int BM = 32 * W, BN = 32 * W, BK = W == 4 ? 8 : 16;
   constexpr int HALF = BM / 2;
-  // each thread moves two vectors of A (rows am, am + BM/2) and two of B
-  // (rows bk, bk + 8) per BK step; the next step's four vectors are in
-  // flight while the current step's FMAs run
-  static_assert(BM * BK == 2 * 256 * W && BK * BN == 2 * 256 * W, "two vectors per thread");
+  constexpr int NV = BM * BK / (256 * W), AR = 256 * W / BK;
+  static_assert(BK * BN == NV * 256 * W && BN / W * 8 == 256, "vectors per thread");
   const int4 tl = tiles[blockIdx.x];
   const GemmProb p = probs[tl.x];
   const int m0 = tl.y * BM, n0 = tl.z * BN;
@@ -178,8 +180,8 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
   auto load_a = [&](int k0, int h) -> V {
     V v;
     const int valid = p.K - (k0 + ak);
-    if ((m0 + am + h * HALF) < p.M && valid > 0) {
-      v = *reinterpret_cast<const V*>(Ab + (int64_t)h * HALF * p.lda + k0);
+    if ((m0 + am + h * AR) < p.M && valid > 0) {
+      v = *reinterpret_cast<const V*>(Ab + (int64_t)h * AR * p.lda + k0);
       v = vmask<T>(v, valid);
     } else {
       v = vmask<T>(V{}, 0);
@@ -198,30 +200,50 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
   };
   auto stage = [&](int b, const V* ra, const V* rb) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NV; ++h) {
       T tmp[W];
       vstore4<T>(tmp, ra[h]);
 #pragma unroll
-      for (int q = 0; q < W; ++q) As[b][ak + q][am + h * HALF] = tmp[q];
+      for (int q = 0; q < W; ++q) As[b][ak + q][am + h * AR] = tmp[q];
       *reinterpret_cast<V*>(&Bs[b][bk + 8 * h][bn]) = rb[h];
     }
   };
+  // The C tile is prefetched into L2 now, so that the epilogue's reads of
+  // C (beta != 0) do not wait on DRAM; short-K sweep updates spend much of
+  // their time there.  Accumulation order is unchanged (products from
+  // zero, then alpha acc + beta C).
+  T* Cb = C + p.c;
+  const bool cvec = ((p.c % W) == 0) && ((p.ldc % W) == 0);
+  if (beta != T(0)) {
+#pragma unroll
+    for (int i = 0; i < 2 * W; ++i) {
+      const int gm = m0 + (i < W ? ty * W + i : HALF + ty * W + (i - W));
+      if (gm < p.M && (tx & 7) == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int gn0 = n0 + h * HALF + tx * W;
+          if (gn0 < p.N)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(Cb + (int64_t)gm * p.ldc + gn0));
+        }
+      }
+    }
+  }
   T acc[2 * W][2 * W];
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i)
 #pragma unroll
     for (int j = 0; j < 2 * W; ++j) acc[i][j] = T(0);
-  V ra[2] = {load_a(0, 0), load_a(0, 1)}, rb[2] = {load_b(0, 0), load_b(0, 1)};
+  V ra[NV], rb[NV];
+#pragma unroll
+  for (int h = 0; h < NV; ++h) { ra[h] = load_a(0, h); rb[h] = load_b(0, h); }
   int buf = 0;
   stage(0, ra, rb);
   __syncthreads();
   for (int k0 = 0; k0 < p.K; k0 += BK) {
     const bool more = (k0 + BK) < p.K;
     if (more) {
-      ra[0] = load_a(k0 + BK, 0);
-      ra[1] = load_a(k0 + BK, 1);
-      rb[0] = load_b(k0 + BK, 0);
-      rb[1] = load_b(k0 + BK, 1);
+#pragma unroll
+      for (int h = 0; h < NV; ++h) { ra[h] = load_a(k0 + BK, h); rb[h] = load_b(k0 + BK, h); }
     }
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
@@ -241,8 +263,7 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
       buf ^= 1;
     }
   }
-  T* Cb = C + p.c;
-  const bool cvec = ((p.c % W) == 0) && ((p.ldc % W) == 0);
+  const T beta_e = beta;
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i) {
     const int gm = m0 + (i < W ? ty * W + i : HALF + ty * W + (i - W));
@@ -253,9 +274,9 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
       T* cp = Cb + (int64_t)gm * p.ldc + gn0;
       if (cvec && gn0 + W <= p.N) {
         T v[W];
-        if (beta != T(0)) vstore4<T>(v, *reinterpret_cast<const V*>(cp));
+        if (beta_e != T(0)) vstore4<T>(v, *reinterpret_cast<const V*>(cp));
 #pragma unroll
-        for (int j = 0; j < W; ++j) v[j] = (beta == T(0)) ? alpha * acc[i][h * W + j] : alpha * acc[i][h * W + j] + beta * v[j];
+        for (int j = 0; j < W; ++j) v[j] = (beta_e == T(0)) ? alpha * acc[i][h * W + j] : alpha * acc[i][h * W + j] + beta_e * v[j];
         V o;
         if constexpr (W == 4) o = V{v[0], v[1], v[2], v[3]};
         else o = V{v[0], v[1]};
@@ -265,7 +286,7 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
         for (int j = 0; j < W; ++j) {
           if (gn0 + j >= p.N) break;
           const T v = alpha * acc[i][h * W + j];
-          cp[j] = (beta == T(0)) ? v : v + beta * cp[j];
+          cp[j] = (beta_e == T(0)) ? v : v + beta_e * cp[j];
         }
       }
     }
