@@ -38,7 +38,8 @@ UNIT = "ms/Newton step"
 WORKLOAD = "slab48_q1"
 
 # name -> (description, problem builder, BDDC levels, level-2 groups, load
-# steps whose Newton states are replayed (None: all), FP64 steps timed)
+# steps whose Newton states are replayed (None: all), FP64 steps timed
+# (None: one per replayed state, so both precisions see the same states))
 WORKLOADS = {
     "slab48_q1": ("48x48x12 Q1 hex slab [0,4]x[0,4]x[0,1], 64 box subdomains (4x4x4), primal VE, "
                   "n_free=86436, follower pressure 1 kPa + activation 30 kPa, 4 load steps",
@@ -49,16 +50,16 @@ WORKLOADS = {
     "lv_p1": ("left-ventricle shell, P1 tets, ~1.0M free DoFs, 512 uneven subdomains (+-30%), "
               "primal VEF, two-level (dense FP64 coarse), endocardial pressure 2 kPa + activation "
               "15 kPa over 8 load steps; Newton states of the first load step",
-              lambda: __import__("workloads").lv_config("lv_p1"), 2, None, 1, 1),
+              lambda: __import__("workloads").lv_config("lv_p1"), 2, None, 1, None),
     "lv_p1_ml": ("left-ventricle shell, P1 tets, ~1.0M free DoFs, 512 uneven subdomains (+-30%) "
                  "nested in 16 level-2 subdomains, three-level BDDC, primal VEF/VEF, pressure 2 kPa "
                  "+ activation 15 kPa over 8 load steps; Newton states of the first load step",
-                 lambda: __import__("workloads").lv_config("lv_p1", n_parts2=16), 3, 16, 1, 1),
+                 lambda: __import__("workloads").lv_config("lv_p1", n_parts2=16), 3, 16, 1, None),
     "lv_p2": ("left-ventricle shell, P2 tets, ~3.0M free DoFs, 4096 uneven subdomains (2048 "
               "surface patches x 2 slabs) nested in 64 level-2 subdomains, three-level BDDC, "
               "primal VEF/VEF, FP64 coarsest solve, pressure 2 kPa + activation 15 kPa over 8 "
               "load steps; Newton states of the first load step",
-              lambda: __import__("workloads").lv_config("lv_p2"), 3, 64, 1, 1),
+              lambda: __import__("workloads").lv_config("lv_p2"), 3, 64, 1, None),
 }
 # reduced ventricles (same generator, 5 x 64 x 32 rings, 64 subdomains) for
 # profiler captures that must stay a few GB on the device
@@ -343,7 +344,10 @@ def run_ours(args, world, rank, local):
     # ---- FP64 local operators
     ctx64 = run_steps(1, opts64, None)
     recs64 = []
-    K64 = max(1, min(K, args.fp64_steps if args.workload == WORKLOAD else fp64_default))
+    if args.workload == WORKLOAD:
+        K64 = max(1, min(K, args.fp64_steps))
+    else:
+        K64 = ns if fp64_default is None else max(1, min(K, fp64_default))
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
@@ -406,7 +410,10 @@ def run_ours(args, world, rank, local):
         "breakdown_fp32": {"ms_assemble": phase(recs32, "ms_assemble"),
                            "ms_setup": phase(recs32, "ms_setup"),
                            "ms_gmres": phase(recs32, "ms_gmres"),
-                           "gmres_its_mean": statistics.mean(r["gmres_its"] for r in recs32)},
+                           "gmres_its_mean": statistics.mean(r["gmres_its"] for r in recs32),
+                           "gmres_its_max": max(r["gmres_its"] for r in recs32),
+                           "ms_step_median": statistics.median(r["ms_total"] for r in recs32),
+                           "ms_step_max": max(r["ms_total"] for r in recs32)},
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(launches),

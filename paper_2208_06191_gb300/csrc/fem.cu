@@ -29,9 +29,9 @@ __constant__ double c_x[2][3];
 // Tetrahedra (index o = order - 1): volume rule points q, shape values
 // c_tN[o][q][a] and reference gradients c_tdN[o][q][a][j]; triangle faces:
 // values c_fN[o][q][a] and parametric derivatives c_fds / c_fdt.
-__constant__ double c_tN[2][4][10];
-__constant__ double c_tdN[2][4][10][3];
-__constant__ double c_tw[2][4];
+__constant__ double c_tN[3][8][10];
+__constant__ double c_tdN[3][8][10][3];
+__constant__ double c_tw[3][8];
 __constant__ double c_fN[2][3][6];
 __constant__ double c_fds[2][3][6];
 __constant__ double c_fdt[2][3][6];
@@ -88,7 +88,7 @@ void tri_shape_host(int k, double s, double t, double* N, double* ds, double* dt
 }
 
 void init_tet_tables() {
-  double tN[2][4][10] = {}, tdN[2][4][10][3] = {}, tw[2][4] = {};
+  double tN[3][8][10] = {}, tdN[3][8][10][3] = {}, tw[3][8] = {};
   double fN[2][3][6] = {}, fds[2][3][6] = {}, fdt[2][3][6] = {}, fw[2][3] = {};
   // P1: centroid, weight 1/6 (volume of the reference tetrahedron)
   {
@@ -105,6 +105,24 @@ void init_tet_tables() {
       const double xi[3] = {bary[1], bary[2], bary[3]};
       tet_shape_host(2, xi, tN[1][q], tdN[1][q]);
       tw[1][q] = 1.0 / 24.0;
+    }
+  }
+  // table 2: the trilinear hexahedron at its 2 x 2 x 2 Gauss points (for the
+  // quadrature-point-parallel kernel), point qx + 2 (qy + 2 qz), node
+  // ax + 2 (ay + 2 az) at (-1 + 2 ax, -1 + 2 ay, -1 + 2 az)
+  {
+    const double g = 1.0 / std::sqrt(3.0);
+    for (int q = 0; q < 8; ++q) {
+      const double x[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
+      for (int a = 0; a < 8; ++a) {
+        const double s[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
+        const double l[3] = {0.5 * (1.0 + s[0] * x[0]), 0.5 * (1.0 + s[1] * x[1]), 0.5 * (1.0 + s[2] * x[2])};
+        tN[2][q][a] = l[0] * l[1] * l[2];
+        tdN[2][q][a][0] = 0.5 * s[0] * l[1] * l[2];
+        tdN[2][q][a][1] = 0.5 * s[1] * l[0] * l[2];
+        tdN[2][q][a][2] = 0.5 * s[2] * l[0] * l[1];
+      }
+      tw[2][q] = 1.0;
     }
   }
   // triangle rules: centroid (weight 1/2) and the 3-point rule of degree 2
@@ -298,20 +316,49 @@ __device__ bool material_point(const MatParams& m, const double F[3][3], const d
   for (int a = 0; a < 3; ++a)
     for (int i = 0; i < 3; ++i) g[a][i] = F[i][0] * R[0][a] + F[i][1] * R[1][a] + F[i][2] * R[2][a];
   const double ga = m.gamma / un;
-  for (int i = 0; i < 3; ++i)
+  // The anisotropic second-derivative term
+  //   lin_iJkL = sum_ab W_ab g_ai R_Jb (g_ak R_Lb + g_bk R_La)
+  // is factored as sum_a g_ai g_ak X_a(J,L) + sum_a (g_ai R_La) V_a(k,J) with
+  //   X_a(J,L) = sum_b W_ab R_Jb R_Lb,   V_a(k,J) = sum_b W_ab g_bk R_Jb,
+  // and A is major-symmetric (A_iJkL = A_kLiJ: the energy depends on F
+  // only), so 45 entries are formed and mirrored (FP64 issue is the
+  // bottleneck of this kernel).
+  double X[3][3][3], V[3][3][3];  // X[a][J][L] (symmetric in J, L), V[a][k][J]
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
     for (int Jx = 0; Jx < 3; ++Jx)
-      for (int k = 0; k < 3; ++k)
-        for (int L = 0; L < 3; ++L) {
-          double lin = 0.0;
-          for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b)
-              lin += m.W[a][b] * g[a][i] * R[Jx][b] * (g[a][k] * R[L][b] + g[b][k] * R[L][a]);
-          double v = eQ * (2.0 * FS[i][Jx] * FS[k][L] + 0.5 * lin);
-          if (i == k) v += eQ * Sh[L][Jx];
-          v += J * dkap * Fi[Jx][i] * Fi[L][k] - kap * Fi[Jx][k] * Fi[L][i];
-          v += ga * ((i == k ? 1.0 : 0.0) - mv[i] * mv[k]) * f[Jx] * f[L];
-          A[((i * 3 + Jx) * 3 + k) * 3 + L] = v;
-        }
+#pragma unroll
+      for (int L = Jx; L < 3; ++L) {
+        const double v = m.W[a][0] * R[Jx][0] * R[L][0] + m.W[a][1] * R[Jx][1] * R[L][1] +
+                         m.W[a][2] * R[Jx][2] * R[L][2];
+        X[a][Jx][L] = v;
+        X[a][L][Jx] = v;
+      }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int Jx = 0; Jx < 3; ++Jx)
+        V[a][k][Jx] = m.W[a][0] * g[0][k] * R[Jx][0] + m.W[a][1] * g[1][k] * R[Jx][1] +
+                      m.W[a][2] * g[2][k] * R[Jx][2];
+  }
+#pragma unroll
+  for (int pq = 0; pq < 9; ++pq) {
+    const int i = pq / 3, Jx = pq % 3;
+#pragma unroll
+    for (int qq = pq; qq < 9; ++qq) {
+      const int k = qq / 3, L = qq % 3;
+      double lin = 0.0;
+      for (int a = 0; a < 3; ++a)
+        lin += g[a][i] * (g[a][k] * X[a][Jx][L] + R[L][a] * V[a][k][Jx]);
+      double v = eQ * (2.0 * FS[i][Jx] * FS[k][L] + 0.5 * lin);
+      if (i == k) v += eQ * Sh[L][Jx];
+      v += J * dkap * Fi[Jx][i] * Fi[L][k] - kap * Fi[Jx][k] * Fi[L][i];
+      v += ga * ((i == k ? 1.0 : 0.0) - mv[i] * mv[k]) * f[Jx] * f[L];
+      A[pq * 9 + qq] = v;
+      A[qq * 9 + pq] = v;
+    }
+  }
   return true;
 }
 
@@ -444,8 +491,10 @@ element_kernel(MatParams mp, const double* __restrict__ coords, const int* __res
 }
 
 
-// Tetrahedra, TET_THREADS material points per CTA (EPB = TET_THREADS / NQ
-// elements).  Phase 1: one thread per quadrature point computes the
+// Quadrature-point-parallel element kernel for elements with few points
+// (P1: 1, P2: 4, Q1: 8; shape table O = 0, 1, 2), TET_THREADS material
+// points per CTA (EPB = TET_THREADS / NQ elements), so that every lane of
+// the FP64 material evaluation has work.  Phase 1: one thread per quadrature point computes the
 // geometry, F, the fibre frame and the material point, and stores
 // w detJ0 P and w detJ0 dP/dF in shared memory (stride 81 per point keeps
 // the 8-byte accesses conflict-free).  Phase 2: one thread per residual
@@ -453,14 +502,14 @@ element_kernel(MatParams mp, const double* __restrict__ coords, const int* __res
 // matrix, K[a][b][i][k] = sum_q sum_L (sum_J G_aJ A_iJkL) G_bL for all b.
 constexpr int TET_THREADS = 32;
 
-template <int K>
+template <int NEN, int NQ, int O>
 __global__ void __launch_bounds__(TET_THREADS)
-tet_element_kernel(MatParams mp, const double* __restrict__ coords, const int* __restrict__ elems,
-                   const double* __restrict__ fib, const double* __restrict__ d_full,
-                   double* __restrict__ rcontrib, double* __restrict__ contrib,
-                   int* __restrict__ status, int want_tangent, int n_el) {
-  constexpr int NEN = K == 1 ? 4 : 10, NQ = K == 1 ? 1 : 4, O = K - 1;
+qp_element_kernel(MatParams mp, const double* __restrict__ coords, const int* __restrict__ elems,
+                  const double* __restrict__ fib, const double* __restrict__ d_full,
+                  double* __restrict__ rcontrib, double* __restrict__ contrib,
+                  int* __restrict__ status, int want_tangent, int n_el) {
   constexpr int EPB = TET_THREADS / NQ;
+  static_assert(EPB * NQ == TET_THREADS, "whole elements per CTA");
   __shared__ double As[TET_THREADS * 81];
   __shared__ double Ps[TET_THREADS * 9];
   __shared__ double Gs[TET_THREADS][NEN][3];
@@ -735,20 +784,21 @@ void assemble(fem_problem* P, const double* d, double lam, double* residual, boo
   const int wt = want_tangent ? 1 : 0;
   timer_begin(CBDDC_TIMER_ELEMENT, s);
   const double* fib = P->fib_nodal.p;
-  if (P->tet) {
+  if (P->tet || P->order == 1) {
     const int epb = TET_THREADS / P->n_qp;
     const int grid = (int)cdiv(P->n_el, epb);
-    if (P->order == 1)
-      tet_element_kernel<1><<<grid, TET_THREADS, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
-                                                         P->rcontrib.p, P->contrib.p, P->status.p, wt,
-                                                         P->n_el);
+    if (P->tet && P->order == 1)
+      qp_element_kernel<4, 1, 0><<<grid, TET_THREADS, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
+                                                              P->rcontrib.p, P->contrib.p, P->status.p, wt,
+                                                              P->n_el);
+    else if (P->tet)
+      qp_element_kernel<10, 4, 1><<<grid, TET_THREADS, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
+                                                               P->rcontrib.p, P->contrib.p, P->status.p, wt,
+                                                               P->n_el);
     else
-      tet_element_kernel<2><<<grid, TET_THREADS, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
-                                                         P->rcontrib.p, P->contrib.p, P->status.p, wt,
-                                                         P->n_el);
-  } else if (P->order == 1) {
-    element_kernel<1, 64><<<P->n_el, 64, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
-                                                  P->rcontrib.p, P->contrib.p, P->status.p, wt);
+      qp_element_kernel<8, 8, 2><<<grid, TET_THREADS, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
+                                                              P->rcontrib.p, P->contrib.p, P->status.p, wt,
+                                                              P->n_el);
   } else {
     element_kernel<2, 256><<<P->n_el, 256, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
                                                     P->rcontrib.p, P->contrib.p, P->status.p, wt);
