@@ -225,12 +225,13 @@ __global__ void cons_y_kernel(const int* __restrict__ nr, const int* __restrict_
   const int row = blockIdx.x * (blockDim.x >> 5) + warp;
   if (row >= nr[s]) return;
   const T* Srow = Sw + offS[s] + (int64_t)row * ldS[s];
-  for (int q = 0; q < na[s]; ++q) {
+  // one lane per constraint (classes have few members): no reductions,
+  // and the row's Y entries are written together
+  for (int q = lane; q < na[s]; q += 32) {
     const int64_t gq = offCon[s] + q;
     double acc = 0.0;
-    for (int j = cptr[gq] + lane; j < cptr[gq + 1]; j += 32) acc += (double)Srow[cidx[j]];
-    acc = warp_sum(acc);
-    if (lane == 0) Y[offY[s] + (int64_t)row * ldY[s] + q] = (T)(acc * cw[gq]);
+    for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += (double)Srow[cidx[j]];
+    Y[offY[s] + (int64_t)row * ldY[s] + q] = (T)(acc * cw[gq]);
   }
 }
 

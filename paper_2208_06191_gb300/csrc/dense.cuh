@@ -363,14 +363,15 @@ struct SweepDesc {
 };
 
 // P = inverse of the kb x kb diagonal block of pivot step k, by Gauss-Jordan
-// in the operator precision T on a shared-memory copy of the block.
-// Thread (c, g) = (tid % 64, tid / 64) owns rows [16 g, 16 g + 16) of
-// column c, so the 256 threads keep all four SM sub-partitions busy (the
-// FP64 case of the coarse matrix needs every FP64 unit).  At pivot j each
-// thread first reads the pivot-row entry of its column and the column-j
-// entries of its rows, then, after a barrier, updates its entries:
+// in the operator precision T.  Thread (c, g) = (tid % 64, tid / 64) keeps
+// rows [16 g, 16 g + 16) of column c in registers, so the 256 threads keep
+// all four SM sub-partitions busy (the FP64 case of the coarse matrix needs
+// every FP64 unit).  At pivot j every thread reads the old pivot column and
+// pivot row from a double-buffered shared copy, updates its entries
 //   a[j][c] <- a[j][c] / p,  a[i][c] <- a[i][c] - a[i][j] a[j][c] / p (c != j),
-//   a[i][j] <- -a[i][j] / p, a[j][j] <- 1 / p.
+//   a[i][j] <- -a[i][j] / p, a[j][j] <- 1 / p,
+// and the owners of column j + 1 and row j + 1 publish them into the other
+// buffer, so one barrier per pivot suffices.
 constexpr int DIAG_THREADS = 256;
 template <typename T>
 __global__ void __launch_bounds__(DIAG_THREADS)
@@ -378,7 +379,8 @@ sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat
                   int* __restrict__ status, double tol) {
   constexpr int NB = SWEEP_NB;
   constexpr int RG = NB / (DIAG_THREADS / NB);  // rows per thread
-  __shared__ T a[NB][NB + 1];
+  __shared__ T blk[NB][NB + 1];
+  __shared__ T colb[2][NB], rowb[2][NB];
   __shared__ double piv_scale;
   __shared__ int bad;
   const SweepDesc d = desc[blockIdx.x];
@@ -390,42 +392,65 @@ sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat
   const T* A = mat + d.off + (int64_t)k0 * d.ld + k0;
   for (int t = tid; t < NB * NB; t += DIAG_THREADS) {
     const int i = t / NB, cc = t % NB;
-    a[i][cc] = (i < kb && cc < kb) ? A[(int64_t)i * d.ld + cc] : T(0);
+    blk[i][cc] = (i < kb && cc < kb) ? A[(int64_t)i * d.ld + cc] : T(0);
   }
   if (tid == 0) bad = 0;
   __syncthreads();
+  T a[RG];
+#pragma unroll
+  for (int q = 0; q < RG; ++q) a[q] = blk[r0 + q][c];
+  if (c == 0) {
+#pragma unroll
+    for (int q = 0; q < RG; ++q) colb[0][r0 + q] = a[q];
+  }
+  if (r0 == 0) rowb[0][c] = a[0];
   // scale of the pivots: largest |diagonal| of the block
   if (tid < 32) {
     double dv = 0.0;
-    for (int i = tid; i < kb; i += 32) dv = fmax(dv, fabs((double)a[i][i]));
+    for (int i = tid; i < kb; i += 32) dv = fmax(dv, fabs((double)blk[i][i]));
     for (int o = 16; o > 0; o >>= 1) dv = fmax(dv, __shfl_xor_sync(0xffffffffu, dv, o));
     if (tid == 0) piv_scale = dv;
   }
   __syncthreads();
   const double scale = piv_scale;
   for (int j = 0; j < kb; ++j) {
-    const T pv = a[j][j];
-    const T rowv = a[j][c];
-    T cj[RG];
-#pragma unroll
-    for (int q = 0; q < RG; ++q) cj[q] = a[r0 + q][j];
-    __syncthreads();
+    const int b = j & 1, nb = b ^ 1;
+    const T pv = rowb[b][j];
+    const T rj = rowb[b][c];
     const T inv = T(1) / pv;
     if (c < kb) {
       if (c == j) {
 #pragma unroll
-        for (int q = 0; q < RG; ++q) a[r0 + q][c] = (r0 + q == j) ? inv : -cj[q] * inv;
+        for (int q = 0; q < RG; ++q) a[q] = (r0 + q == j) ? inv : -colb[b][r0 + q] * inv;
       } else {
-        const T t = rowv * inv;
+        const T t = rj * inv;
 #pragma unroll
-        for (int q = 0; q < RG; ++q) a[r0 + q][c] = (r0 + q == j) ? t : a[r0 + q][c] - cj[q] * t;
+        for (int q = 0; q < RG; ++q) a[q] = (r0 + q == j) ? t : a[q] - colb[b][r0 + q] * t;
+      }
+    }
+    if (j + 1 < kb) {
+      if (c == j + 1) {
+#pragma unroll
+        for (int q = 0; q < RG; ++q) colb[nb][r0 + q] = a[q];
+      }
+      const int jr = j + 1 - r0;
+      if (jr >= 0 && jr < RG) {
+        T v = T(0);
+#pragma unroll
+        for (int q = 0; q < RG; ++q)
+          if (q == jr) v = a[q];
+        rowb[nb][c] = v;
       }
     }
     if (tid == 0 && (!(fabs((double)pv) > tol * scale) || !isfinite((double)pv))) bad = 1;
     __syncthreads();
   }
   T* P = Pbuf + d.offP;
-  for (int t = tid; t < kb * kb; t += DIAG_THREADS) P[(t / kb) * NB + t % kb] = a[t / kb][t % kb];
+  if (c < kb) {
+#pragma unroll
+    for (int q = 0; q < RG; ++q)
+      if (r0 + q < kb) P[(r0 + q) * NB + c] = a[q];
+  }
   if (tid == 0 && bad) atomicOr(status, DEV_PIVOT);
 }
 
