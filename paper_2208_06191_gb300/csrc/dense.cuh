@@ -114,13 +114,12 @@ gemm_grouped_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__
 // Fast path for C = alpha A B + beta C (both operands row-major, not
 // transposed): tiles of (32 VEC) x (32 VEC) with VEC = 16 / sizeof(T) (128 x
 // 128 for FP32, 64 x 64 for FP64), 256 threads, a 2 VEC x 2 VEC split
-// micro-tile per thread, 128-bit global loads staged through registers so
-// the next K slice loads while the current one is multiplied, and one
-// barrier per K slice.  Operands must start on 16-byte boundaries with
-// leading dimensions that are multiples of VEC (checked on the host); loads
-// past M, N or K are masked to zero, and every operand buffer carries at
-// least 64 elements of slack so that a masked vector load never leaves its
-// allocation.
+// micro-tile per thread.  K slices of 16 go global -> shared with 16-byte
+// asynchronous copies (cp.async) through a 3-stage ring, so two slices are
+// in flight while one is multiplied, with one barrier per slice.  Operands
+// must start on 16-byte boundaries with leading dimensions that are
+// multiples of VEC (checked on the host); copies past M, N or K read nothing
+// and zero-fill.
 template <typename T> struct VecT;
 template <> struct VecT<float> { using V = float4; static constexpr int W = 4; };
 template <> struct VecT<double> { using V = double2; static constexpr int W = 2; };
@@ -149,69 +148,64 @@ __device__ inline double2 vmask<double>(double2 v, int valid) {
   return v;
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 template <typename T>
 __global__ void __launch_bounds__(256, 2)
 gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ probs, const T* __restrict__ A,
                const T* __restrict__ B, T* __restrict__ C, T alpha, T beta) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
-  // K slice: 8 for FP32 (register budget of the 8 x 8 micro-tile), 16 for
-  // FP64; each thread moves NV vectors of A (rows am + h * AR) and of B
-  // (rows bk + 8 h) per slice, the next slice's loads in flight while the
-  // current slice's FMAs run
-  constexpr int BM = 32 * W, BN = 32 * W, BK = W == 4 ? 8 : 16;
+  constexpr int BM = 32 * W, BN = 32 * W, BK = 16, STAGES = 3;
   constexpr int HALF = BM / 2;
-  constexpr int NV = BM * BK / (256 * W), AR = 256 * W / BK;
-  static_assert(BK * BN == NV * 256 * W && BN / W * 8 == 256, "vectors per thread");
+  constexpr int ACH = BK / W;            // 16-byte chunks per A row slice
+  static_assert(BM * BK / W == 2 * 256 && BK * BN / W == 2 * 256, "two chunks of A and of B per thread");
   const int4 tl = tiles[blockIdx.x];
   const GemmProb p = probs[tl.x];
   const int m0 = tl.y * BM, n0 = tl.z * BN;
   if (m0 >= p.M || n0 >= p.N || p.K <= 0) return;
-  __shared__ __align__(16) T As[2][BK][BM + 4];
-  __shared__ __align__(16) T Bs[2][BK][BN + 4];
+  __shared__ __align__(16) T As[STAGES][BM][BK + 4];   // [m][k]
+  __shared__ __align__(16) T Bs[STAGES][BK][BN + 4];   // [k][n]
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  // global load coordinates
-  const int am = tid / (BK / W), ak = (tid % (BK / W)) * W;
-  const int bk = tid / (BN / W), bn = (tid % (BN / W)) * W;
-  const T* Ab = A + p.a + (int64_t)(m0 + am) * p.lda + ak;
-  const T* Bb = B + p.b + (int64_t)bk * p.ldb + n0 + bn;
-  const int b_col_valid = p.N - (n0 + bn);
-  auto load_a = [&](int k0, int h) -> V {
-    V v;
-    const int valid = p.K - (k0 + ak);
-    if ((m0 + am + h * AR) < p.M && valid > 0) {
-      v = *reinterpret_cast<const V*>(Ab + (int64_t)h * AR * p.lda + k0);
-      v = vmask<T>(v, valid);
-    } else {
-      v = vmask<T>(V{}, 0);
-    }
-    return v;
-  };
-  auto load_b = [&](int k0, int h) -> V {
-    V v;
-    if ((k0 + bk + 8 * h) < p.K && b_col_valid > 0) {
-      v = *reinterpret_cast<const V*>(Bb + (int64_t)(k0 + 8 * h) * p.ldb);
-      v = vmask<T>(v, b_col_valid);
-    } else {
-      v = vmask<T>(V{}, 0);
-    }
-    return v;
-  };
-  auto stage = [&](int b, const V* ra, const V* rb) {
+  const T* Ab = A + p.a;
+  const T* Bb = B + p.b;
+  // issue the copies of K slice kt into stage st (zero-fill outside M, N, K)
+  auto load_slice = [&](int kt, int st) {
+    const int k0 = kt * BK;
 #pragma unroll
-    for (int h = 0; h < NV; ++h) {
-      T tmp[W];
-      vstore4<T>(tmp, ra[h]);
+    for (int h = 0; h < 2; ++h) {
+      const int c = tid + 256 * h;
+      const int row = c / ACH, kq = (c % ACH) * W;
+      const int gm = m0 + row, gk = k0 + kq;
+      const int valid = (gm < p.M) ? max(0, min(W, p.K - gk)) : 0;
+      const T* src = valid > 0 ? Ab + (int64_t)gm * p.lda + gk : Ab;
+      cp_async16(&As[st][row][kq], src, valid * (int)sizeof(T));
+    }
 #pragma unroll
-      for (int q = 0; q < W; ++q) As[b][ak + q][am + h * AR] = tmp[q];
-      *reinterpret_cast<V*>(&Bs[b][bk + 8 * h][bn]) = rb[h];
+    for (int h = 0; h < 2; ++h) {
+      const int c = tid + 256 * h;
+      const int kr = c / (BN / W), nq = (c % (BN / W)) * W;
+      const int gk = k0 + kr, gn = n0 + nq;
+      const int valid = (gk < p.K) ? max(0, min(W, p.N - gn)) : 0;
+      const T* src = valid > 0 ? Bb + (int64_t)gk * p.ldb + gn : Bb;
+      cp_async16(&Bs[st][kr][nq], src, valid * (int)sizeof(T));
     }
   };
+  const int kTiles = (p.K + BK - 1) / BK;
+#pragma unroll
+  for (int st = 0; st < STAGES - 1; ++st) {
+    if (st < kTiles) load_slice(st, st);
+    cp_async_commit();
+  }
   // The C tile is prefetched into L2 now, so that the epilogue's reads of
-  // C (beta != 0) do not wait on DRAM; short-K sweep updates spend much of
-  // their time there.  Accumulation order is unchanged (products from
-  // zero, then alpha acc + beta C).
+  // C (beta != 0) do not wait on DRAM.
   T* Cb = C + p.c;
   const bool cvec = ((p.c % W) == 0) && ((p.ldc % W) == 0);
   if (beta != T(0)) {
@@ -233,37 +227,29 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
   for (int i = 0; i < 2 * W; ++i)
 #pragma unroll
     for (int j = 0; j < 2 * W; ++j) acc[i][j] = T(0);
-  V ra[NV], rb[NV];
-#pragma unroll
-  for (int h = 0; h < NV; ++h) { ra[h] = load_a(0, h); rb[h] = load_b(0, h); }
-  int buf = 0;
-  stage(0, ra, rb);
-  __syncthreads();
-  for (int k0 = 0; k0 < p.K; k0 += BK) {
-    const bool more = (k0 + BK) < p.K;
-    if (more) {
-#pragma unroll
-      for (int h = 0; h < NV; ++h) { ra[h] = load_a(k0 + BK, h); rb[h] = load_b(k0 + BK, h); }
-    }
+  for (int kt = 0; kt < kTiles; ++kt) {
+    cp_async_wait<STAGES - 2>();   // slice kt has landed (this thread's copies)
+    __syncthreads();               // ... and everyone's; stage (kt-1)%S is free
+    if (kt + STAGES - 1 < kTiles) load_slice(kt + STAGES - 1, (kt + STAGES - 1) % STAGES);
+    cp_async_commit();
+    const int st = kt % STAGES;
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
       T a[2 * W], b[2 * W];
-      vstore4<T>(a, *reinterpret_cast<const V*>(&As[buf][k][ty * W]));
-      vstore4<T>(a + W, *reinterpret_cast<const V*>(&As[buf][k][HALF + ty * W]));
-      vstore4<T>(b, *reinterpret_cast<const V*>(&Bs[buf][k][tx * W]));
-      vstore4<T>(b + W, *reinterpret_cast<const V*>(&Bs[buf][k][HALF + tx * W]));
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        a[i] = As[st][ty * W + i][k];
+        a[W + i] = As[st][HALF + ty * W + i][k];
+      }
+      vstore4<T>(b, *reinterpret_cast<const V*>(&Bs[st][k][tx * W]));
+      vstore4<T>(b + W, *reinterpret_cast<const V*>(&Bs[st][k][HALF + tx * W]));
 #pragma unroll
       for (int i = 0; i < 2 * W; ++i)
 #pragma unroll
         for (int j = 0; j < 2 * W; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
-    if (more) {
-      stage(buf ^ 1, ra, rb);
-      __syncthreads();
-      buf ^= 1;
-    }
   }
-  const T beta_e = beta;
+  cp_async_wait<0>();
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i) {
     const int gm = m0 + (i < W ? ty * W + i : HALF + ty * W + (i - W));
@@ -274,9 +260,9 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
       T* cp = Cb + (int64_t)gm * p.ldc + gn0;
       if (cvec && gn0 + W <= p.N) {
         T v[W];
-        if (beta_e != T(0)) vstore4<T>(v, *reinterpret_cast<const V*>(cp));
+        if (beta != T(0)) vstore4<T>(v, *reinterpret_cast<const V*>(cp));
 #pragma unroll
-        for (int j = 0; j < W; ++j) v[j] = (beta_e == T(0)) ? alpha * acc[i][h * W + j] : alpha * acc[i][h * W + j] + beta_e * v[j];
+        for (int j = 0; j < W; ++j) v[j] = (beta == T(0)) ? alpha * acc[i][h * W + j] : alpha * acc[i][h * W + j] + beta * v[j];
         V o;
         if constexpr (W == 4) o = V{v[0], v[1], v[2], v[3]};
         else o = V{v[0], v[1]};
@@ -286,7 +272,7 @@ gemm_nn_kernel(const int4* __restrict__ tiles, const GemmProb* __restrict__ prob
         for (int j = 0; j < W; ++j) {
           if (gn0 + j >= p.N) break;
           const T v = alpha * acc[i][h * W + j];
-          cp[j] = (beta_e == T(0)) ? v : v + beta_e * cp[j];
+          cp[j] = (beta == T(0)) ? v : v + beta * cp[j];
         }
       }
     }
