@@ -8,6 +8,16 @@ Follows Section 2 of the paper:
   -p J F^{-T} N, written in the weak form as +p J F^{-T} N . d*,
 * Newton tangent DF(d)[delta d] of Eq. (tangent problem), taken exactly.
 
+Time-dependent terms (Section 2, time discretization), active when a time
+state is set with ``set_time_state``:
+* inertia  rho (d^n - 2 d^{n-1} + d^{n-2}) / dt^2 . d*  (the printed /dt is
+  read as /dt^2, the dimensionally consistent backward second difference),
+  with the consistent mass matrix;
+* the generalized Robin condition of Eq. (bc epi) on the listed faces,
+  traction -[(N x N)(K_perp d + C_perp v) + (I - N x N)(K_par d + C_par v)]
+  with the reference normal N and v = (d^n - d^{n-1}) / dt; without a time
+  state only the spring part (v = 0) acts.
+
 Free degrees of freedom: nodes in increasing id, Dirichlet nodes removed,
 three interleaved components per node (Section 4, block size 3).
 """
@@ -69,6 +79,36 @@ class FEProblem:
             Xt = J0f @ et_
             Aref = np.cross(Xs, Xt)                        # N dA / (ds dt)
             self.faces.append((int(e), Nf, dNdXf, Aref, fw))
+        # Robin faces: reference normal, area weights, shape values; the
+        # parameter set of each face (K_perp, K_par, C_perp, C_par)
+        self.robin = []
+        sets = prob.get("robin", [])
+        for e, f, k in np.asarray(prob.get("robin_faces", np.zeros((0, 3))), dtype=np.int64).reshape(-1, 3):
+            fp, fw, es, et_ = el.face_rule(et, int(f))
+            Nf, dNf = el.shape(et, fp)
+            J0f = np.einsum("ai,qaj->qij", Xe[e], dNf)
+            Aref = np.cross(J0f @ es, J0f @ et_)
+            area = np.linalg.norm(Aref, axis=1)
+            self.robin.append((int(e), Nf, Aref / area[:, None], fw * area, sets[int(k)]))
+        # consistent mass: shape values at the volume points
+        self.Nq = N
+        self.rho = float(prob.get("rho", 0.0))
+        self.time = None
+
+    def set_time_state(self, dt, d_prev, d_prev2):
+        """Backward-Euler time step dt with the two previous displacements
+        (free-DoF vectors); dt = None returns to the quasi-static problem."""
+        if dt is None:
+            self.time = None
+        else:
+            self.time = (float(dt), np.asarray(d_prev, dtype=float), np.asarray(d_prev2, dtype=float))
+
+    def _robin_matrix(self, Nn, par, dt):
+        """3x3 stiffness of the Robin traction at one point, d g / d d^n."""
+        kp = par["k_perp"] + (par["c_perp"] / dt if dt else 0.0)
+        kt = par["k_par"] + (par["c_par"] / dt if dt else 0.0)
+        nn = np.einsum("qi,qk->qik", Nn, Nn)
+        return kp * nn + kt * (np.eye(3) - nn)
 
     # -- helpers ---------------------------------------------------------
     def full_displacement(self, d_free):
@@ -104,6 +144,23 @@ class FEProblem:
             cof = Jf[:, None, None] * np.swapaxes(np.linalg.inv(Ff), -1, -2)
             t = p * np.einsum("qiJ,qJ->qi", cof, Aref)     # p J F^-T N dA
             rf.append((e, np.einsum("q,qa,qi->ai", fw, Nf, t)))
+        if self.time is not None and self.rho > 0.0:
+            dt, dp, dpp = self.time
+            acc = self.full_displacement(np.asarray(d_free) - 2.0 * dp + dpp)
+            aq = np.einsum("qa,eai->eqi", self.Nq, acc[self.elems])
+            re = re + self.rho / dt ** 2 * np.einsum("qa,eqi,eq->eai", self.Nq, aq, self.wdet)
+        if self.robin:
+            dt = self.time[0] if self.time is not None else None
+            vel = self.full_displacement((np.asarray(d_free) - self.time[1]) / dt) if dt else None
+            for e, Nf, Nn, wa, par in self.robin:
+                uq = Nf @ u[self.elems[e]]
+                nn = np.einsum("qi,qk->qik", Nn, Nn)
+                tan = np.eye(3) - nn
+                g = par["k_perp"] * np.einsum("qik,qk->qi", nn, uq) + par["k_par"] * np.einsum("qik,qk->qi", tan, uq)
+                if vel is not None:
+                    vq = Nf @ vel[self.elems[e]]
+                    g = g + par["c_perp"] * np.einsum("qik,qk->qi", nn, vq) + par["c_par"] * np.einsum("qik,qk->qi", tan, vq)
+                rf.append((e, np.einsum("q,qa,qi->ai", wa, Nf, g)))
         return re, rf
 
     def residual(self, d_free, lam):
@@ -137,6 +194,14 @@ class FEProblem:
             dt = p * np.einsum("qiJkL,qJ->qikL", dcof, Aref)
             Kf.append((e, np.einsum("q,qa,qikL,qbL->aibk", fw, Nf, dt,
                                     dNdXf)))
+        if self.time is not None and self.rho > 0.0:
+            dt = self.time[0]
+            M = np.einsum("qa,qb,eq->eab", self.Nq, self.Nq, self.wdet)
+            Ke = Ke + self.rho / dt ** 2 * np.einsum("eab,ik->eaibk", M, np.eye(3))
+        dt = self.time[0] if self.time is not None else None
+        for e, Nf, Nn, wa, par in self.robin:
+            Kq = self._robin_matrix(Nn, par, dt)
+            Kf.append((e, np.einsum("q,qa,qik,qb->aibk", wa, Nf, Kq, Nf)))
         return Ke, Kf
 
     def assemble(self, Ke, Kf, elem_subset=None, dof_map=None, n_dof=None):
