@@ -113,6 +113,16 @@ typedef struct {
   double gamma;                /* activation gamma at load factor 1 (Pa)    */
   const double* fiber_nodal;   /* [n_nodes][6] for CBDDC_FIBER_NODAL, else
                                   ignored (may be NULL)                     */
+  /* Time-dependent terms (Section 2; active with fem_set_time_state).
+     rho: density of the inertia term rho (d^n - 2 d^{n-1} + d^{n-2})/dt^2
+     (consistent mass; 0 = none).  Robin faces carry the generalized Robin
+     condition of Eq. (bc epi): traction -[(N x N)(K_perp d + C_perp v) +
+     (I - N x N)(K_par d + C_par v)], N the reference outward normal and
+     v = (d^n - d^{n-1})/dt (v = 0 without a time state). */
+  double rho;
+  int n_robin_faces;
+  const int32_t* robin_faces;  /* [n][3] (element, local face, set 0 or 1)  */
+  double robin[2][4];          /* per set: K_perp, K_par, C_perp, C_par    */
 } fem_problem_desc;
 
 typedef struct fem_problem fem_problem;
@@ -178,6 +188,17 @@ CBDDC_API int fem_tangent_copy(const fem_problem* P, double* vals, int32_t* row_
 
 /* y = K x with the last assembled tangent.  x, y: dev [n_free]. */
 CBDDC_API int fem_spmv(fem_problem* P, const double* x, double* y, cbddc_stream_t stream);
+
+/* Time state of the backward-Euler step (Section 2, time discretization):
+   with dt > 0 the residual and tangent gain the inertia term
+   rho (d - 2 d_prev + d_prev2)/dt^2 (the printed /dt read as /dt^2) and the
+   damping part C v, v = (d - d_prev)/dt, of the Robin traction; dt = 0
+   returns to the quasi-static problem (Robin springs only).  d_prev and
+   d_prev2: device FP64 [n_free], borrowed: they must stay valid and hold
+   their values while the state is set (until dt = 0 or destroy).  Host
+   call, no device work. */
+CBDDC_API int fem_set_time_state(fem_problem* P, double dt, const double* d_prev,
+                                 const double* d_prev2);
 
 /* ---------------------------------------------------------------- BDDC */
 

@@ -31,7 +31,7 @@ MAX_RECORDS = 512
 
 EXPORTED_SYMBOLS = [
     "fem_problem_create", "fem_problem_destroy", "fem_problem_get_info",
-    "fem_residual", "fem_assemble_tangent", "fem_tangent_copy", "fem_spmv",
+    "fem_residual", "fem_assemble_tangent", "fem_tangent_copy", "fem_spmv", "fem_set_time_state",
     "bddc_setup", "bddc_apply", "bddc_apply_noalloc", "bddc_destroy", "bddc_get_info",
     "gmres_solve", "newton_step", "newton_step_host", "newton_gmres_solve",
     "cbddc_kernel_launches", "cbddc_timer_start", "cbddc_timer_stop",
@@ -67,6 +67,8 @@ class _Desc(ctypes.Structure):
         ("fiber_kind", ctypes.c_int), ("fiber_params", ctypes.c_double * 8),
         ("material", ctypes.c_double * 8), ("pressure", ctypes.c_double),
         ("gamma", ctypes.c_double), ("fiber_nodal", _dp),
+        ("rho", ctypes.c_double), ("n_robin_faces", ctypes.c_int), ("robin_faces", _i32p),
+        ("robin", (ctypes.c_double * 4) * 2),
     ]
 
 
@@ -156,6 +158,7 @@ def load_library():
         "fem_residual": (c_int, [vp, vp, c_double, vp, vp]),
         "fem_assemble_tangent": (c_int, [vp, vp, c_double, vp, ctypes.POINTER(_Tangent), vp]),
         "fem_spmv": (c_int, [vp, vp, vp, vp]),
+        "fem_set_time_state": (c_int, [vp, c_double, vp, vp]),
         "fem_tangent_copy": (c_int, [vp, vp, vp, vp, vp]),
         "bddc_setup": (c_int, [vp, ctypes.POINTER(_Tangent), ctypes.POINTER(_BddcOptions),
                                ctypes.POINTER(vp), vp]),
@@ -314,6 +317,14 @@ class Problem:
             d.material[i] = float(mat[k])
         d.pressure = float(prob["pressure"])
         d.gamma = float(prob["gamma"])
+        # time-dependent terms: density and Robin faces (optional keys)
+        d.rho = float(prob.get("rho", 0.0))
+        rf = np.asarray(prob.get("robin_faces", np.zeros((0, 3))), dtype=np.int32).reshape(-1, 3)
+        d.n_robin_faces = rf.shape[0]
+        d.robin_faces = i32(rf)
+        for q, par in enumerate(prob.get("robin", [])[:2]):
+            for c, key in enumerate(("k_perp", "k_par", "c_perp", "c_par")):
+                d.robin[q][c] = float(par[key])
         h = ctypes.c_void_p()
         _check(lib.fem_problem_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -364,6 +375,19 @@ class Problem:
         import torch
         _check(_LIB.fem_spmv(self._h, _ptr(x, torch.float64), _ptr(y, torch.float64), _stream()))
         return y
+
+    def set_time_state(self, dt, d_prev=None, d_prev2=None):
+        """Backward-Euler step dt with the two previous displacements (CUDA
+        FP64 tensors, kept referenced here while the state is set); dt = 0
+        returns to the quasi-static problem."""
+        import torch
+        if dt and dt > 0:
+            self._time_keep = (d_prev, d_prev2)
+            _check(_LIB.fem_set_time_state(self._h, float(dt), _ptr(d_prev, torch.float64),
+                                           _ptr(d_prev2, torch.float64)))
+        else:
+            _check(_LIB.fem_set_time_state(self._h, 0.0, None, None))
+            self._time_keep = None
 
     def tangent_to_host(self):
         """Copies the last tangent to host numpy arrays:

@@ -287,6 +287,17 @@ int fem_spmv(fem_problem* P, const double* x, double* y, cbddc_stream_t stream) 
   });
 }
 
+int fem_set_time_state(fem_problem* P, double dt, const double* d_prev, const double* d_prev2) {
+  return guard([&] {
+    CB_CHECK(P != nullptr, CBDDC_EINVAL, "null problem");
+    CB_CHECK(dt >= 0.0 && std::isfinite(dt), CBDDC_EINVAL, "dt must be finite and >= 0");
+    if (dt > 0.0) CB_CHECK(d_prev && d_prev2, CBDDC_EINVAL, "previous displacements missing");
+    P->dt = dt;
+    P->d_prev = dt > 0.0 ? d_prev : nullptr;
+    P->d_prev2 = dt > 0.0 ? d_prev2 : nullptr;
+  });
+}
+
 int bddc_setup(fem_problem* P, const fem_tangent* K, const bddc_options* opt, bddc_ctx** inout,
                cbddc_stream_t stream) {
   return guard([&] {

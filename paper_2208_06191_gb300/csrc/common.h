@@ -108,7 +108,12 @@ struct fem_problem {
   // description
   int elem_type = 0, order = 1, n_en = 8, n_qp = 8, n_fn = 4, n_fqp = 4;
   bool tet = false;                         // tetrahedra (else hexahedra)
-  int n_nodes = 0, n_el = 0, n_parts = 0, n_faces = 0;
+  int n_nodes = 0, n_el = 0, n_parts = 0, n_faces = 0, n_robin = 0;
+  double rho = 0.0, robin_par[2][4] = {{0}};  // density; Robin K_perp, K_par, C_perp, C_par
+  // time state (fem_set_time_state): dt > 0 switches inertia and damping on
+  double dt = 0.0;
+  const double* d_prev = nullptr;           // borrowed device vectors [n_free]
+  const double* d_prev2 = nullptr;
   int64_t n_free_nodes = 0, n_free = 0, nnzb = 0;
   int fiber_kind = 0;
   double fiber[8] = {0};
@@ -126,7 +131,9 @@ struct fem_problem {
   cbddc::DVec<double> coords;               // n_nodes*3
   cbddc::DVec<double> fib_nodal;            // n_nodes*6 (f, n) for nodal fibres
   cbddc::DVec<int> elems;                   // n_el*n_en
-  cbddc::DVec<int> face_nodes;              // n_faces*n_fn (outward order)
+  cbddc::DVec<int> face_nodes;              // (n_faces+n_robin)*n_fn (outward order)
+  cbddc::DVec<int> robin_set;               // n_robin parameter-set ids
+  cbddc::DVec<double> acc_full, vel_full;   // n_nodes*3: d-2d'+d'', (d-d')/dt
   cbddc::DVec<int> free_nodes;              // n_free_nodes -> node id
   cbddc::DVec<double> d_full;               // n_nodes*3 displacement
   cbddc::DVec<double> contrib;              // 3x3 blocks of element/face matrices

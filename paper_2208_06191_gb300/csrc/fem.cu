@@ -186,6 +186,7 @@ struct MatParams {
   double fz0, fz1, fa0, fa1;  // slab helix fibre field
   double gamma, pressure;
   int nodal;                  // fibres from interpolated nodal (f, n)
+  double rho_dt2;             // rho / dt^2 of the inertia term (0: off)
 };
 
 __device__ inline double det3(const double A[3][3]) {
@@ -376,7 +377,7 @@ template <int K, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 element_kernel(MatParams mp, const double* __restrict__ coords, const int* __restrict__ elems,
                const double* __restrict__ fib, const double* __restrict__ d_full,
-               double* __restrict__ rcontrib,
+               const double* __restrict__ acc_full, double* __restrict__ rcontrib,
                double* __restrict__ contrib, int* __restrict__ status, int want_tangent) {
   constexpr int M = K + 1, NEN = M * M * M, NQ = NEN;
   constexpr int O = K - 1;
@@ -386,7 +387,9 @@ element_kernel(MatParams mp, const double* __restrict__ coords, const int* __res
   __shared__ double Pq[NQ][9];
   __shared__ double Aq[NQ][81];
   __shared__ double T[NEN * 27];
+  __shared__ double Nq[NQ][NEN], Aq3[NQ][3];  // shape values; d - 2d' + d'' at the points
   __shared__ int bad;
+  const bool inertia = mp.rho_dt2 > 0.0;
   const int e = blockIdx.x;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
@@ -408,6 +411,7 @@ element_kernel(MatParams mp, const double* __restrict__ coords, const int* __res
       const double dn[3] = {c_dL[O][qx][ax] * ly * lz, lx * c_dL[O][qy][ay] * lz,
                             lx * ly * c_dL[O][qz][az]};
       const double n = lx * ly * lz;
+      Nq[q][a] = n;
       for (int i = 0; i < 3; ++i) {
         Xq[i] += n * X[a][i];
         for (int j = 0; j < 3; ++j) J0[i][j] += X[a][i] * dn[j];
@@ -419,6 +423,14 @@ element_kernel(MatParams mp, const double* __restrict__ coords, const int* __res
       G[q][a][0] = dn[0];
       G[q][a][1] = dn[1];
       G[q][a][2] = dn[2];
+    }
+    if (inertia) {
+      double aq[3] = {0, 0, 0};
+      for (int a = 0; a < NEN; ++a) {
+        const double* va = acc_full + (int64_t)elems[(int64_t)e * NEN + a] * 3;
+        for (int i = 0; i < 3; ++i) aq[i] += Nq[q][a] * va[i];
+      }
+      for (int i = 0; i < 3; ++i) Aq3[q][i] = aq[i];
     }
     double J0i[3][3];
     const double det0 = inv3(J0, J0i);
@@ -453,6 +465,8 @@ element_kernel(MatParams mp, const double* __restrict__ coords, const int* __res
     for (int q = 0; q < NQ; ++q)
       r += Wd[q] * (Pq[q][i * 3 + 0] * G[q][a][0] + Pq[q][i * 3 + 1] * G[q][a][1] +
                     Pq[q][i * 3 + 2] * G[q][a][2]);
+    if (inertia)
+      for (int q = 0; q < NQ; ++q) r += mp.rho_dt2 * Wd[q] * Nq[q][a] * Aq3[q][i];
     rcontrib[((int64_t)e * NEN + a) * 3 + i] = r;
   }
   if (!want_tangent) return;
@@ -483,6 +497,21 @@ element_kernel(MatParams mp, const double* __restrict__ coords, const int* __res
       }
     }
   }
+  if (inertia) {
+    // consistent mass rho/dt^2 sum_q w detJ0 N_a N_b on the diagonal i = k
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int t = tid + j * THREADS;
+      if (t < NE) {
+        const int a = t / (NEN * 9), b = (t / 9) % NEN, i = (t % 9) / 3, k = t % 3;
+        if (i == k) {
+          double m = 0.0;
+          for (int q = 0; q < NQ; ++q) m += Wd[q] * Nq[q][a] * Nq[q][b];
+          acc[j] += mp.rho_dt2 * m;
+        }
+      }
+    }
+  }
 #pragma unroll
   for (int j = 0; j < PER; ++j) {
     const int t = tid + j * THREADS;
@@ -506,14 +535,16 @@ template <int NEN, int NQ, int O>
 __global__ void __launch_bounds__(TET_THREADS)
 qp_element_kernel(MatParams mp, const double* __restrict__ coords, const int* __restrict__ elems,
                   const double* __restrict__ fib, const double* __restrict__ d_full,
-                  double* __restrict__ rcontrib, double* __restrict__ contrib,
-                  int* __restrict__ status, int want_tangent, int n_el) {
+                  const double* __restrict__ acc_full, double* __restrict__ rcontrib,
+                  double* __restrict__ contrib, int* __restrict__ status, int want_tangent, int n_el) {
   constexpr int EPB = TET_THREADS / NQ;
   static_assert(EPB * NQ == TET_THREADS, "whole elements per CTA");
   __shared__ double As[TET_THREADS * 81];
   __shared__ double Ps[TET_THREADS * 9];
   __shared__ double Gs[TET_THREADS][NEN][3];
   __shared__ double Xs[EPB][NEN][3], Us[EPB][NEN][3];
+  __shared__ double Wq[TET_THREADS], Aq3[TET_THREADS][3];  // w detJ0 and the point's d - 2d' + d''
+  const bool inertia = mp.rho_dt2 > 0.0;
   __shared__ int Ns[EPB][NEN];
   __shared__ int bad;
   const int tid = threadIdx.x;
@@ -565,6 +596,13 @@ qp_element_kernel(MatParams mp, const double* __restrict__ coords, const int* __
       if (mp.nodal) frame_from_fn(fq, nq, R);
       else fibre_frame(mp, Xq, R);
       ok = det0 > 0.0 && material_point(mp, F, R, P, want_tangent ? A : nullptr);
+      if (inertia) {
+        double aq[3] = {0, 0, 0};
+        for (int a = 0; a < NEN; ++a)
+          for (int i = 0; i < 3; ++i) aq[i] += c_tN[O][q][a] * acc_full[(int64_t)Ns[el][a] * 3 + i];
+        for (int i = 0; i < 3; ++i) Aq3[p][i] = aq[i];
+      }
+      Wq[p] = c_tw[O][q] * det0;
       if (ok) {
         const double wd = c_tw[O][q] * det0;
         for (int i = 0; i < 9; ++i) P[i] *= wd;
@@ -575,6 +613,8 @@ qp_element_kernel(MatParams mp, const double* __restrict__ coords, const int* __
       }
     }
     if (!ok) {
+      Wq[p] = 0.0;
+      Aq3[p][0] = Aq3[p][1] = Aq3[p][2] = 0.0;
       for (int i = 0; i < 9; ++i) P[i] = 0.0;
       for (int i = 0; i < 81; ++i) A[i] = 0.0;
       for (int a = 0; a < NEN; ++a) Gs[p][a][0] = Gs[p][a][1] = Gs[p][a][2] = 0.0;
@@ -590,6 +630,7 @@ qp_element_kernel(MatParams mp, const double* __restrict__ coords, const int* __
       const int p = el * NQ + q;
       r += Ps[p * 9 + i * 3 + 0] * Gs[p][a][0] + Ps[p * 9 + i * 3 + 1] * Gs[p][a][1] +
            Ps[p * 9 + i * 3 + 2] * Gs[p][a][2];
+      if (inertia) r += mp.rho_dt2 * Wq[p] * c_tN[O][q][a] * Aq3[p][i];
     }
     rcontrib[((e0 + el) * NEN + a) * 3 + i] = r;
   }
@@ -609,6 +650,11 @@ qp_element_kernel(MatParams mp, const double* __restrict__ coords, const int* __
       const double T2 = g0 * A[2] + g1 * A[11] + g2 * A[20];
 #pragma unroll
       for (int b = 0; b < NEN; ++b) acc[b] += T0 * Gs[p][b][0] + T1 * Gs[p][b][1] + T2 * Gs[p][b][2];
+      if (inertia && i == k) {
+        const double wa = mp.rho_dt2 * Wq[p] * c_tN[O][q][a];
+#pragma unroll
+        for (int b = 0; b < NEN; ++b) acc[b] += wa * c_tN[O][q][b];
+      }
     }
     double* out = contrib + ((e0 + el) * NEN * NEN + (int64_t)a * NEN) * 9 + i * 3 + k;
 #pragma unroll
@@ -662,6 +708,122 @@ tri_face_kernel(double pressure, const double* __restrict__ coords, const int* _
     }
     contrib[(int64_t)f * NE + t] = pressure * v;
   }
+}
+
+
+// Generalized Robin condition of Eq. (bc epi) on one face per CTA: traction
+// g = (N x N)(K_perp u + C_perp v) + (I - N x N)(K_par u + C_par v) with the
+// reference unit normal N, u the displacement and v = (d - d_prev)/dt at the
+// face points (v = 0 without a time state); residual N_a g dS and tangent
+// N_a N_b [(N x N) k_perp + (I - N x N) k_par] dS, k = K + C / dt.  TRI
+// selects the triangle rules (tetrahedra) or the tensor rules (hexahedra).
+struct RobinParams {
+  double par[2][4];  // K_perp, K_par, C_perp, C_par per set
+  double inv_dt;     // 1/dt, 0 without a time state
+};
+
+template <bool TRI, int K, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+robin_face_kernel(RobinParams rp, const double* __restrict__ coords, const int* __restrict__ face_nodes,
+                  const int* __restrict__ robin_set, const double* __restrict__ d_full,
+                  const double* __restrict__ vel_full, double* __restrict__ rcontrib,
+                  double* __restrict__ contrib, int want_tangent) {
+  constexpr int M = K + 1;
+  constexpr int NFN = TRI ? (K == 1 ? 3 : 6) : M * M;
+  constexpr int NQ = TRI ? (K == 1 ? 1 : 3) : M * M;
+  constexpr int O = K - 1;
+  __shared__ double X[NFN][3], U[NFN][3], Vv[NFN][3];
+  __shared__ double Nn[NQ][3], wa[NQ], gq[NQ][3];
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x;
+  // face shape value / derivatives at point q for node a
+  auto shp = [&](int q, int a, double& n, double& ds, double& dt) {
+    if constexpr (TRI) {
+      n = c_fN[O][q][a]; ds = c_fds[O][q][a]; dt = c_fdt[O][q][a];
+    } else {
+      const int qs = q % M, qt = q / M, as = a % M, at = a / M;
+      n = c_L[O][qs][as] * c_L[O][qt][at];
+      ds = c_dL[O][qs][as] * c_L[O][qt][at];
+      dt = c_L[O][qs][as] * c_dL[O][qt][at];
+    }
+  };
+  auto wq = [&](int q) -> double {
+    if constexpr (TRI) return c_fw[O][q];
+    else return c_w[O][q % M] * c_w[O][q / M];
+  };
+  const double* par = rp.par[robin_set[f]];
+  const double kp = par[0], kt = par[1], cp = par[2], ct = par[3];
+  for (int t = tid; t < NFN * 3; t += THREADS) {
+    const int a = t / 3, c = t % 3;
+    const int node = face_nodes[(int64_t)f * NFN + a];
+    X[a][c] = coords[(int64_t)node * 3 + c];
+    U[a][c] = d_full[(int64_t)node * 3 + c];
+    Vv[a][c] = vel_full ? vel_full[(int64_t)node * 3 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int q = tid; q < NQ; q += THREADS) {
+    double xs[3] = {0, 0, 0}, xt[3] = {0, 0, 0}, u[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+    for (int a = 0; a < NFN; ++a) {
+      double n, ds, dt;
+      shp(q, a, n, ds, dt);
+      for (int i = 0; i < 3; ++i) {
+        xs[i] += ds * X[a][i];
+        xt[i] += dt * X[a][i];
+        u[i] += n * U[a][i];
+        v[i] += n * Vv[a][i];
+      }
+    }
+    const double A[3] = {xs[1] * xt[2] - xs[2] * xt[1], xs[2] * xt[0] - xs[0] * xt[2],
+                         xs[0] * xt[1] - xs[1] * xt[0]};
+    const double area = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+    const double N[3] = {A[0] / area, A[1] / area, A[2] / area};
+    const double un = N[0] * u[0] + N[1] * u[1] + N[2] * u[2];
+    const double vn = N[0] * v[0] + N[1] * v[1] + N[2] * v[2];
+    for (int i = 0; i < 3; ++i) {
+      Nn[q][i] = N[i];
+      gq[q][i] = kp * un * N[i] + kt * (u[i] - un * N[i]) + cp * vn * N[i] + ct * (v[i] - vn * N[i]);
+    }
+    wa[q] = wq(q) * area;
+  }
+  __syncthreads();
+  for (int t = tid; t < NFN * 3; t += THREADS) {
+    const int a = t / 3, i = t % 3;
+    double r = 0.0;
+    for (int q = 0; q < NQ; ++q) {
+      double n, ds, dt;
+      shp(q, a, n, ds, dt);
+      r += wa[q] * n * gq[q][i];
+    }
+    rcontrib[((int64_t)f * NFN + a) * 3 + i] = r;
+  }
+  if (!want_tangent) return;
+  const double kpe = kp + cp * rp.inv_dt, kte = kt + ct * rp.inv_dt;
+  constexpr int NE = NFN * NFN * 9;
+  for (int t = tid; t < NE; t += THREADS) {
+    const int a = t / (NFN * 9), b = (t / 9) % NFN, i = (t % 9) / 3, k = t % 3;
+    double v = 0.0;
+    for (int q = 0; q < NQ; ++q) {
+      double na, nb, ds, dt;
+      shp(q, a, na, ds, dt);
+      shp(q, b, nb, ds, dt);
+      const double nn = Nn[q][i] * Nn[q][k];
+      v += wa[q] * na * nb * (kpe * nn + kte * ((i == k ? 1.0 : 0.0) - nn));
+    }
+    contrib[(int64_t)f * NE + t] = v;
+  }
+}
+
+// d_full-style node arrays of the time state: acc = d - 2 d_prev + d_prev2
+// and vel = (d - d_prev)/dt at the free nodes (Dirichlet nodes stay zero).
+__global__ void time_vectors_kernel(const double* __restrict__ d, const double* __restrict__ dp,
+                                    const double* __restrict__ dpp, const int* __restrict__ free_nodes,
+                                    int64_t n_free_nodes, double inv_dt, double* __restrict__ acc,
+                                    double* __restrict__ vel) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= 3 * n_free_nodes) return;
+  const int64_t j = (int64_t)free_nodes[i / 3] * 3 + i % 3;
+  acc[j] = d[i] - 2.0 * dp[i] + dpp[i];
+  vel[j] = (d[i] - dp[i]) * inv_dt;
 }
 
 // Follower pressure on one face per CTA: residual p (x_s x x_t) N_a and its
@@ -770,6 +932,7 @@ MatParams make_params(const fem_problem* P, double lam) {
   m.gamma = lam * P->gamma;
   m.pressure = lam * P->pressure;
   m.nodal = P->fiber_kind == CBDDC_FIBER_NODAL ? 1 : 0;
+  m.rho_dt2 = (P->dt > 0.0 && P->rho > 0.0) ? P->rho / (P->dt * P->dt) : 0.0;
   return m;
 }
 
@@ -779,6 +942,20 @@ void assemble(fem_problem* P, const double* d, double lam, double* residual, boo
   const int64_t nf = P->n_free_nodes;
   scatter_free_kernel<<<cdiv(3 * nf, 256), 256, 0, s>>>(d, P->free_nodes.p, nf, P->d_full.p);
   CB_LAUNCH();
+  // time state: d - 2 d_prev + d_prev2 and (d - d_prev)/dt as node arrays
+  const bool timed = P->dt > 0.0;
+  if (timed) {
+    if (!P->acc_full.p) {
+      P->acc_full.alloc((size_t)P->n_nodes * 3);
+      P->vel_full.alloc((size_t)P->n_nodes * 3);
+      CB_CUDA(cudaMemsetAsync(P->acc_full.p, 0, P->acc_full.bytes(), s));
+      CB_CUDA(cudaMemsetAsync(P->vel_full.p, 0, P->vel_full.bytes(), s));
+    }
+    time_vectors_kernel<<<cdiv(3 * nf, 256), 256, 0, s>>>(d, P->d_prev, P->d_prev2, P->free_nodes.p, nf,
+                                                          1.0 / P->dt, P->acc_full.p, P->vel_full.p);
+    CB_LAUNCH();
+  }
+  const double* accf = timed ? P->acc_full.p : nullptr;
   double* fc = P->contrib.p + P->n_elem_blocks * 9;
   double* fr = P->rcontrib.p + P->n_elem_vec * 3;
   const int wt = want_tangent ? 1 : 0;
@@ -789,19 +966,19 @@ void assemble(fem_problem* P, const double* d, double lam, double* residual, boo
     const int grid = (int)cdiv(P->n_el, epb);
     if (P->tet && P->order == 1)
       qp_element_kernel<4, 1, 0><<<grid, TET_THREADS, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
-                                                              P->rcontrib.p, P->contrib.p, P->status.p, wt,
+                                                              accf, P->rcontrib.p, P->contrib.p, P->status.p, wt,
                                                               P->n_el);
     else if (P->tet)
       qp_element_kernel<10, 4, 1><<<grid, TET_THREADS, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
-                                                               P->rcontrib.p, P->contrib.p, P->status.p, wt,
+                                                               accf, P->rcontrib.p, P->contrib.p, P->status.p, wt,
                                                                P->n_el);
     else
       qp_element_kernel<8, 8, 2><<<grid, TET_THREADS, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
-                                                              P->rcontrib.p, P->contrib.p, P->status.p, wt,
+                                                              accf, P->rcontrib.p, P->contrib.p, P->status.p, wt,
                                                               P->n_el);
   } else {
     element_kernel<2, 256><<<P->n_el, 256, 0, s>>>(mp, P->coords.p, P->elems.p, fib, P->d_full.p,
-                                                    P->rcontrib.p, P->contrib.p, P->status.p, wt);
+                                                    accf, P->rcontrib.p, P->contrib.p, P->status.p, wt);
   }
   CB_LAUNCH();
   {
@@ -828,6 +1005,30 @@ void assemble(fem_problem* P, const double* d, double lam, double* residual, boo
     else
       face_kernel<2, 128><<<P->n_faces, 128, 0, s>>>(mp.pressure, P->coords.p, P->face_nodes.p,
                                                       P->d_full.p, fr, fc, wt);
+    CB_LAUNCH();
+  }
+  if (P->n_robin) {
+    RobinParams rp;
+    for (int q = 0; q < 2; ++q)
+      for (int c = 0; c < 4; ++c) rp.par[q][c] = P->robin_par[q][c];
+    rp.inv_dt = timed ? 1.0 / P->dt : 0.0;
+    const int nfn = P->n_fn;
+    const int* rfn = P->face_nodes.p + (int64_t)P->n_faces * nfn;
+    double* rr = fr + (int64_t)P->n_faces * nfn * 3;
+    double* rc = fc + (int64_t)P->n_faces * nfn * nfn * 9;
+    const double* vel = timed ? P->vel_full.p : nullptr;
+    if (P->tet && P->order == 1)
+      robin_face_kernel<true, 1, 32><<<P->n_robin, 32, 0, s>>>(rp, P->coords.p, rfn, P->robin_set.p, P->d_full.p,
+                                                               vel, rr, rc, wt);
+    else if (P->tet)
+      robin_face_kernel<true, 2, 64><<<P->n_robin, 64, 0, s>>>(rp, P->coords.p, rfn, P->robin_set.p, P->d_full.p,
+                                                               vel, rr, rc, wt);
+    else if (P->order == 1)
+      robin_face_kernel<false, 1, 64><<<P->n_robin, 64, 0, s>>>(rp, P->coords.p, rfn, P->robin_set.p,
+                                                                P->d_full.p, vel, rr, rc, wt);
+    else
+      robin_face_kernel<false, 2, 128><<<P->n_robin, 128, 0, s>>>(rp, P->coords.p, rfn, P->robin_set.p,
+                                                                  P->d_full.p, vel, rr, rc, wt);
     CB_LAUNCH();
   }
   if (residual) {

@@ -240,6 +240,16 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
   P->n_el = d->n_elems;
   P->n_parts = d->n_parts;
   P->n_faces = d->n_pressure_faces;
+  P->n_robin = d->n_robin_faces;
+  CB_CHECK(P->n_faces >= 0 && P->n_robin >= 0, CBDDC_EINVAL, "negative face count");
+  CB_CHECK(P->n_robin == 0 || d->robin_faces != nullptr, CBDDC_EINVAL, "Robin faces missing");
+  CB_CHECK(d->rho >= 0.0, CBDDC_EINVAL, "negative density");
+  P->rho = d->rho;
+  for (int q = 0; q < 2; ++q)
+    for (int c = 0; c < 4; ++c) {
+      CB_CHECK(d->robin[q][c] >= 0.0, CBDDC_EINVAL, "negative Robin coefficient");
+      P->robin_par[q][c] = d->robin[q][c];
+    }
   P->fiber_kind = d->fiber_kind;
   for (int i = 0; i < 8; ++i) { P->fiber[i] = d->fiber_params[i]; P->mat[i] = d->material[i]; }
   P->pressure = d->pressure;
@@ -268,13 +278,23 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
   const int64_t nf = P->n_free_nodes;
   const std::vector<int>& n2f = P->node_to_free;
 
-  // pressure faces -> node lists
+  // pressure faces, then Robin faces -> node lists
   const int nfn = P->n_fn;
-  std::vector<int> face_nodes((size_t)P->n_faces * nfn);
-  std::vector<int> face_elem(P->n_faces);
-  for (int f = 0; f < P->n_faces; ++f) {
-    int e = d->pressure_faces[2 * f], lf = d->pressure_faces[2 * f + 1];
-    CB_CHECK(e >= 0 && e < ne && lf >= 0 && lf < n_lfaces, CBDDC_EINVAL, "bad pressure face");
+  const int n_all_faces = P->n_faces + P->n_robin;
+  std::vector<int> face_nodes((size_t)n_all_faces * nfn);
+  std::vector<int> face_elem(n_all_faces);
+  std::vector<int> robin_set(P->n_robin);
+  for (int f = 0; f < n_all_faces; ++f) {
+    const bool rob = f >= P->n_faces;
+    const int g = rob ? f - P->n_faces : f;
+    int e = rob ? d->robin_faces[3 * g] : d->pressure_faces[2 * f];
+    int lf = rob ? d->robin_faces[3 * g + 1] : d->pressure_faces[2 * f + 1];
+    CB_CHECK(e >= 0 && e < ne && lf >= 0 && lf < n_lfaces, CBDDC_EINVAL,
+             rob ? "bad Robin face" : "bad pressure face");
+    if (rob) {
+      robin_set[g] = d->robin_faces[3 * g + 2];
+      CB_CHECK(robin_set[g] == 0 || robin_set[g] == 1, CBDDC_EINVAL, "Robin parameter set must be 0 or 1");
+    }
     int loc[9];
     face_node_list(tet, k, lf, loc);
     for (int a = 0; a < nfn; ++a) face_nodes[(size_t)f * nfn + a] = P->elems_h[(size_t)e * nen + loc[a]];
@@ -314,9 +334,9 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
 
   // contribution blocks: elements then faces
   P->n_elem_blocks = (int64_t)ne * nen * nen;
-  P->n_face_blocks = (int64_t)P->n_faces * nfn * nfn;
+  P->n_face_blocks = (int64_t)n_all_faces * nfn * nfn;
   P->n_elem_vec = (int64_t)ne * nen;
-  P->n_face_vec = (int64_t)P->n_faces * nfn;
+  P->n_face_vec = (int64_t)n_all_faces * nfn;
   CB_CHECK(P->n_elem_blocks + P->n_face_blocks < INT32_MAX, CBDDC_EINVAL,
            "too many element blocks for 32-bit indices");
   std::vector<std::pair<int64_t, int>> kv;
@@ -334,7 +354,7 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
       }
     }
   }
-  for (int f = 0; f < P->n_faces; ++f) {
+  for (int f = 0; f < n_all_faces; ++f) {
     const int* fn = &face_nodes[(size_t)f * nfn];
     for (int a = 0; a < nfn; ++a) {
       int ra = n2f[fn[a]];
@@ -432,7 +452,7 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
       cpart.push_back(P->part_h[e]);
       cbase.push_back((int64_t)e * nen * nen);
     }
-    for (int f = 0; f < P->n_faces; ++f) {
+    for (int f = 0; f < n_all_faces; ++f) {
       for (int a = 0; a < nfn; ++a) cidx.push_back(face_nodes[(size_t)f * nfn + a]);
       cptr.push_back((int)cidx.size());
       cpart.push_back(P->part_h[face_elem[f]]);
@@ -455,6 +475,7 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
   }
   P->elems.upload(P->elems_h);
   P->face_nodes.upload(face_nodes);
+  P->robin_set.upload(robin_set);
   P->free_nodes.upload(free_nodes);
   P->d_full.alloc((size_t)nn * 3);
   CB_CUDA(cudaMemset(P->d_full.p, 0, P->d_full.bytes()));
@@ -476,7 +497,8 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
 }  // namespace cbddc
 
 int64_t fem_problem::device_bytes() const {
-  return (int64_t)(coords.bytes() + fib_nodal.bytes() + elems.bytes() + face_nodes.bytes() + free_nodes.bytes() +
+  return (int64_t)(coords.bytes() + fib_nodal.bytes() + elems.bytes() + face_nodes.bytes() + robin_set.bytes() +
+                   acc_full.bytes() + vel_full.bytes() + free_nodes.bytes() +
                    d_full.bytes() + contrib.bytes() + rcontrib.bytes() + bsr_row_ptr.bytes() +
                    bsr_col.bytes() + bsr_vals.bytes() + slot_ptr.bytes() + slot_src.bytes() +
                    res_ptr.bytes() + res_src.bytes() + lslot_sub.bytes() + lslot_row.bytes() +
