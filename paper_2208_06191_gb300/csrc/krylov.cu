@@ -6,7 +6,10 @@
 // h = V^T w, w -= V h), Givens rotations and the least-squares residual
 // |g_{j+1}| kept on the device; restart after m steps with the true
 // residual recomputed.
+#include <algorithm>
 #include <cmath>
+
+#include <cooperative_groups.h>
 
 #include "bddc.h"
 #include "fem.h"
@@ -14,9 +17,12 @@
 
 namespace cbddc {
 
+namespace cg = cooperative_groups;
+
 namespace {
 
 constexpr int DOT_THREADS = 256;
+constexpr int64_t kCoopMaxN = 1000000;  // longest vector for the cooperative orthogonalisation
 constexpr int MAXV = 128;       // maximum Krylov vectors per dot launch
 
 __device__ inline double wsum(double v) {
@@ -145,15 +151,13 @@ __global__ void __launch_bounds__(DOT_THREADS) fused_dots_kernel(DotArgs a) {
 // Column j of the Hessenberg matrix from h1 + h2 (the two CGS passes) and
 // ||w||^2, previous rotations, the new rotation and the residual estimate.
 // scal[0] = |g_{j+1}| / ||b||, scal[1] = 1 / h_{j+1,j}, scal[2] = ||b||.
-__global__ void givens_kernel(int j, int m, double* __restrict__ H, double* __restrict__ cs,
-                              double* __restrict__ sn, double* __restrict__ g,
-                              const double* __restrict__ h1, const double* __restrict__ h2,
-                              const double* __restrict__ wn2, double* __restrict__ scal, double rtol,
+__device__ void givens_update(int j, int m, double* __restrict__ H, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g, const double* h1,
+                              const double* h2, double wn2, double* __restrict__ scal, double rtol,
                               int* __restrict__ done, int* __restrict__ iters) {
-  if (*done) return;
   double* col = H + (int64_t)j * (m + 1);
   for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-  const double hn = sqrt(fmax(wn2[0], 0.0));
+  const double hn = sqrt(fmax(wn2, 0.0));
   col[j + 1] = hn;
   scal[1] = hn > 0.0 ? 1.0 / hn : 0.0;
   for (int i = 0; i < j; ++i) {
@@ -172,6 +176,133 @@ __global__ void givens_kernel(int j, int m, double* __restrict__ H, double* __re
   scal[0] = res;
   *iters += 1;
   if (res <= rtol || hn == 0.0) *done = 1;
+}
+
+__global__ void givens_kernel(int j, int m, double* __restrict__ H, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g,
+                              const double* __restrict__ h1, const double* __restrict__ h2,
+                              const double* __restrict__ wn2, double* __restrict__ scal, double rtol,
+                              int* __restrict__ done, int* __restrict__ iters) {
+  if (*done) return;
+  givens_update(j, m, H, cs, sn, g, h1, h2, wn2[0], scal, rtol, done, iters);
+}
+
+// The whole orthogonalisation of one Arnoldi step in one cooperative launch
+// (all CTAs resident, grid-wide barriers): h1 = V^T w; w -= V h1, h2 = V^T w;
+// w -= V h2, ||w||^2; the Givens update (CTA 0) and v_{j+1} = w / ||w||.
+// Row tiles of 256 go to the CTAs round-robin; each warp keeps partial dot
+// products of its columns in registers across tiles, every CTA writes its
+// partials, and after each barrier every CTA sums all CTAs' partials in CTA
+// order (identical on every CTA, independent of scheduling).  This replaces
+// five launches and their tails, which dominate at small n.
+struct CgsArgs {
+  const double* V;   // nvec columns of length n (stride n)
+  int64_t n;
+  int nvec;          // j + 1
+  double* w;
+  double* vnext;     // column j + 1
+  double* part;      // [3][gridDim.x][MAXV]
+  int j, m;
+  double *H, *cs, *sn, *g, *scal;
+  double rtol;
+  int *done, *iters;
+};
+
+__device__ void cgs_phase(const CgsArgs& a, const double* hin, bool norm, double* ws, double* part) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int CPW = MAXV / (DOT_THREADS / 32);  // columns per warp
+  double acc[CPW];
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) acc[q] = 0.0;
+  double nacc = 0.0;
+  const int64_t ntiles = (a.n + DOT_THREADS - 1) / DOT_THREADS;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * DOT_THREADS;
+    const int rows = (int)min((int64_t)DOT_THREADS, a.n - r0);
+    double x = tid < rows ? a.w[r0 + tid] : 0.0;
+    if (hin && tid < rows) {
+      for (int j = 0; j < a.nvec; ++j) x -= a.V[(int64_t)j * a.n + r0 + tid] * hin[j];
+      a.w[r0 + tid] = x;
+    }
+    if (norm) {
+      nacc += x * x;
+    } else {
+      __syncthreads();   // the previous tile's readers of ws are done
+      ws[tid] = x;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) {
+        const int j = warp + (DOT_THREADS / 32) * q;
+        if (j < a.nvec) {
+          const double* Vj = a.V + (int64_t)j * a.n + r0;
+          for (int rr = lane; rr < rows; rr += 32) acc[q] += Vj[rr] * ws[rr];
+        }
+      }
+    }
+  }
+  __shared__ double red[DOT_THREADS / 32];
+  if (norm) {
+    nacc = wsum(nacc);
+    if (lane == 0) red[warp] = nacc;
+    __syncthreads();
+    if (tid == 0) {
+      double sm = 0.0;
+      for (int q = 0; q < DOT_THREADS / 32; ++q) sm += red[q];
+      part[(int64_t)blockIdx.x * MAXV] = sm;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+      const int j = warp + (DOT_THREADS / 32) * q;
+      const double v = wsum(acc[q]);
+      if (lane == 0 && j < a.nvec) part[(int64_t)blockIdx.x * MAXV + j] = v;
+    }
+  }
+}
+
+// sums of every CTA's partials into out[0:nout] (shared memory): 4 threads
+// per output, each over every 4th CTA, combined in a fixed order (identical
+// on every CTA, independent of scheduling)
+__device__ void cgs_reduce(const double* part, int nout, double* out) {
+  __shared__ double red4[4][64];
+  const int jl = threadIdx.x & 63, grp = threadIdx.x >> 6;
+  for (int j0 = 0; j0 < nout; j0 += 64) {
+    const int j = j0 + jl;
+    double sacc = 0.0;
+    if (j < nout)
+      for (unsigned c = grp; c < gridDim.x; c += 4) sacc += __ldcg(part + (int64_t)c * MAXV + j);
+    red4[grp][jl] = sacc;
+    __syncthreads();
+    if (grp == 0 && j < nout) out[j] = (red4[0][jl] + red4[1][jl]) + (red4[2][jl] + red4[3][jl]);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(DOT_THREADS) cgs2_coop_kernel(CgsArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  if (*a.done) return;  // read by every CTA before any barrier: uniform
+  __shared__ double ws[DOT_THREADS];
+  __shared__ double h1[MAXV], h2[MAXV], wn2s[1];
+  const int64_t stride = (int64_t)gridDim.x * MAXV;
+  cgs_phase(a, nullptr, false, ws, a.part);
+  grid.sync();
+  cgs_reduce(a.part, a.nvec, h1);
+  cgs_phase(a, h1, false, ws, a.part + stride);
+  grid.sync();
+  cgs_reduce(a.part + stride, a.nvec, h2);
+  cgs_phase(a, h2, true, ws, a.part + 2 * stride);
+  grid.sync();
+  cgs_reduce(a.part + 2 * stride, 1, wn2s);
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    givens_update(a.j, a.m, a.H, a.cs, a.sn, a.g, h1, h2, wn2s[0], a.scal, a.rtol, a.done, a.iters);
+  // v_{j+1} = w / ||w|| (the same value on every CTA)
+  const double hn = sqrt(fmax(wn2s[0], 0.0));
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  const int64_t ntiles = (a.n + DOT_THREADS - 1) / DOT_THREADS;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r = t * DOT_THREADS + threadIdx.x;
+    if (r < a.n) a.vnext[r] = a.w[r] * inv;
+  }
 }
 
 __global__ void scale_kernel(const double* __restrict__ w, double* __restrict__ v, int64_t n,
@@ -245,6 +376,23 @@ void Gmres::ensure_small(int64_t n_) {
 void Gmres::ensure(int64_t n_, int m_) {
   ensure_small(n_);
   if (n == n_ && m == m_) return;
+  // cooperative orthogonalisation: at most two CTAs per SM, about four row
+  // tiles per CTA; 0 when the device cannot launch cooperatively
+  {
+    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    CB_CUDA(cudaGetDevice(&dev));
+    CB_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    CB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cgs2_coop_kernel, DOT_THREADS, 0));
+    const int64_t tiles = cdiv(n_, DOT_THREADS);
+    // a few row tiles per CTA, so that the cross-CTA sums stay short; long
+    // vectors (n > 1M, bandwidth-bound) keep the multi-launch path with its
+    // larger row tiles
+    coop_grid = (coop && n_ <= kCoopMaxN) ? (int)std::min<int64_t>(std::min(per_sm, 2) * (int64_t)sms,
+                                                                   std::max<int64_t>(1, tiles / 4))
+                                          : 0;
+    if (coop_grid > 0) cpart.alloc((size_t)3 * coop_grid * MAXV);
+  }
   CB_CHECK(m_ >= 1 && m_ < MAXV, CBDDC_EINVAL, "restart must be in [1, 127]");
   n = n_;
   m = m_;
@@ -332,14 +480,23 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
       double* h2 = G.h.p + MAXV;
       double* wn2 = G.h.p + 2 * MAXV;
       timer_begin(CBDDC_TIMER_ORTH, s);
-      fused_dots(G, G.V.p, n, j + 1, G.w.p, n, nullptr, 0, h1, done, s);
-      fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h1, 0, h2, done, s);
-      fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h2, 1, wn2, done, s);
-      givens_kernel<<<1, 1, 0, s>>>(j, m, G.H.p, G.cs.p, G.sn.p, G.g.p, h1, h2, wn2, G.scal.p, rtol, done,
-                                    kcount);
-      CB_LAUNCH();
-      scale_kernel<<<nb, 256, 0, s>>>(G.w.p, G.V.p + (int64_t)(j + 1) * n, n, G.scal.p, 1, done);
-      CB_LAUNCH();
+      if (G.coop_grid > 0) {
+        CgsArgs ca{G.V.p, n, j + 1, G.w.p, G.V.p + (int64_t)(j + 1) * n, G.cpart.p, j, m,
+                   G.H.p, G.cs.p, G.sn.p, G.g.p, G.scal.p, rtol, done, kcount};
+        void* args[] = {&ca};
+        CB_CUDA(cudaLaunchCooperativeKernel((const void*)cgs2_coop_kernel, dim3(G.coop_grid),
+                                            dim3(DOT_THREADS), args, 0, s));
+        CB_LAUNCH();
+      } else {
+        fused_dots(G, G.V.p, n, j + 1, G.w.p, n, nullptr, 0, h1, done, s);
+        fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h1, 0, h2, done, s);
+        fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h2, 1, wn2, done, s);
+        givens_kernel<<<1, 1, 0, s>>>(j, m, G.H.p, G.cs.p, G.sn.p, G.g.p, h1, h2, wn2, G.scal.p, rtol,
+                                      done, kcount);
+        CB_LAUNCH();
+        scale_kernel<<<nb, 256, 0, s>>>(G.w.p, G.V.p + (int64_t)(j + 1) * n, n, G.scal.p, 1, done);
+        CB_LAUNCH();
+      }
       // algorithmic traffic: V read three times (dots, update + dots,
       // update), w read 3x / written 2x, v_{j+1} written
       timer_end(CBDDC_TIMER_ORTH, s, 6.0 * (j + 1) * (double)n,

@@ -13,6 +13,8 @@ struct Gmres {
   DVec<double> V, Zb, w, r, H, cs, sn, g, y, h, partial, scal;
   DVec<int> flags;
   DVec<unsigned> ticket;
+  DVec<double> cpart;        // per-CTA partials of the cooperative orthogonalisation
+  int coop_grid = 0;         // its grid size (0: use the multi-launch path)
   double* host_scal = nullptr;
   int* host_flags = nullptr;
   void ensure_small(int64_t n_);
