@@ -1044,7 +1044,7 @@ static void run_sweep(const DVec<SweepDesc>& desc, int nmat, const std::vector<G
   for (int k = 0; k < (int)lists.size(); ++k) {
     sweep_diag_kernel<T><<<nmat, DIAG_THREADS, 0, s>>>(desc.p, k, mat, Pbuf, status, tol);
     CB_LAUNCH();
-    dim3 grid(cdiv(std::max(maxRows, maxCols), 64), nmat);
+    dim3 grid(cdiv(std::max(maxRows, maxCols), PANEL_CH), nmat);
     sweep_panel_kernel<T><<<grid, 256, 0, s>>>(desc.p, k, mat, Pbuf, X, Y);
     CB_LAUNCH();
     launch_list<T, false, false>(lists[k], X, Y, mat, T(-1), T(1), s);

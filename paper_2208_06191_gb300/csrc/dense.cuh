@@ -441,19 +441,20 @@ sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat
 }
 
 // Builds X and Y panels and zeroes the pivot rows/columns, for indices
-// [blockIdx.x*64, +64) of each matrix (as columns for Y, as rows for X).
-// Reads and writes of different CTAs touch disjoint entries: the Y part
-// reads pivot rows outside the pivot columns, the X part reads pivot
+// [blockIdx.x*PANEL_CH, +PANEL_CH) of each matrix (as columns for Y, as rows
+// for X).  Reads and writes of different CTAs touch disjoint entries: the Y
+// part reads pivot rows outside the pivot columns, the X part reads pivot
 // columns outside the pivot rows (the pivot block itself is read only into
-// Y entries that are replaced by P).  Each thread forms a 4 x 4 block of Y
-// (16 independent FMA chains) and gathers its 16 X entries before storing,
-// so that loads are in flight together.
+// Y entries that are replaced by P).  Narrow chunks keep many CTAs in flight
+// (a single coarse matrix still spreads over the GPU); each thread forms 4
+// rows of one Y column and gathers its 4 X entries before storing.
+constexpr int PANEL_CH = 16;
 template <typename T>
 __global__ void __launch_bounds__(256)
 sweep_panel_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat,
                    const T* __restrict__ Pbuf, T* __restrict__ Xbuf, T* __restrict__ Ybuf) {
-  constexpr int NB = SWEEP_NB, CH = 64, PER = NB * CH / 256;
-  static_assert(NB == 64 && CH == 64, "4 x 4 register tiles over 256 threads");
+  constexpr int NB = SWEEP_NB, CH = PANEL_CH, PER = NB * CH / 256;
+  static_assert(NB == 64 && CH == 16 && PER == 4, "4 x 1 register tiles over 256 threads");
   __shared__ T Ps[NB][NB + 1];
   __shared__ T col[NB][CH + 1];
   const SweepDesc d = desc[blockIdx.y];
@@ -501,36 +502,22 @@ sweep_panel_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ ma
   if (cn == 0) return;
   __syncthreads();
   // Y[r, j] = sum_q P[r][q] A[k0+q, j]  (j outside kk),  Y[:, kk] = P
-  const int ty = tid / 16, tx = tid % 16;
-  T acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  const int ty = tid / CH, c = tid % CH;   // rows 4 ty .. 4 ty + 3 of column c
+  T acc[4] = {T(0), T(0), T(0), T(0)};
   for (int q = 0; q < kb; ++q) {
-    T pr[4], cc[4];
+    const T cq = col[q][c];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) pr[i] = Ps[4 * ty + i][q];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) cc[j] = col[q][4 * tx + j];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fma(pr[i], cc[j], acc[i][j]);
+    for (int i = 0; i < 4; ++i) acc[i] = fma(Ps[4 * ty + i][q], cq, acc[i]);
   }
+  if (c >= cn) return;
+  const int jg = c0 + c;
+  const bool pivc = jg >= k0 && jg < k0 + kb;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = 4 * ty + i;
     if (r >= kb) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = 4 * tx + j;
-      if (c >= cn) continue;
-      const int jg = c0 + c;
-      const T v = (jg >= k0 && jg < k0 + kb) ? Ps[r][jg - k0] : acc[i][j];
-      Y[(int64_t)r * d.ld + jg] = v;
-      A[(int64_t)(k0 + r) * d.ld + jg] = T(0);
-    }
+    Y[(int64_t)r * d.ld + jg] = pivc ? Ps[r][jg - k0] : acc[i];
+    A[(int64_t)(k0 + r) * d.ld + jg] = T(0);
   }
 }
 
