@@ -10,6 +10,8 @@ Setup, per subdomain i (the unassembled local matrix A^(i), A = sum A^(i)):
   which is where the subdomain corners sit when the coordinates are known);
 * primal constraints: vertex values ("V"), and edge ("E") or face ("F")
   arithmetic averages per displacement component (Sections 3.2 and 6.2);
+  with "R", also the rigid-body rotations of every averaged class (the
+  near-null space taken into the primal space, Section 4);
 * counting scaling delta_i^dagger = 1 / #subdomains sharing the DoF;
 * coarse basis Phi_i: the minimum-energy extension of each primal
   constraint (the local saddle-point problem with unit constraint values),
@@ -36,6 +38,33 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.csgraph as csg
 import scipy.sparse.linalg as spla
+
+# Rotational constraints whose squared singular value falls below this
+# fraction of the class's largest are dropped (the rotation about the axis
+# of a straight edge leaves every node of the edge in place).
+RIGID_DROP = 1e-8
+
+
+def class_rotations(X):
+    """Rotational primal constraints of one interface class with node
+    coordinates X (m, 3): the infinitesimal rotations a -> e_k x (x_a - xbar)
+    about the class centroid, k = x, y, z, restricted to the class, as
+    orthonormal rows of length 3m (node-major, xyz per node).  Rotations
+    about the centroid have zero component sums, so the rows are orthogonal
+    to the three averages; together the rows span the rigid motions of the
+    class (Section 4, rigid motions as primal degrees of freedom)."""
+    X = np.asarray(X, dtype=float)
+    y = X - X.mean(axis=0)
+    R = np.zeros((3 * len(X), 3))
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = 1.0
+        R[:, k] = np.cross(e, y).reshape(-1)
+    U, s, _ = np.linalg.svd(R, full_matrices=False)
+    if s.size == 0 or s[0] == 0.0:
+        return np.zeros((0, 3 * len(X)))
+    keep = s ** 2 >= RIGID_DROP * s[0] ** 2
+    return U[:, keep].T
 
 
 def outer_boundary_nodes(fe):
@@ -188,7 +217,10 @@ class BDDC:
     ``part`` (level-2 subdomain of every subdomain of this level),
     ``n_parts`` and ``primal``: the coarse problem is then approximated by
     one application of BDDC on those level-2 subdomains (multilevel BDDC,
-    Section 3.2); a nested ``level2`` entry adds a further level."""
+    Section 3.2); a nested ``level2`` entry adds a further level.
+    ``primal`` holds the letters V, E, F and R (rotations of the averaged
+    classes, fine level of a two-level method only: the rotations need node
+    coordinates, and a coarse node of the multilevel method carries 3 DoFs)."""
 
     def __init__(self, fe, Ke=None, Kf=None, primal="V", classification=None, level2=None):
         level = fe if isinstance(fe, CoarseLevel) else FineLevel(fe, Ke, Kf)
@@ -196,16 +228,24 @@ class BDDC:
         cl = classification or Classification(level)
         self.cl = cl
         use_v = "V" in primal
+        use_r = "R" in primal
+        if use_r and (not isinstance(level, FineLevel) or level2 is not None):
+            raise ValueError("rigid-body constraints need a two-level method on the fine level")
         avg_classes = []
         if "E" in primal:
             avg_classes += cl.edges
         if "F" in primal:
             avg_classes += cl.faces
-        # global primal numbering: vertex DoFs, then 3 averages per class
+        rot = [class_rotations(level.fe.coords[c]) if use_r else np.zeros((0, 3 * len(c)))
+               for c in avg_classes]
+        # global primal numbering: vertex DoFs, then per class its 3 averages
+        # and its rotations
         vert = cl.vertices if use_v else []
-        self.n_pi = 3 * len(vert) + 3 * len(avg_classes)
+        ncls = [3 + r.shape[0] for r in rot]
+        self.n_pi = 3 * len(vert) + int(sum(ncls))
         vpos = {a: 3 * j for j, a in enumerate(vert)}
-        apos = [3 * len(vert) + 3 * j for j in range(len(avg_classes))]
+        apos = list(3 * len(vert) + np.concatenate([[0], np.cumsum(ncls)[:-1]]).astype(int)) \
+            if avg_classes else []
         node_class = {}
         for j, c in enumerate(avg_classes):
             for a in c:
@@ -244,17 +284,22 @@ class BDDC:
             # averages touching this subdomain
             loc_cls = sorted({node_class[a] for a in nodes if a in node_class})
             rows, cols, vals, gA = [], [], [], []
-            for q, j in enumerate(loc_cls):
+            for j in loc_cls:
                 cnodes = avg_classes[j]
                 lidx = np.searchsorted(nodes, cnodes)
                 for c in range(3):
-                    r = 3 * q + c
                     for li in lidx:
-                        rows.append(r)
+                        rows.append(len(gA))
                         cols.append(rpos[3 * li + c])
                         vals.append(1.0 / len(cnodes))
                     gA.append(apos[j] + c)
-            na = 3 * len(loc_cls)
+                ldof = (3 * lidx[:, None] + np.arange(3)).reshape(-1)
+                for k, w in enumerate(rot[j]):
+                    rows.extend([len(gA)] * w.size)
+                    cols.extend(rpos[ldof])
+                    vals.extend(w)
+                    gA.append(apos[j] + 3 + k)
+            na = len(gA)
             Cr = sp.coo_matrix((vals, (rows, cols)),
                                shape=(na, ldofR.size)).tocsr()
             Krr = A[ldofR][:, ldofR]
