@@ -61,6 +61,10 @@ WORKLOADS = {
               "load steps; Newton states of the first load step",
               lambda: __import__("workloads").lv_config("lv_p2"), 3, 64, 1, None),
 }
+WORKLOADS["slab48_q1_ver"] = ("48x48x12 Q1 hex slab as slab48_q1 with primal VE plus the rotations "
+                              "of every edge (rigid-body primal constraints)",
+                              lambda: __import__("workloads").slab_config("slab48_q1", primal="VER"),
+                              2, None, None, 3)
 # reduced ventricles (same generator, 5 x 64 x 32 rings, 64 subdomains) for
 # profiler captures that must stay a few GB on the device
 WORKLOADS["lv_p1_small"] = ("left-ventricle shell, P1 tets, 5 x 64 x 32 rings, 64 subdomains",

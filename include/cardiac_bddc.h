@@ -203,7 +203,16 @@ CBDDC_API int fem_set_time_state(fem_problem* P, double dt, const double* d_prev
 /* ---------------------------------------------------------------- BDDC */
 
 enum { CBDDC_FP64 = 0, CBDDC_FP32 = 1 };      /* local operator precision */
-enum { CBDDC_PRIMAL_V = 1, CBDDC_PRIMAL_E = 2, CBDDC_PRIMAL_F = 4 };
+enum { CBDDC_PRIMAL_V = 1, CBDDC_PRIMAL_E = 2, CBDDC_PRIMAL_F = 4, CBDDC_PRIMAL_R = 8 };
+/* CBDDC_PRIMAL_R adds, to every edge (E) or face (F) class, constraints on
+   the infinitesimal rotations about the class centroid (the rigid motions,
+   near-null space of elasticity, taken into the primal space: Section 4):
+   the rotation fields e_k x (x - xbar), k = x, y, z, restricted to the class
+   nodes, orthonormalised along the principal axes of the class; an axis
+   whose principal moment is below 1e-8 of the largest (the axis of a
+   straight edge) gives no constraint.  So a planar face carries 6 primal
+   DoFs, a straight edge 5.  Two-level method only (levels = 2, not in
+   primal2): bddc_setup returns CBDDC_EINVAL otherwise. */
 
 typedef struct {
   int precision;     /* CBDDC_FP64: all local operators in FP64;

@@ -18,7 +18,7 @@ from . import _build
 
 __all__ = [
     "build", "load_library", "Problem", "BDDC", "SolveOptions", "CBDDCError",
-    "FP64", "FP32", "PRIMAL_V", "PRIMAL_E", "PRIMAL_F", "primal_mask",
+    "FP64", "FP32", "PRIMAL_V", "PRIMAL_E", "PRIMAL_F", "PRIMAL_R", "primal_mask",
     "EXPORTED_SYMBOLS",
 ]
 
@@ -26,7 +26,7 @@ OK, EINVAL, ECUDA, EPIVOT, EINVERTED, ENOCONV, ETIMEOUT, ENOMEM = range(8)
 HEX_Q1, HEX_Q2, TET_P1, TET_P2 = 1, 2, 3, 4
 FIBER_SLAB_HELIX, FIBER_NODAL = 1, 2
 FP64, FP32 = 0, 1
-PRIMAL_V, PRIMAL_E, PRIMAL_F = 1, 2, 4
+PRIMAL_V, PRIMAL_E, PRIMAL_F, PRIMAL_R = 1, 2, 4, 8
 MAX_RECORDS = 512
 
 EXPORTED_SYMBOLS = [
@@ -41,10 +41,11 @@ TIMER_OFF, TIMER_SWEEP_GEMM, TIMER_ELEMENT, TIMER_APPLY, TIMER_SPMV, TIMER_ORTH 
 
 
 def primal_mask(spec):
-    """'V', 'VE', 'VEF', 'EF', ... -> bit mask."""
+    """'V', 'VE', 'VEF', 'EF', 'VER', ... -> bit mask (R: rotations of the
+    edge and face classes)."""
     m = 0
     for ch in spec:
-        m |= {"V": PRIMAL_V, "E": PRIMAL_E, "F": PRIMAL_F}[ch]
+        m |= {"V": PRIMAL_V, "E": PRIMAL_E, "F": PRIMAL_F, "R": PRIMAL_R}[ch]
     return m
 
 

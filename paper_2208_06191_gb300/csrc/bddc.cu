@@ -29,6 +29,7 @@
 
 #include "bddc.h"
 #include "fem.h"
+#include "rigid.h"
 
 namespace cbddc {
 
@@ -174,12 +175,12 @@ __global__ void copy_e_kernel(const int* __restrict__ nI, const int* __restrict_
   Aloc[offA[s] + (int64_t)i * ldA[s] + cI + j] = Et[offE[s] + (int64_t)i * ldE[s] + j];
 }
 
-// S_rr += alpha C^T C with C the average constraints (alpha = largest |S_ii|
-// of the subdomain, and each class block scaled by its size).  Since C w = 0
-// for every admissible w, the constrained solution operator and the coarse
-// basis are unchanged, while S_rr becomes invertible for floating subdomains
-// whose primal space has no vertices.  Members of different constraints are
-// disjoint, so the updates do not overlap.  One CTA per subdomain.
+// S_rr += alpha sum_q c_q c_q^T / |c_q|^2 over the constraint rows c_q
+// (alpha = largest |S_ii| of the subdomain).  Since C w = 0 for every
+// admissible w, the constrained solution operator and the coarse basis are
+// unchanged, while S_rr becomes invertible for floating subdomains whose
+// primal space has no vertices.  One CTA per subdomain; constraints are
+// added one after the other.
 template <typename T>
 __global__ void __launch_bounds__(256)
 augment_kernel(const int* __restrict__ nr, const int* __restrict__ na,
@@ -204,15 +205,18 @@ augment_kernel(const int* __restrict__ nr, const int* __restrict__ na,
   for (int q = 0; q < na[s]; ++q) {
     const int64_t gq = offCon[s] + q;
     const int b = cptr[gq], cnt = cptr[gq + 1] - b;
-    const T add = (T)(alpha * cw[gq]);  // alpha / |class|
+    double nrm2 = 0.0;
+    for (int j = 0; j < cnt; ++j) nrm2 += cw[b + j] * cw[b + j];
+    const double scale = alpha / nrm2;  // alpha c c^T / |c|^2
     for (int t = threadIdx.x; t < cnt * cnt; t += blockDim.x) {
-      const int i = cidx[b + t / cnt], j = cidx[b + t % cnt];
-      S0[(int64_t)i * ld + j] += add;
+      const int a = b + t / cnt, e = b + t % cnt;
+      S0[(int64_t)cidx[a] * ld + cidx[e]] += (T)(scale * cw[a] * cw[e]);
     }
+    __syncthreads();  // the rotations of a class share members with its averages
   }
 }
 
-// Y[row][q] = w_q sum_{j in q} Sw[row][j], one warp per row (row < n_r).
+// Y[row][q] = sum_{j in q} w_j Sw[row][j], one warp per row (row < n_r).
 template <typename T>
 __global__ void cons_y_kernel(const int* __restrict__ nr, const int* __restrict__ na,
                               const int64_t* __restrict__ offCon, const int* __restrict__ cptr,
@@ -230,12 +234,12 @@ __global__ void cons_y_kernel(const int* __restrict__ nr, const int* __restrict_
   for (int q = lane; q < na[s]; q += 32) {
     const int64_t gq = offCon[s] + q;
     double acc = 0.0;
-    for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += (double)Srow[cidx[j]];
-    Y[offY[s] + (int64_t)row * ldY[s] + q] = (T)(acc * cw[gq]);
+    for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += (double)Srow[cidx[j]] * cw[j];
+    Y[offY[s] + (int64_t)row * ldY[s] + q] = (T)acc;
   }
 }
 
-// Zf[q][col] = w_q sum_{j in q} Sw[j][col] for all n_G columns.
+// Zf[q][col] = sum_{j in q} w_j Sw[j][col] for all n_G columns.
 template <typename T>
 __global__ void cons_z_kernel(const int* __restrict__ nG, const int* __restrict__ na,
                               const int64_t* __restrict__ offCon, const int* __restrict__ cptr,
@@ -251,12 +255,12 @@ __global__ void cons_z_kernel(const int* __restrict__ nG, const int* __restrict_
   for (int q = 0; q < na[s]; ++q) {
     const int64_t gq = offCon[s] + q;
     double acc = 0.0;
-    for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += (double)S0[(int64_t)cidx[j] * ld + col];
-    Zf[offZ[s] + (int64_t)q * ld + col] = (T)(acc * cw[gq]);
+    for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += (double)S0[(int64_t)cidx[j] * ld + col] * cw[j];
+    Zf[offZ[s] + (int64_t)q * ld + col] = (T)acc;
   }
 }
 
-// G[q][q2] = w_q sum_{j in q} Y[j][q2]
+// G[q][q2] = sum_{j in q} w_j Y[j][q2]
 template <typename T>
 __global__ void cons_g_kernel(const int* __restrict__ na, const int64_t* __restrict__ offCon,
                               const int* __restrict__ cptr, const int* __restrict__ cidx,
@@ -270,8 +274,9 @@ __global__ void cons_g_kernel(const int* __restrict__ na, const int64_t* __restr
   const int q = t / n, q2 = t % n;
   const int64_t gq = offCon[s] + q;
   double acc = 0.0;
-  for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += (double)Y[offY[s] + (int64_t)cidx[j] * ldY[s] + q2];
-  G[offG[s] + (int64_t)q * ldG[s] + q2] = (T)(acc * cw[gq]);
+  for (int j = cptr[gq]; j < cptr[gq + 1]; ++j)
+    acc += (double)Y[offY[s] + (int64_t)cidx[j] * ldY[s] + q2] * cw[j];
+  G[offG[s] + (int64_t)q * ldG[s] + q2] = (T)acc;
 }
 
 // Phi[0:nr, 0:nv] = -Sw[0:nr, nr:nG] ; Phi[nr:nG, :] = [I 0]
@@ -663,7 +668,12 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   const bool useV = opt->primal & CBDDC_PRIMAL_V;
   const bool useE = opt->primal & CBDDC_PRIMAL_E;
   const bool useF = opt->primal & CBDDC_PRIMAL_F;
+  const bool useR = opt->primal & CBDDC_PRIMAL_R;
   const int nn = P->n_nodes;
+  CB_CHECK(!useR || (C->levels == 2 && P->coords_h.size() == (size_t)nn * 3), CBDDC_EINVAL,
+           "rotational primal constraints need the two-level method on the fine level");
+  CB_CHECK(C->levels == 2 || !(C->primal2 & CBDDC_PRIMAL_R), CBDDC_EINVAL,
+           "rotational primal constraints are not available on level 2");
   std::vector<int> vert_pos(nn, -1);
   int n_vert = 0;
   if (useV)
@@ -674,7 +684,21 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   std::vector<int> node_cls(nn, -1);
   for (size_t j = 0; j < avg.size(); ++j)
     for (int v : *avg[j]) node_cls[v] = (int)j;
-  C->n_pi = 3 * n_vert + 3 * (int)avg.size();
+  // per class: 3 averages, then its rotations (rows of 3 * |class| weights
+  // at rot_w[rot_off[j]]); global primal numbering: vertex DoFs, then the
+  // constraints of each class at apos[j]
+  std::vector<int> nrot(avg.size(), 0);
+  std::vector<int64_t> rot_off(avg.size(), 0);
+  std::vector<double> rot_w;
+  std::vector<int> apos(avg.size(), 0);
+  int n_pi = 3 * n_vert;
+  for (size_t j = 0; j < avg.size(); ++j) {
+    rot_off[j] = (int64_t)rot_w.size();
+    if (useR) nrot[j] = class_rotations(P->coords_h, *avg[j], rot_w);
+    apos[j] = n_pi;
+    n_pi += 3 + nrot[j];
+  }
+  C->n_pi = n_pi;
 
   C->nI.assign(nsub, 0); C->nG = C->nr = C->nv = C->na = C->nc = C->ns = C->nI;
   std::vector<int> perm_h;
@@ -724,27 +748,41 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
       if (node_cls[sub.nodes[l]] >= 0) cls.push_back(node_cls[sub.nodes[l]]);
     std::sort(cls.begin(), cls.end());
     cls.erase(std::unique(cls.begin(), cls.end()), cls.end());
+    const size_t con0 = cptr.size();
     for (int j : cls) {
       const std::vector<int>& cn = *avg[j];
-      for (int c = 0; c < 3; ++c) {
-        for (int v : cn) {
-          auto it = std::lower_bound(sub.nodes.begin(), sub.nodes.end(), v);
-          CB_CHECK(it != sub.nodes.end() && *it == v, CBDDC_EINVAL, "class node not in subdomain");
-          const int l = (int)(it - sub.nodes.begin());
-          CB_CHECK(rpos[l] >= 0, CBDDC_EINVAL, "class node is not a dual interface node");
-          cidx.push_back(3 * rpos[l] + c);
+      std::vector<int> rl(cn.size());  // r-block position of each class node
+      for (size_t a = 0; a < cn.size(); ++a) {
+        auto it = std::lower_bound(sub.nodes.begin(), sub.nodes.end(), cn[a]);
+        CB_CHECK(it != sub.nodes.end() && *it == cn[a], CBDDC_EINVAL, "class node not in subdomain");
+        const int l = (int)(it - sub.nodes.begin());
+        CB_CHECK(rpos[l] >= 0, CBDDC_EINVAL, "class node is not a dual interface node");
+        rl[a] = rpos[l];
+      }
+      for (int c = 0; c < 3; ++c) {  // averages: weight 1 / |class| per member
+        for (int r : rl) {
+          cidx.push_back(3 * r + c);
+          cw.push_back(1.0 / (double)cn.size());
         }
         cptr.push_back((int)cidx.size());
-        cw.push_back(1.0 / (double)cn.size());
+      }
+      for (int k = 0; k < nrot[j]; ++k) {  // rotations: all 3 components
+        const double* wk = rot_w.data() + rot_off[j] + (int64_t)k * 3 * (int64_t)cn.size();
+        for (size_t a = 0; a < cn.size(); ++a)
+          for (int c = 0; c < 3; ++c) {
+            cidx.push_back(3 * rl[a] + c);
+            cw.push_back(wk[3 * a + c]);
+          }
+        cptr.push_back((int)cidx.size());
       }
     }
-    C->na[s] = 3 * (int)cls.size();
+    C->na[s] = (int)(cptr.size() - con0);
     C->nc[s] = C->nv[s] + C->na[s];
     CB_CHECK(C->nc[s] <= NC_MAX, CBDDC_EINVAL, "more than 512 primal constraints in one subdomain");
     for (int l : Gv)
       for (int c = 0; c < 3; ++c) gprim.push_back(3 * vert_pos[sub.nodes[l]] + c);
     for (int j : cls)
-      for (int c = 0; c < 3; ++c) gprim.push_back(3 * n_vert + 3 * j + c);
+      for (int c = 0; c < 3 + nrot[j]; ++c) gprim.push_back(apos[j] + c);
     C->offI[s + 1] = C->offI[s] + C->nI[s];
     C->offGam[s + 1] = C->offGam[s] + C->nG[s];
     C->offC[s + 1] = C->offC[s] + C->nc[s];

@@ -31,7 +31,7 @@ struct bddc_ctx {
   cbddc::DVec<int> gdofI, gdofG, gam_if, if_dof, if_ptr, if_src;
   cbddc::DVec<double> Dg;
   cbddc::DVec<int> cons_ptr, cons_idx;   // constraint -> members (local r index)
-  cbddc::DVec<double> cons_w;            // 1 / class size
+  cbddc::DVec<double> cons_w;            // weight of each member
   cbddc::DVec<int> gprim, cg_ptr, cg_src;  // coarse rhs gather
   cbddc::DVec<int> ce_key, ce_ptr, ce_src; // coarse matrix entries
   int64_t n_ce = 0;

@@ -127,6 +127,7 @@ struct fem_problem {
   std::vector<int> share_count;             // per node (free nodes only)
   std::vector<int> vertices;                // vertex nodes
   std::vector<std::vector<int>> edges, faces;  // classes (node lists)
+  std::vector<double> coords_h;             // n_nodes*3 (fine level only)
   // device data
   cbddc::DVec<double> coords;               // n_nodes*3
   cbddc::DVec<double> fib_nodal;            // n_nodes*6 (f, n) for nodal fibres

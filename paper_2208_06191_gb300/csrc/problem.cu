@@ -464,6 +464,7 @@ void build_problem(const fem_problem_desc* d, fem_problem* P) {
   // uploads
   std::vector<double> coords(d->coords, d->coords + (size_t)nn * 3);
   P->coords.upload(coords);
+  P->coords_h = std::move(coords);
   if (P->fiber_kind == CBDDC_FIBER_NODAL) {
     std::vector<double> fn(d->fiber_nodal, d->fiber_nodal + (size_t)nn * 6);
     for (int v = 0; v < nn; ++v) {

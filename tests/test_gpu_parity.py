@@ -110,7 +110,7 @@ def _bddc_pair(prob, primal, precision, lam=0.8, seed=0):
     return fe, K, ref, P, pc
 
 
-@pytest.mark.parametrize("primal", ["V", "VE", "VEF", "EF"])
+@pytest.mark.parametrize("primal", ["V", "VE", "VEF", "EF", "VER", "EFR"])
 @pytest.mark.parametrize("precision,tol", [(pkg.FP64, 1e-9), (pkg.FP32, 1e-3)])
 def test_bddc_apply_parity(primal, precision, tol):
     prob = slab_problem(order=1, **RAGGED)
@@ -146,7 +146,7 @@ def test_single_subdomain_is_exact_solve():
     assert np.linalg.norm(K @ _host(x) - b) <= 1e-10 * np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("primal", ["V", "VE"])
+@pytest.mark.parametrize("primal", ["V", "VE", "EFR"])
 def test_gmres_parity(primal):
     prob = slab_problem(order=1, **RAGGED)
     fe, K, ref, P, pc = _bddc_pair(prob, primal, pkg.FP64)
@@ -280,6 +280,19 @@ def test_multilevel_apply_parity(precision, tol):
     pc.apply(_dev(r), z)
     z_ref = ref.apply(r)
     assert np.linalg.norm(_host(z) - z_ref) <= tol * np.linalg.norm(z_ref)
+
+
+def test_rotations_refused_for_multilevel():
+    from workloads import box_groups
+    prob = slab_problem(4, 4, 2, order=1, parts=(2, 2, 1), pressure=1e3, gamma=3e4)
+    P = pkg.Problem(prob)
+    P.assemble_tangent(_dev(np.zeros(P.n_free)), 0.5)
+    part2, n2 = box_groups((2, 2, 1), (2, 1, 1))
+    for primal, primal2 in (("VER", "VEF"), ("VE", "VEFR")):
+        with pytest.raises(pkg.CBDDCError) as ei:
+            pkg.BDDC(P, precision=pkg.FP64, primal=primal, levels=3, part2=part2, n_parts2=n2,
+                     primal2=primal2).setup()
+        assert ei.value.code == pkg.EINVAL
 
 
 def test_multilevel_with_one_group_equals_two_level_on_gpu():

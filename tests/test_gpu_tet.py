@@ -85,7 +85,7 @@ def _tet_pair(order, primal, precision, **kw):
 
 
 @pytest.mark.parametrize("order", [1, 2])
-@pytest.mark.parametrize("primal", ["V", "VEF"])
+@pytest.mark.parametrize("primal", ["V", "VEF", "VEFR"])
 @pytest.mark.parametrize("precision,tol", [(pkg.FP64, 1e-9), (pkg.FP32, 1e-3)])
 def test_tet_bddc_apply_parity(order, primal, precision, tol):
     fe, K, ref, P, pc = _tet_pair(order, primal, precision)
