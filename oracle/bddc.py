@@ -12,7 +12,11 @@ Setup, per subdomain i (the unassembled local matrix A^(i), A = sum A^(i)):
   arithmetic averages per displacement component (Sections 3.2 and 6.2);
   with "R", also the rigid-body rotations of every averaged class (the
   near-null space taken into the primal space, Section 4);
-* counting scaling delta_i^dagger = 1 / #subdomains sharing the DoF;
+* counting scaling delta_i^dagger = 1 / #subdomains sharing the DoF, or
+  deluxe scaling (Section 3.2 names it as the more robust choice): on every
+  edge and face class K, D_K^(i) = (sum_j S_K^(j))^-1 S_K^(i) with S_K^(j)
+  the class block of subdomain j's Schur complement onto its interface;
+  vertex nodes keep the counting weights;
 * coarse basis Phi_i: the minimum-energy extension of each primal
   constraint (the local saddle-point problem with unit constraint values),
   and the coarse matrix S_PiPi = sum_i R_Pi^T Phi_i^T A^(i) Phi_i R_Pi.
@@ -20,11 +24,11 @@ Setup, per subdomain i (the unassembled local matrix A^(i), A = sum A^(i)):
 Apply z = M^-1 r:
   1. u0 = A_II^-1 r_I                           (block diagonal)
   2. g  = r_Gamma - A_GammaI u0                 (assembled on Gamma)
-  3. g_i = D_i R_i g
+  3. g_i = D_i R_i g      (deluxe: D_K^(i)^T on each class block)
   4. w_i: local Neumann solve with all primal constraints set to zero
      (vertices eliminated, averages through Lagrange multipliers)
   5. u_c = S_PiPi^-1 sum_i R_Pi^T Phi_i^T g_i;   w_i += Phi_i R_Pi u_c
-  6. z_Gamma = sum_i R_i^T D_i w_i
+  6. z_Gamma = sum_i R_i^T D_i w_i   (deluxe: D_K^(i) on each class block)
   7. z_I = A_II^-1 (r_I - A_IGamma z_Gamma)
 Steps 2-6 are M_BDDC^-1 = R_D^T S~^-1 R_D applied to the Schur complement
 system; steps 1 and 7 are the exact outer block factors.
@@ -220,9 +224,15 @@ class BDDC:
     Section 3.2); a nested ``level2`` entry adds a further level.
     ``primal`` holds the letters V, E, F and R (rotations of the averaged
     classes, fine level of a two-level method only: the rotations need node
-    coordinates, and a coarse node of the multilevel method carries 3 DoFs)."""
+    coordinates, and a coarse node of the multilevel method carries 3 DoFs).
+    ``scaling``: "counting" or "deluxe" on this level (a level-2 method
+    takes its own from ``level2["scaling"]``, counting by default)."""
 
-    def __init__(self, fe, Ke=None, Kf=None, primal="V", classification=None, level2=None):
+    def __init__(self, fe, Ke=None, Kf=None, primal="V", classification=None, level2=None,
+                 scaling="counting"):
+        if scaling not in ("counting", "deluxe"):
+            raise ValueError("scaling is 'counting' or 'deluxe'")
+        self.scaling = scaling
         level = fe if isinstance(fe, CoarseLevel) else FineLevel(fe, Ke, Kf)
         self.level = level
         cl = classification or Classification(level)
@@ -333,13 +343,16 @@ class BDDC:
                        AGI=A[ldofG][:, ldofI], AIG=A[ldofI][:, ldofG])
             self.subs.append(sub)
         self.n_free = level.n_free
+        if scaling == "deluxe":
+            self._setup_deluxe(cl)
         self.coarse = None
         if level2 is not None and self.n_pi > 0:
             # coarse nodes: 3 consecutive primal DoFs each (node-major)
             clevel = CoarseLevel(self.n_pi // 3, [sub["gP"][::3] // 3 for sub in self.subs],
                                  Sc_list, level2["part"], level2["n_parts"])
             self.coarse = BDDC(clevel, primal=level2.get("primal", "VEF"),
-                               level2=level2.get("level2"))
+                               level2=level2.get("level2"),
+                               scaling=level2.get("scaling", "counting"))
             self.S_pipi = None
         else:
             S = np.zeros((self.n_pi, self.n_pi))
@@ -347,6 +360,39 @@ class BDDC:
                 if sub["gP"].size:
                     S[np.ix_(sub["gP"], sub["gP"])] += sub["Sc"]
             self.S_pipi = S
+
+    def _setup_deluxe(self, cl):
+        """Deluxe scaling: for every edge and face class K and every
+        subdomain i sharing it, the block S_K^(i) of the local Schur
+        complement S_i = A_GG - A_GI A_II^-1 A_IG on the class DoFs, and
+        D_K^(i) = (sum_j S_K^(j))^-1 S_K^(i).  Each subdomain gets
+        ``deluxe``: a list of (positions of the class DoFs in its interface
+        vector, D_K^(i)); the counting weight of those DoFs becomes 1."""
+        blocks = {}
+        for i, sub in enumerate(self.subs):
+            A = sub["A"]
+            AGG = A[sub["ldofG"]][:, sub["ldofG"]].toarray()
+            if sub["luII"] is not None:
+                S = AGG - sub["AGI"] @ sub["luII"].solve(sub["AIG"].toarray())
+            else:
+                S = AGG
+            sub["S"] = S
+            sub["deluxe"] = []
+            nodes = sub["nodes"]
+            for k, cls in enumerate(cl.edges + cl.faces):
+                li = np.searchsorted(nodes, cls)
+                if li[0] >= nodes.size or nodes[li[0]] != cls[0]:
+                    continue
+                ldof = (3 * li[:, None] + np.arange(3)).reshape(-1)
+                pos = np.searchsorted(sub["ldofG"], ldof)
+                blocks.setdefault(k, []).append((i, pos, S[np.ix_(pos, pos)]))
+        for k, lst in blocks.items():
+            Shat = sum(Sk for _, _, Sk in lst)
+            for i, pos, Sk in lst:
+                D = np.linalg.solve(Shat, Sk)
+                sub = self.subs[i]
+                sub["deluxe"].append((pos, D))
+                sub["Dg"][pos] = 1.0
 
     def _local_solve(self, sub, f_loc):
         """Constrained Neumann solve with zero primal values: w_v = 0,
@@ -384,7 +430,10 @@ class BDDC:
         for sub in self.subs:
             gd = sub["gdof"]
             f = np.zeros(gd.size)
-            f[sub["ldofG"]] = sub["Dg"] * g[gd[sub["ldofG"]]]
+            fG = sub["Dg"] * g[gd[sub["ldofG"]]]
+            for pos, D in sub.get("deluxe", ()):
+                fG[pos] = D.T @ fG[pos]
+            f[sub["ldofG"]] = fG
             w = self._local_solve(sub, f)
             if sub["gP"].size:
                 np.add.at(c, sub["gP"], sub["Phi"].T @ f)
@@ -395,7 +444,10 @@ class BDDC:
             gd = sub["gdof"]
             if sub["gP"].size:
                 w = w + sub["Phi"] @ uc[sub["gP"]]
-            np.add.at(zG, gd[sub["ldofG"]], sub["Dg"] * w[sub["ldofG"]])
+            yG = sub["Dg"] * w[sub["ldofG"]]
+            for pos, D in sub.get("deluxe", ()):
+                yG[pos] = D @ yG[pos]
+            np.add.at(zG, gd[sub["ldofG"]], yG)
         z[:] = zG
         for sub, u in zip(self.subs, u0):
             gd = sub["gdof"]
