@@ -65,6 +65,20 @@ WORKLOADS["slab48_q1_ver"] = ("48x48x12 Q1 hex slab as slab48_q1 with primal VE 
                               "of every edge (rigid-body primal constraints)",
                               lambda: __import__("workloads").slab_config("slab48_q1", primal="VER"),
                               2, None, None, 3)
+
+
+def _with_scaling(build, scaling):
+    def f():
+        prob = build()
+        prob["scaling"] = scaling
+        return prob
+    return f
+
+
+WORKLOADS["slab48_q1_dlx"] = ("48x48x12 Q1 hex slab as slab48_q1 (primal VE) with deluxe scaling",
+                              _with_scaling(WORKLOADS["slab48_q1"][1], "deluxe"), 2, None, None, 3)
+WORKLOADS["lv_p1_dlx"] = (WORKLOADS["lv_p1"][0] + "; deluxe scaling",
+                          _with_scaling(WORKLOADS["lv_p1"][1], "deluxe"), 2, None, 1, None)
 # reduced ventricles (same generator, 5 x 64 x 32 rings, 64 subdomains) for
 # profiler captures that must stay a few GB on the device
 WORKLOADS["lv_p1_small"] = ("left-ventricle shell, P1 tets, 5 x 64 x 32 rings, 64 subdomains",
@@ -76,6 +90,8 @@ WORKLOADS["lv_p2_small"] = ("left-ventricle shell, P2 tets, 5 x 64 x 32 rings, 1
                             lambda: __import__("workloads").lv_problem(
                                 nt=5, ntheta=64, nu=32, order=2, n_parts=128, n_parts2=8,
                                 n_layers=2, load_steps=8, gamma=0.25 * 6.0e4), 3, 8, 1, 1)
+WORKLOADS["lv_p1_small_dlx"] = (WORKLOADS["lv_p1_small"][0] + "; deluxe scaling",
+                                _with_scaling(WORKLOADS["lv_p1_small"][1], "deluxe"), 2, None, 1, 1)
 WORKLOAD_DESC = WORKLOADS[WORKLOAD][0]
 
 
@@ -271,10 +287,11 @@ def run_ours(args, world, rank, local):
     ml = {}
     if levels == 3:
         ml = dict(levels=3, part2=prob["part2"], n_parts2=prob["n_parts2"], primal2="VEF")
+    scaling = prob.get("scaling", "counting")
     opts32 = pkg.SolveOptions(precision=pkg.FP32, primal=prob["primal"], max_gmres=args.max_gmres,
-                              precision2=pkg.FP32, **ml)
+                              precision2=pkg.FP32, scaling=scaling, **ml)
     opts64 = pkg.SolveOptions(precision=pkg.FP64, primal=prob["primal"], max_gmres=args.max_gmres,
-                              precision2=pkg.FP64, **ml)
+                              precision2=pkg.FP64, scaling=scaling, **ml)
 
     # untimed: Newton states of a full FP32 solve (or of its first load steps)
     states = []
@@ -461,7 +478,8 @@ def run_kernels(args):
     if levels == 3:
         ml = dict(levels=3, part2=prob["part2"], n_parts2=prob["n_parts2"], primal2="VEF",
                   precision2=pkg.FP32)
-    pc = pkg.BDDC(P, precision=pkg.FP32, primal=prob["primal"], **ml).setup()
+    pc = pkg.BDDC(P, precision=pkg.FP32, primal=prob["primal"], scaling=prob.get("scaling", "counting"),
+                  **ml).setup()
     z = torch.empty_like(d)
     y = torch.empty_like(d)
     for _ in range(3):

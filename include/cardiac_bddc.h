@@ -203,6 +203,15 @@ CBDDC_API int fem_set_time_state(fem_problem* P, double dt, const double* d_prev
 /* ---------------------------------------------------------------- BDDC */
 
 enum { CBDDC_FP64 = 0, CBDDC_FP32 = 1 };      /* local operator precision */
+/* Interface scaling D_i of the restriction and extension (Section 3.2).
+   COUNTING: delta_i^dagger = 1 / #subdomains sharing the DoF.  DELUXE: on
+   every edge and face class K (vertex nodes keep counting),
+   D_K^(i) = (sum_j S_K^(j))^-1 S_K^(i), with S_K^(j) the class block of
+   subdomain j's Schur complement onto its interface; the extension applies
+   D_K^(i), the restriction its transpose.  Deluxe is set up per Newton
+   step from the local Schur complements (dense, in the local operator
+   precision) and applies to the first level of a multilevel method. */
+enum { CBDDC_SCALING_COUNTING = 0, CBDDC_SCALING_DELUXE = 1 };
 enum { CBDDC_PRIMAL_V = 1, CBDDC_PRIMAL_E = 2, CBDDC_PRIMAL_F = 4, CBDDC_PRIMAL_R = 8 };
 /* CBDDC_PRIMAL_R adds, to every edge (E) or face (F) class, constraints on
    the infinitesimal rotations about the class centroid (the rigid motions,
@@ -236,6 +245,9 @@ typedef struct {
   const int32_t* part2;
   int primal2;
   int precision2;
+  int scaling;       /* CBDDC_SCALING_COUNTING (0) or CBDDC_SCALING_DELUXE;
+                        deluxe allows at most 65535 edge and face classes,
+                        of at most 2048 nodes each (CBDDC_EINVAL otherwise) */
 } bddc_options;
 
 typedef struct bddc_ctx bddc_ctx;
@@ -329,6 +341,7 @@ typedef struct {
   const int32_t* part2;
   int primal2;
   int precision2;
+  int scaling;         /* as in bddc_options                                 */
 } solve_options;
 
 #define CBDDC_MAX_RECORDS 512

@@ -279,6 +279,62 @@ __global__ void cons_g_kernel(const int* __restrict__ na, const int64_t* __restr
   G[offG[s] + (int64_t)q * ldG[s] + q2] = (T)acc;
 }
 
+// ------------------------------------------------- deluxe scaling (setup)
+// S_b = the class block of block b's subdomain Schur complement S = A_GG -
+// A_GI A_II^-1 A_IG (the GG block of Aloc), rows and columns at the class
+// DoFs' interface positions.  One CTA per block.
+template <typename T>
+__global__ void __launch_bounds__(256)
+deluxe_gather_kernel(const int* __restrict__ bn, const int* __restrict__ bsub, const int* __restrict__ bld,
+                     const int64_t* __restrict__ poff, const int* __restrict__ pos,
+                     const int64_t* __restrict__ boff, const int* __restrict__ nI,
+                     const int64_t* __restrict__ offA, const int* __restrict__ ldA,
+                     const T* __restrict__ Aloc, T* __restrict__ Sb) {
+  const int b = blockIdx.x;
+  const int n = bn[b], s = bsub[b], ld = bld[b];
+  const int ni = nI[s], lda = ldA[s];
+  const T* S = Aloc + offA[s] + (int64_t)ni * lda + round_up_dev(ni, 4);
+  const int* p = pos + poff[b];
+  T* out = Sb + boff[b];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, j = t % n;
+    out[(int64_t)i * ld + j] = S[(int64_t)p[i] * lda + p[j]];
+  }
+}
+
+// Shat_K = sum of the class's blocks S_b, in block order.  One CTA per class.
+template <typename T>
+__global__ void __launch_bounds__(256)
+deluxe_sum_kernel(const int* __restrict__ cptr, const int* __restrict__ cblk, const int* __restrict__ bn,
+                  const int* __restrict__ bld, const int64_t* __restrict__ boff,
+                  const int64_t* __restrict__ coff, const T* __restrict__ Sb, T* __restrict__ Sh) {
+  const int k = blockIdx.x;
+  const int b0 = cptr[k], b1 = cptr[k + 1];
+  const int n = bn[cblk[b0]], ld = bld[cblk[b0]];
+  T* out = Sh + coff[k];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, j = t % n;
+    T v = T(0);
+    for (int q = b0; q < b1; ++q) v += Sb[boff[cblk[q]] + (int64_t)i * ld + j];
+    out[(int64_t)i * ld + j] = v;
+  }
+}
+
+// E_b = D_b^T.  One CTA per block.
+template <typename T>
+__global__ void __launch_bounds__(256)
+deluxe_transpose_kernel(const int* __restrict__ bn, const int* __restrict__ bld,
+                        const int64_t* __restrict__ boff, const T* __restrict__ D, T* __restrict__ E) {
+  const int b = blockIdx.x;
+  const int n = bn[b], ld = bld[b];
+  const T* d = D + boff[b];
+  T* e = E + boff[b];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, j = t % n;
+    e[(int64_t)j * ld + i] = d[(int64_t)i * ld + j];
+  }
+}
+
 // Phi[0:nr, 0:nv] = -Sw[0:nr, nr:nG] ; Phi[nr:nG, :] = [I 0]
 template <typename T>
 __global__ void phi_vertex_kernel(const int* __restrict__ nG, const int* __restrict__ nr,
@@ -491,6 +547,45 @@ __global__ void dense_gemv_kernel(const double* __restrict__ A, int n, const dou
   if (lane == 0) y[row] = acc;
 }
 
+// Deluxe blocks of the apply: out[og + pos_j] = sum_i M_b[i][j] x_i for the
+// class DoFs of block b (og: the subdomain's first interface position).
+// Restriction: x_i = gI[gam_if[og + pos_i]] (assembled interface values),
+// M_b = D_b, so g_i gets D_b^T g on the class.  Extension: x_i = yG[og +
+// pos_i], M_b = E_b = D_b^T, so the class part of y_i becomes D_b y_i.
+// Inputs and outputs are different vectors, so the 128-column slices of a
+// block (blockIdx.y) run independently; one output per thread, columns of
+// M_b read coalesced.
+constexpr int DLX_COLS = 128;
+template <typename T, bool GATHER>
+__global__ void __launch_bounds__(DLX_COLS)
+deluxe_apply_kernel(const int* __restrict__ bn, const int* __restrict__ bsub, const int* __restrict__ bld,
+                    const int64_t* __restrict__ poff, const int* __restrict__ pos,
+                    const int64_t* __restrict__ boff, const int64_t* __restrict__ offGam,
+                    const int* __restrict__ gam_if, const T* __restrict__ M,
+                    const double* __restrict__ in, double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* xs = reinterpret_cast<T*>(smraw);
+  const int b = blockIdx.x;
+  const int n = bn[b];
+  const int j0 = blockIdx.y * DLX_COLS;
+  if (j0 >= n) return;
+  const int64_t og = offGam[bsub[b]];
+  const int* p = pos + poff[b];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t q = og + p[i];
+    xs[i] = (T)(GATHER ? in[gam_if[q]] : in[q]);
+  }
+  __syncthreads();
+  const int j = j0 + threadIdx.x;
+  if (j >= n) return;
+  const T* Mb = M + boff[b] + j;
+  const int ld = bld[b];
+  T acc = T(0);
+#pragma unroll 8
+  for (int i = 0; i < n; ++i) acc = fma(Mb[(int64_t)i * ld], xs[i], acc);
+  out[og + p[j]] = (double)acc;
+}
+
 // y_i = D_i (w_i + Phi_i R_Pi u_c); 8 lanes per interface row.
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -674,6 +769,26 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
            "rotational primal constraints need the two-level method on the fine level");
   CB_CHECK(C->levels == 2 || !(C->primal2 & CBDDC_PRIMAL_R), CBDDC_EINVAL,
            "rotational primal constraints are not available on level 2");
+  CB_CHECK(opt->scaling == CBDDC_SCALING_COUNTING || opt->scaling == CBDDC_SCALING_DELUXE, CBDDC_EINVAL,
+           "bad scaling");
+  C->scaling = opt->scaling;
+  const bool deluxe = opt->scaling == CBDDC_SCALING_DELUXE;
+  // deluxe classes: every edge and face (vertex nodes keep counting)
+  std::vector<const std::vector<int>*> dcls;
+  std::vector<int> node_dcls(nn, -1);
+  if (deluxe) {
+    for (auto& e : P->edges) dcls.push_back(&e);
+    for (auto& f : P->faces) dcls.push_back(&f);
+    CB_CHECK(dcls.size() <= 65535, CBDDC_EINVAL, "deluxe scaling allows at most 65535 interface classes");
+    for (size_t k = 0; k < dcls.size(); ++k) {
+      CB_CHECK(!dcls[k]->empty() && dcls[k]->size() <= 2048, CBDDC_EINVAL,
+               "deluxe scaling allows classes of 1 to 2048 nodes");
+      for (int v : *dcls[k]) node_dcls[v] = (int)k;
+    }
+  }
+  // deluxe blocks (class, subdomain) and the class DoFs' interface positions
+  std::vector<int> dlx_cls, dlx_sub_h;
+  std::vector<std::vector<int>> dlx_pos_h;
   std::vector<int> vert_pos(nn, -1);
   int n_vert = 0;
   if (useV)
@@ -740,8 +855,28 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
       for (int l : *lst)
         for (int c = 0; c < 3; ++c) {
           gdofG.push_back(3 * n2f[sub.nodes[l]] + c);
-          Dg.push_back(1.0 / P->share_count[sub.nodes[l]]);
+          Dg.push_back(node_dcls[sub.nodes[l]] >= 0 ? 1.0 : 1.0 / P->share_count[sub.nodes[l]]);
         }
+    if (deluxe) {
+      std::vector<int> dk;
+      for (int l : Gr)
+        if (node_dcls[sub.nodes[l]] >= 0) dk.push_back(node_dcls[sub.nodes[l]]);
+      std::sort(dk.begin(), dk.end());
+      dk.erase(std::unique(dk.begin(), dk.end()), dk.end());
+      for (int k : dk) {
+        std::vector<int> ps;
+        for (int v : *dcls[k]) {
+          auto it = std::lower_bound(sub.nodes.begin(), sub.nodes.end(), v);
+          CB_CHECK(it != sub.nodes.end() && *it == v, CBDDC_EINVAL, "class node not in subdomain");
+          const int l = (int)(it - sub.nodes.begin());
+          CB_CHECK(rpos[l] >= 0, CBDDC_EINVAL, "class node is not a dual interface node");
+          for (int c = 0; c < 3; ++c) ps.push_back(3 * rpos[l] + c);
+        }
+        dlx_cls.push_back(k);
+        dlx_sub_h.push_back(s);
+        dlx_pos_h.push_back(std::move(ps));
+      }
+    }
     // average constraints of classes touching this subdomain
     std::vector<int> cls;
     for (int l : Gr)
@@ -917,6 +1052,74 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   sweep_gemms(sw1, C->steps1, C->gl_sw1);
   sweep_gemms(sw2, C->steps2, C->gl_sw2);
   sweep_gemms(swg, C->stepsg, C->gl_swg);
+  double dlx_flops = 0.0;   // deluxe setup: class inverses and D_b products
+  int64_t dlx_bytes = 0;    // deluxe blocks read per apply (D_b and E_b)
+  if (deluxe && !dlx_cls.empty()) {
+    // blocks in (class, subdomain) order; S_b, D_b, E_b at the same offsets
+    const int nb = (int)dlx_cls.size(), nk = (int)dcls.size();
+    std::vector<int> order(nb);
+    for (int b = 0; b < nb; ++b) order[b] = b;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+      return dlx_cls[a] != dlx_cls[b] ? dlx_cls[a] < dlx_cls[b] : dlx_sub_h[a] < dlx_sub_h[b];
+    });
+    std::vector<int> bn(nb), bsub(nb), bld(nb), bpos, cptr(nk + 1, 0), cblk(nb);
+    std::vector<int64_t> bpoff(nb), boff(nb + 1, 0);
+    for (int q = 0; q < nb; ++q) {
+      const int b = order[q];
+      bn[q] = (int)dlx_pos_h[b].size();
+      bsub[q] = dlx_sub_h[b];
+      bld[q] = (int)round_up(bn[q], 8);
+      bpoff[q] = (int64_t)bpos.size();
+      bpos.insert(bpos.end(), dlx_pos_h[b].begin(), dlx_pos_h[b].end());
+      boff[q + 1] = boff[q] + round_up((int64_t)bn[q] * bld[q], kAlign);
+      cptr[dlx_cls[b] + 1]++;
+      cblk[q] = q;
+      C->maxDn = std::max(C->maxDn, bn[q]);
+    }
+    for (int k = 0; k < nk; ++k) cptr[k + 1] += cptr[k];
+    CB_CHECK(cptr[nk] == nb, CBDDC_EINVAL, "deluxe block lists are inconsistent");
+    // class matrices Shat_K (inverted in place by a sweep) and sweep panels
+    std::vector<int64_t> coff(nk + 1, 0);
+    std::vector<SweepDesc> swd(nk);
+    int64_t xo = 0, yo = 0;
+    for (int k = 0; k < nk; ++k) {
+      CB_CHECK(cptr[k + 1] > cptr[k], CBDDC_EINVAL, "interface class without subdomains");
+      const int q0 = cptr[k];
+      const int n = bn[q0], ld = bld[q0];
+      for (int q = q0; q < cptr[k + 1]; ++q) {
+        CB_CHECK(bn[q] == n, CBDDC_EINVAL, "deluxe blocks of one class differ in size");
+        dlx_flops += 2.0 * n * (double)n * n;
+        dlx_bytes += 2 * (int64_t)n * n * (int64_t)es;
+      }
+      dlx_flops += 2.0 * n * (double)n * n;
+      coff[k + 1] = coff[k] + round_up((int64_t)n * ld, kAlign);
+      swd[k] = SweepDesc{n, n, ld, n, coff[k], xo, yo, (int64_t)k * NB * NB};
+      xo += round_up((int64_t)n * NB, kAlign);
+      yo += round_up((int64_t)NB * ld, kAlign);
+      C->stepsd = std::max(C->stepsd, (int)cdiv(n, NB));
+    }
+    C->n_dlx = nb;
+    C->n_dcls = nk;
+    C->dlx_n.upload(bn); C->dlx_sub.upload(bsub); C->dlx_ld.upload(bld); C->dlx_pos.upload(bpos);
+    C->dlx_poff.upload(bpoff); C->dlx_off.upload(boff); C->dcls_ptr.upload(cptr); C->dcls_blk.upload(cblk);
+    C->dcls_off.upload(coff);
+    C->swd.upload(swd);
+    sweep_gemms(swd, C->stepsd, C->gl_swd);
+    std::vector<GemmProb> gd(nb);
+    for (int k = 0; k < nk; ++k)
+      for (int q = cptr[k]; q < cptr[k + 1]; ++q)
+        gd[q] = GemmProb{bn[q], bn[q], bn[q], bld[q], bld[q], bld[q], coff[k], boff[q], boff[q]};
+    C->gl_dlx.set(gd, es);
+    auto sz = [&](int64_t n) { return (size_t)(std::max<int64_t>(n, 1) + kAlign) * es; };
+    C->Dsb.alloc(sz(boff[nb]));
+    C->Ddb.alloc(sz(boff[nb]));
+    C->Deb.alloc(sz(boff[nb]));
+    C->Dsh.alloc(sz(coff[nk]));
+    C->DX.alloc(sz(xo));
+    C->DY.alloc(sz(yo));
+    C->DP.alloc(sz((int64_t)nk * NB * NB));
+    C->yD.alloc(std::max<int64_t>(C->totG, 1));
+  }
   std::vector<GemmProb> gE, gS, gW, gT, gPA, gSP, gKc;
   for (int s = 0; s < nsub; ++s) {
     const int cI = (int)round_up(C->nI[s], 4);
@@ -1050,6 +1253,8 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
           2.0 * nc * nc * ng;
     lb += (int64_t)((ni * ni + 2.0 * ni * ng + nr * nr + 2.0 * ng * nc) * C->esize);
   }
+  fl += dlx_flops;
+  lb += dlx_bytes;
   // multilevel: coarse problem and its BDDC context
   if (C->levels == 3 && C->n_pi > 0) {
     C->coarse_prob.reset(new fem_problem);
@@ -1123,6 +1328,26 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
   copy_e_kernel<T><<<dim3(cdiv((int64_t)C->maxI * C->maxG, 256), nsub), 256, 0, s>>>(
       C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offE.p, C->d_ldS.p, Et, Aloc);
   CB_LAUNCH();
+  // 2b. deluxe scaling from the class blocks of the Schur complements:
+  //     Shat_K = sum_b S_b inverted by a sweep, D_b = Shat_K^-1 S_b, E_b = D_b^T
+  if (C->n_dlx > 0) {
+    T* Dsb = reinterpret_cast<T*>(C->Dsb.p);
+    T* Ddb = reinterpret_cast<T*>(C->Ddb.p);
+    T* Dsh = reinterpret_cast<T*>(C->Dsh.p);
+    deluxe_gather_kernel<T><<<C->n_dlx, 256, 0, s>>>(C->dlx_n.p, C->dlx_sub.p, C->dlx_ld.p, C->dlx_poff.p,
+                                                     C->dlx_pos.p, C->dlx_off.p, C->d_nI.p, C->d_offA.p,
+                                                     C->d_ldA.p, Aloc, Dsb);
+    CB_LAUNCH();
+    deluxe_sum_kernel<T><<<C->n_dcls, 256, 0, s>>>(C->dcls_ptr.p, C->dcls_blk.p, C->dlx_n.p, C->dlx_ld.p,
+                                                   C->dlx_off.p, C->dcls_off.p, Dsb, Dsh);
+    CB_LAUNCH();
+    run_sweep<T>(C->swd, C->n_dcls, C->gl_swd, C->maxDn, C->maxDn, Dsh, reinterpret_cast<T*>(C->DX.p),
+                 reinterpret_cast<T*>(C->DY.p), reinterpret_cast<T*>(C->DP.p), status, tol, s);
+    launch_list<T, false, false>(C->gl_dlx, Dsh, Dsb, Ddb, T(1), T(0), s);
+    deluxe_transpose_kernel<T><<<C->n_dlx, 256, 0, s>>>(C->dlx_n.p, C->dlx_ld.p, C->dlx_off.p, Ddb,
+                                                        reinterpret_cast<T*>(C->Deb.p));
+    CB_LAUNCH();
+  }
   // 3. Schur complement copy, augmentation and sweep over Gamma_r
   copy_schur_kernel<T><<<dim3(cdiv((int64_t)C->maxG * C->maxG, 256), nsub), 256, 0, s>>>(
       C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offS.p, C->d_ldS.p, Aloc, Sw);
@@ -1192,38 +1417,51 @@ void bddc_run_setup(bddc_ctx* C, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------- apply
+namespace {
+
+struct ApplyWork {
+  double *u0, *hG, *gI, *gl, *wG, *cl, *rc, *uc, *yG, *xI, *zl, *yD;
+};
+
+// z = M^-1 r with caller-chosen work vectors (the context's own, or the
+// static array of bddc_apply_noalloc).
 template <typename T>
-static void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
-  const int nsub = C->nsub;
+void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w, cudaStream_t s) {
   const T* Aloc = reinterpret_cast<const T*>(C->Aloc.p);
   const T* Sw = reinterpret_cast<const T*>(C->Sw.p);
   const T* Phi = reinterpret_cast<const T*>(C->Phi.p);
-  double* gl = C->gl.p;
   const size_t smI = (size_t)round_up(std::max(C->maxI, 4), 4) * sizeof(T);
-  gather_kernel<<<cdiv(std::max<int64_t>(C->totI, 1), 256), 256, 0, s>>>(C->gdofI.p, C->totI, r, C->xI.p);
+  const size_t smD = (size_t)round_up(std::max(C->maxDn, 4), 4) * sizeof(T);
+  gather_kernel<<<cdiv(std::max<int64_t>(C->totI, 1), 256), 256, 0, s>>>(C->gdofI.p, C->totI, r, w.xI);
   CB_LAUNCH();
   if (C->n_itI > 0) {
     apply_interior_kernel<T><<<C->n_itI, 256, smI, s>>>(
-        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, Aloc, C->xI.p, C->u0.p);
+        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, Aloc, w.xI, w.u0);
     CB_LAUNCH();
   }
   if (C->maxG > 0) {
     if (C->n_itG > 0) {
       apply_gi_kernel<T><<<C->n_itG, 256, smI, s>>>(
-          C->itG.p, C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, Aloc, C->u0.p, C->hG.p);
+          C->itG.p, C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, Aloc, w.u0, w.hG);
       CB_LAUNCH();
     }
   }
   if (C->n_if > 0) {
     assemble_g_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
-                                                        r, C->hG.p, C->gI.p);
+                                                        r, w.hG, w.gI);
     CB_LAUNCH();
-    restrict_kernel<<<cdiv(C->totG, 256), 256, 0, s>>>(C->gam_if.p, C->Dg.p, C->totG, C->gI.p, gl);
+    restrict_kernel<<<cdiv(C->totG, 256), 256, 0, s>>>(C->gam_if.p, C->Dg.p, C->totG, w.gI, w.gl);
     CB_LAUNCH();
+    if (C->n_dlx > 0) {  // deluxe: g_i = D_b^T g on each class
+      deluxe_apply_kernel<T, true><<<dim3(C->n_dlx, cdiv(C->maxDn, DLX_COLS)), DLX_COLS, smD, s>>>(
+          C->dlx_n.p, C->dlx_sub.p, C->dlx_ld.p, C->dlx_poff.p, C->dlx_pos.p, C->dlx_off.p, C->d_offGam.p,
+          C->gam_if.p, reinterpret_cast<const T*>(C->Ddb.p), w.gI, w.gl);
+      CB_LAUNCH();
+    }
     if (C->n_itG > 0) {
       apply_local_kernel<T><<<C->n_itG, 256,
                               (size_t)round_up(std::max(C->maxR, 4), 4) * sizeof(T), s>>>(
-          C->itG.p, C->d_nG.p, C->d_nr.p, C->d_offS.p, C->d_ldS.p, C->d_offGam.p, Sw, gl, C->wG.p);
+          C->itG.p, C->d_nG.p, C->d_nr.p, C->d_offS.p, C->d_ldS.p, C->d_offGam.p, Sw, w.gl, w.wG);
       CB_LAUNCH();
     }
     if (C->n_pi > 0) {
@@ -1231,38 +1469,56 @@ static void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) 
       if (C->n_itP > 0) {
         apply_phit_kernel<T><<<C->n_itP, 256, 0, s>>>(C->itP.p, C->d_nG.p, C->d_nc.p, C->d_offPhi.p,
                                                             C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, Phi,
-                                                            gl, C->cl.p, nch);
+                                                            w.gl, w.cl, nch);
         CB_LAUNCH();
       }
-      coarse_rhs_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, C->cl.p, nch,
-                                                           C->cnch.p, C->rc.p);
+      coarse_rhs_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, w.cl, nch,
+                                                           C->cnch.p, w.rc);
       CB_LAUNCH();
       if (C->next) {
-        bddc_run_apply(C->next.get(), C->rc.p, C->uc.p, s);
+        // the level-2 context uses its own work vectors, allocated at setup
+        bddc_run_apply(C->next.get(), w.rc, w.uc, s);
       } else {
-        dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, C->rc.p,
-                                                                           C->uc.p);
+        dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, w.rc, w.uc);
         CB_LAUNCH();
       }
     }
     if (C->n_itR > 0) {
       apply_prolong_kernel<T><<<C->n_itR, 256, 0, s>>>(
           C->itR.p, C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, C->gprim.p, Phi,
-          C->uc.p, C->wG.p, C->Dg.p, C->yG.p);
+          w.uc, w.wG, C->Dg.p, w.yG);
       CB_LAUNCH();
     }
+    const double* yavg = w.yG;
+    if (C->n_dlx > 0) {  // deluxe: the class part of y_i becomes D_b y_i
+      CB_CUDA(cudaMemcpyAsync(w.yD, w.yG, (size_t)C->totG * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      deluxe_apply_kernel<T, false><<<dim3(C->n_dlx, cdiv(C->maxDn, DLX_COLS)), DLX_COLS, smD, s>>>(
+          C->dlx_n.p, C->dlx_sub.p, C->dlx_ld.p, C->dlx_poff.p, C->dlx_pos.p, C->dlx_off.p, C->d_offGam.p,
+          C->gam_if.p, reinterpret_cast<const T*>(C->Deb.p), w.yG, w.yD);
+      CB_LAUNCH();
+      yavg = w.yD;
+    }
     average_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
-                                                     C->yG.p, z, C->zl.p);
+                                                     yavg, z, w.zl);
     CB_LAUNCH();
   }
   if (C->n_itI > 0) {
     apply_extend_kernel<T><<<C->n_itI, 256,
                              (size_t)round_up(std::max(C->maxG, 4), 4) * sizeof(T), s>>>(
         C->itI.p, C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p,
-        Aloc, C->zl.p, C->u0.p, z);
+        Aloc, w.zl, w.u0, z);
     CB_LAUNCH();
   }
 }
+
+template <typename T>
+void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
+  ApplyWork w{C->u0.p, C->hG.p, C->gI.p, C->gl.p, C->wG.p, C->cl.p, C->rc.p,
+              C->uc.p, C->yG.p, C->xI.p, C->zl.p, C->yD.p};
+  apply_with_work<T>(C, r, z, w, s);
+}
+
+}  // namespace
 
 void bddc_run_apply(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
   timer_begin(CBDDC_TIMER_APPLY, s);
@@ -1300,88 +1556,13 @@ double* noalloc_scratch_address() {
   return static_cast<double*>(ptr);
 }
 
-struct ApplyWork {
-  double *u0, *hG, *gI, *gl, *wG, *cl, *rc, *uc, *yG, *xI, *zl;
-};
-
-// Same launch sequence as apply_impl, with caller-chosen work vectors.
-template <typename T>
-void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w, cudaStream_t s) {
-  const int nsub = C->nsub;
-  const T* Aloc = reinterpret_cast<const T*>(C->Aloc.p);
-  const T* Sw = reinterpret_cast<const T*>(C->Sw.p);
-  const T* Phi = reinterpret_cast<const T*>(C->Phi.p);
-  const size_t smI = (size_t)round_up(std::max(C->maxI, 4), 4) * sizeof(T);
-  gather_kernel<<<cdiv(std::max<int64_t>(C->totI, 1), 256), 256, 0, s>>>(C->gdofI.p, C->totI, r, w.xI);
-  CB_LAUNCH();
-  if (C->n_itI > 0) {
-    apply_interior_kernel<T><<<C->n_itI, 256, smI, s>>>(
-        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, Aloc, w.xI, w.u0);
-    CB_LAUNCH();
-  }
-  if (C->maxG > 0) {
-    if (C->n_itG > 0) {
-      apply_gi_kernel<T><<<C->n_itG, 256, smI, s>>>(
-          C->itG.p, C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, Aloc, w.u0, w.hG);
-      CB_LAUNCH();
-    }
-  }
-  if (C->n_if > 0) {
-    assemble_g_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
-                                                        r, w.hG, w.gI);
-    CB_LAUNCH();
-    restrict_kernel<<<cdiv(C->totG, 256), 256, 0, s>>>(C->gam_if.p, C->Dg.p, C->totG, w.gI, w.gl);
-    CB_LAUNCH();
-    if (C->n_itG > 0) {
-      apply_local_kernel<T><<<C->n_itG, 256,
-                              (size_t)round_up(std::max(C->maxR, 4), 4) * sizeof(T), s>>>(
-          C->itG.p, C->d_nG.p, C->d_nr.p, C->d_offS.p, C->d_ldS.p, C->d_offGam.p, Sw, w.gl, w.wG);
-      CB_LAUNCH();
-    }
-    if (C->n_pi > 0) {
-      const int nch = (int)cdiv(C->maxG, PHIT_ROWS);
-      if (C->n_itP > 0) {
-        apply_phit_kernel<T><<<C->n_itP, 256, 0, s>>>(C->itP.p, C->d_nG.p, C->d_nc.p, C->d_offPhi.p,
-                                                            C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, Phi,
-                                                            w.gl, w.cl, nch);
-        CB_LAUNCH();
-      }
-      coarse_rhs_kernel<<<cdiv(C->n_pi, 256), 256, 0, s>>>(C->cg_ptr.p, C->cg_src.p, C->n_pi, w.cl, nch,
-                                                           C->cnch.p, w.rc);
-      CB_LAUNCH();
-      if (C->next) {
-        // the level-2 context uses its own work vectors, allocated at setup
-        bddc_run_apply(C->next.get(), w.rc, w.uc, s);
-      } else {
-        dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, w.rc, w.uc);
-        CB_LAUNCH();
-      }
-    }
-    if (C->n_itR > 0) {
-      apply_prolong_kernel<T><<<C->n_itR, 256, 0, s>>>(
-          C->itR.p, C->d_nG.p, C->d_nc.p, C->d_offPhi.p, C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, C->gprim.p, Phi,
-          w.uc, w.wG, C->Dg.p, w.yG);
-      CB_LAUNCH();
-    }
-    average_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
-                                                     w.yG, z, w.zl);
-    CB_LAUNCH();
-  }
-  if (C->n_itI > 0) {
-    apply_extend_kernel<T><<<C->n_itI, 256,
-                             (size_t)round_up(std::max(C->maxG, 4), 4) * sizeof(T), s>>>(
-        C->itI.p, C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p,
-        Aloc, w.zl, w.u0, z);
-    CB_LAUNCH();
-  }
-}
-
 }  // namespace
 
 int64_t bddc_noalloc_scratch_needed(const bddc_ctx* C) {
   auto pad = [](int64_t n) { return round_up(std::max<int64_t>(n, 1), 32); };
   const int64_t nch = cdiv(std::max(C->maxG, 1), PHIT_ROWS);
-  return 2 * pad(C->totI) + 5 * pad(C->totG) + pad(C->n_if) + pad(C->totC * nch) + 2 * pad(C->n_pi);
+  return 2 * pad(C->totI) + (C->n_dlx > 0 ? 6 : 5) * pad(C->totG) + pad(C->n_if) + pad(C->totC * nch) +
+         2 * pad(C->n_pi);
 }
 
 int64_t bddc_noalloc_scratch_capacity() { return kNoAllocScratchDoubles; }
@@ -1406,7 +1587,8 @@ void bddc_run_apply_noalloc(bddc_ctx* C, const double* r, double* z, cudaStream_
   w.gI = p; p += pad(C->n_if);
   w.cl = p; p += pad(C->totC * (int64_t)cdiv(std::max(C->maxG, 1), PHIT_ROWS));
   w.rc = p; p += pad(C->n_pi);
-  w.uc = p;
+  w.uc = p; p += pad(C->n_pi);
+  w.yD = C->n_dlx > 0 ? p : nullptr;
   if (C->precision == CBDDC_FP32) apply_with_work<float>(C, r, z, w, s);
   else apply_with_work<double>(C, r, z, w, s);
 }
@@ -1417,6 +1599,8 @@ int64_t bddc_ctx::device_bytes() const {
   return (int64_t)(Aloc.bytes() + Sw.bytes() + Phi.bytes() + Y.bytes() + Zf.bytes() + Wf.bytes() +
                    G.bytes() + SPhi.bytes() + Kc.bytes() + Xp.bytes() + Yp.bytes() + Pd.bytes() + Et.bytes() +
                    Sc.bytes() + ScX.bytes() + ScY.bytes() + ScP.bytes() + u0.bytes() + hG.bytes() +
-                   gI.bytes() + wG.bytes() + cl.bytes() + rc.bytes() + uc.bytes() + yG.bytes() + gl.bytes() + xI.bytes() + zl.bytes()) +
+                   gI.bytes() + wG.bytes() + cl.bytes() + rc.bytes() + uc.bytes() + yG.bytes() + gl.bytes() + xI.bytes() + zl.bytes() +
+                   Dsb.bytes() + Ddb.bytes() + Deb.bytes() + Dsh.bytes() + DX.bytes() + DY.bytes() + DP.bytes() +
+                   yD.bytes()) +
          (next ? next->device_bytes() + coarse_prob->device_bytes() : 0);
 }

@@ -48,6 +48,19 @@ struct bddc_ctx {
   std::vector<cbddc::GemmList> gl_sw1, gl_sw2, gl_swg, gl_swc;
   cbddc::GemmList gl_E, gl_S, gl_W, gl_T, gl_PhiA, gl_SPhi, gl_Kc;
   cbddc::DVec<double> gl;                  // scaled interface restriction
+  // deluxe scaling: blocks b = (edge or face class K, subdomain s sharing
+  // it) with the class DoFs' positions in s's interface vector; S_b (class
+  // block of s's Schur complement), D_b = Shat_K^-1 S_b (Shat_K = sum of
+  // the class's S_b, inverted in place) and E_b = D_b^T share the offsets
+  int scaling = CBDDC_SCALING_COUNTING;
+  int n_dlx = 0, n_dcls = 0, maxDn = 0, stepsd = 0;
+  cbddc::DVec<int> dlx_n, dlx_sub, dlx_ld, dlx_pos, dcls_ptr, dcls_blk;
+  cbddc::DVec<int64_t> dlx_poff, dlx_off, dcls_off;
+  cbddc::DVec<unsigned char> Dsb, Ddb, Deb, Dsh, DX, DY, DP;
+  cbddc::DVec<cbddc::SweepDesc> swd;
+  std::vector<cbddc::GemmList> gl_swd;
+  cbddc::GemmList gl_dlx;
+  cbddc::DVec<double> yD;                  // averaging input, deluxe blocks applied
   double setup_flops = 0.0, apply_flops = 0.0;
   int64_t local_bytes = 0;
   // Krylov and Newton workspaces (allocated on first use)

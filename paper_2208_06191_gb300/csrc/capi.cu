@@ -112,6 +112,7 @@ static void ensure_ctx(fem_problem* P, const solve_options* opt, bddc_ctx** C) {
   bo.part2 = opt->part2;
   bo.primal2 = opt->primal2;
   bo.precision2 = opt->precision2;
+  bo.scaling = opt->scaling;
   bddc_ctx* c = new bddc_ctx;
   try {
     bddc_create(P, &bo, c);
@@ -317,7 +318,7 @@ int bddc_setup(fem_problem* P, const fem_tangent* K, const bddc_options* opt, bd
     } else {
       bddc_ctx* c = *inout;
       CB_CHECK(c->P == P && c->precision == opt->precision && c->primal == opt->primal &&
-                   c->levels == (opt->levels >= 3 ? 3 : 2),
+                   c->levels == (opt->levels >= 3 ? 3 : 2) && c->scaling == opt->scaling,
                CBDDC_EINVAL, "context was created for another problem or options");
     }
     bddc_run_setup(*inout, s);
