@@ -247,7 +247,7 @@ typedef struct {
   int precision2;
   int scaling;       /* CBDDC_SCALING_COUNTING (0) or CBDDC_SCALING_DELUXE;
                         deluxe allows at most 65535 edge and face classes,
-                        of at most 2048 nodes each (CBDDC_EINVAL otherwise) */
+                        of at most 1024 nodes each (CBDDC_EINVAL otherwise) */
 } bddc_options;
 
 typedef struct bddc_ctx bddc_ctx;

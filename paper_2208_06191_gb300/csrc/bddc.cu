@@ -282,7 +282,8 @@ __global__ void cons_g_kernel(const int* __restrict__ na, const int64_t* __restr
 // ------------------------------------------------- deluxe scaling (setup)
 // S_b = the class block of block b's subdomain Schur complement S = A_GG -
 // A_GI A_II^-1 A_IG (the GG block of Aloc), rows and columns at the class
-// DoFs' interface positions.  One CTA per block.
+// DoFs' interface positions.  Block b = blockIdx.x; its n^2 entries are
+// spread over the gridDim.y CTAs of the block.
 template <typename T>
 __global__ void __launch_bounds__(256)
 deluxe_gather_kernel(const int* __restrict__ bn, const int* __restrict__ bsub, const int* __restrict__ bld,
@@ -296,13 +297,14 @@ deluxe_gather_kernel(const int* __restrict__ bn, const int* __restrict__ bsub, c
   const T* S = Aloc + offA[s] + (int64_t)ni * lda + round_up_dev(ni, 4);
   const int* p = pos + poff[b];
   T* out = Sb + boff[b];
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+  for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n * n; t += gridDim.y * blockDim.x) {
     const int i = t / n, j = t % n;
     out[(int64_t)i * ld + j] = S[(int64_t)p[i] * lda + p[j]];
   }
 }
 
-// Shat_K = sum of the class's blocks S_b, in block order.  One CTA per class.
+// Shat_K = sum of the class's blocks S_b, in block order.  Class k =
+// blockIdx.x, its entries spread over gridDim.y CTAs.
 template <typename T>
 __global__ void __launch_bounds__(256)
 deluxe_sum_kernel(const int* __restrict__ cptr, const int* __restrict__ cblk, const int* __restrict__ bn,
@@ -312,7 +314,7 @@ deluxe_sum_kernel(const int* __restrict__ cptr, const int* __restrict__ cblk, co
   const int b0 = cptr[k], b1 = cptr[k + 1];
   const int n = bn[cblk[b0]], ld = bld[cblk[b0]];
   T* out = Sh + coff[k];
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+  for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n * n; t += gridDim.y * blockDim.x) {
     const int i = t / n, j = t % n;
     T v = T(0);
     for (int q = b0; q < b1; ++q) v += Sb[boff[cblk[q]] + (int64_t)i * ld + j];
@@ -320,7 +322,7 @@ deluxe_sum_kernel(const int* __restrict__ cptr, const int* __restrict__ cblk, co
   }
 }
 
-// E_b = D_b^T.  One CTA per block.
+// E_b = D_b^T.  Block b = blockIdx.x, its entries spread over gridDim.y CTAs.
 template <typename T>
 __global__ void __launch_bounds__(256)
 deluxe_transpose_kernel(const int* __restrict__ bn, const int* __restrict__ bld,
@@ -329,7 +331,7 @@ deluxe_transpose_kernel(const int* __restrict__ bn, const int* __restrict__ bld,
   const int n = bn[b], ld = bld[b];
   const T* d = D + boff[b];
   T* e = E + boff[b];
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+  for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n * n; t += gridDim.y * blockDim.x) {
     const int i = t / n, j = t % n;
     e[(int64_t)j * ld + i] = d[(int64_t)i * ld + j];
   }
@@ -552,12 +554,13 @@ __global__ void dense_gemv_kernel(const double* __restrict__ A, int n, const dou
 // Restriction: x_i = gI[gam_if[og + pos_i]] (assembled interface values),
 // M_b = D_b, so g_i gets D_b^T g on the class.  Extension: x_i = yG[og +
 // pos_i], M_b = E_b = D_b^T, so the class part of y_i becomes D_b y_i.
-// Inputs and outputs are different vectors, so the 128-column slices of a
-// block (blockIdx.y) run independently; one output per thread, columns of
-// M_b read coalesced.
-constexpr int DLX_COLS = 128;
+// Inputs and outputs are different vectors, so the 64-column slices of a
+// block (blockIdx.y) run independently.  Thread (g, c) sums rows i = g mod
+// 4 of column c (a warp reads 32 consecutive entries of a row), and the
+// four partial sums are added in a fixed order.
+constexpr int DLX_COLS = 64, DLX_RG = 4;
 template <typename T, bool GATHER>
-__global__ void __launch_bounds__(DLX_COLS)
+__global__ void __launch_bounds__(DLX_COLS * DLX_RG)
 deluxe_apply_kernel(const int* __restrict__ bn, const int* __restrict__ bsub, const int* __restrict__ bld,
                     const int64_t* __restrict__ poff, const int* __restrict__ pos,
                     const int64_t* __restrict__ boff, const int64_t* __restrict__ offGam,
@@ -565,10 +568,11 @@ deluxe_apply_kernel(const int* __restrict__ bn, const int* __restrict__ bsub, co
                     const double* __restrict__ in, double* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* xs = reinterpret_cast<T*>(smraw);
+  __shared__ T part[DLX_RG][DLX_COLS];
   const int b = blockIdx.x;
   const int n = bn[b];
   const int j0 = blockIdx.y * DLX_COLS;
-  if (j0 >= n) return;
+  if (j0 >= n) return;  // whole CTA
   const int64_t og = offGam[bsub[b]];
   const int* p = pos + poff[b];
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -576,14 +580,23 @@ deluxe_apply_kernel(const int* __restrict__ bn, const int* __restrict__ bsub, co
     xs[i] = (T)(GATHER ? in[gam_if[q]] : in[q]);
   }
   __syncthreads();
-  const int j = j0 + threadIdx.x;
-  if (j >= n) return;
-  const T* Mb = M + boff[b] + j;
-  const int ld = bld[b];
+  const int c = threadIdx.x % DLX_COLS, g = threadIdx.x / DLX_COLS;
+  const int j = j0 + c;
   T acc = T(0);
-#pragma unroll 8
-  for (int i = 0; i < n; ++i) acc = fma(Mb[(int64_t)i * ld], xs[i], acc);
-  out[og + p[j]] = (double)acc;
+  if (j < n) {
+    const T* Mb = M + boff[b] + j;
+    const int64_t ld = bld[b];
+#pragma unroll 4
+    for (int i = g; i < n; i += DLX_RG) acc = fma(Mb[i * ld], xs[i], acc);
+  }
+  part[g][c] = acc;
+  __syncthreads();
+  if (g == 0 && j < n) {
+    T v = part[0][c];
+#pragma unroll
+    for (int q = 1; q < DLX_RG; ++q) v += part[q][c];
+    out[og + p[j]] = (double)v;
+  }
 }
 
 // y_i = D_i (w_i + Phi_i R_Pi u_c); 8 lanes per interface row.
@@ -781,8 +794,8 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     for (auto& f : P->faces) dcls.push_back(&f);
     CB_CHECK(dcls.size() <= 65535, CBDDC_EINVAL, "deluxe scaling allows at most 65535 interface classes");
     for (size_t k = 0; k < dcls.size(); ++k) {
-      CB_CHECK(!dcls[k]->empty() && dcls[k]->size() <= 2048, CBDDC_EINVAL,
-               "deluxe scaling allows classes of 1 to 2048 nodes");
+      CB_CHECK(!dcls[k]->empty() && dcls[k]->size() <= 1024, CBDDC_EINVAL,
+               "deluxe scaling allows classes of 1 to 1024 nodes");
       for (int v : *dcls[k]) node_dcls[v] = (int)k;
     }
   }
@@ -1325,26 +1338,30 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
   if (C->maxG == 0) return;  // one subdomain: no interface
   launch_list<T, false, false>(C->gl_E, Aloc, Aloc, Et, T(1), T(0), s);
   launch_list<T, false, false>(C->gl_S, Aloc, Et, Aloc, T(-1), T(1), s);
-  copy_e_kernel<T><<<dim3(cdiv((int64_t)C->maxI * C->maxG, 256), nsub), 256, 0, s>>>(
-      C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offE.p, C->d_ldS.p, Et, Aloc);
-  CB_LAUNCH();
+  if (C->maxI > 0) {
+    copy_e_kernel<T><<<dim3(cdiv((int64_t)C->maxI * C->maxG, 256), nsub), 256, 0, s>>>(
+        C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offE.p, C->d_ldS.p, Et, Aloc);
+    CB_LAUNCH();
+  }
   // 2b. deluxe scaling from the class blocks of the Schur complements:
   //     Shat_K = sum_b S_b inverted by a sweep, D_b = Shat_K^-1 S_b, E_b = D_b^T
   if (C->n_dlx > 0) {
     T* Dsb = reinterpret_cast<T*>(C->Dsb.p);
     T* Ddb = reinterpret_cast<T*>(C->Ddb.p);
     T* Dsh = reinterpret_cast<T*>(C->Dsh.p);
-    deluxe_gather_kernel<T><<<C->n_dlx, 256, 0, s>>>(C->dlx_n.p, C->dlx_sub.p, C->dlx_ld.p, C->dlx_poff.p,
+    const dim3 gb(C->n_dlx, std::min<unsigned>(cdiv((int64_t)C->maxDn * C->maxDn, 256), 64));
+    const dim3 gk(C->n_dcls, gb.y);
+    deluxe_gather_kernel<T><<<gb, 256, 0, s>>>(C->dlx_n.p, C->dlx_sub.p, C->dlx_ld.p, C->dlx_poff.p,
                                                      C->dlx_pos.p, C->dlx_off.p, C->d_nI.p, C->d_offA.p,
                                                      C->d_ldA.p, Aloc, Dsb);
     CB_LAUNCH();
-    deluxe_sum_kernel<T><<<C->n_dcls, 256, 0, s>>>(C->dcls_ptr.p, C->dcls_blk.p, C->dlx_n.p, C->dlx_ld.p,
+    deluxe_sum_kernel<T><<<gk, 256, 0, s>>>(C->dcls_ptr.p, C->dcls_blk.p, C->dlx_n.p, C->dlx_ld.p,
                                                    C->dlx_off.p, C->dcls_off.p, Dsb, Dsh);
     CB_LAUNCH();
     run_sweep<T>(C->swd, C->n_dcls, C->gl_swd, C->maxDn, C->maxDn, Dsh, reinterpret_cast<T*>(C->DX.p),
                  reinterpret_cast<T*>(C->DY.p), reinterpret_cast<T*>(C->DP.p), status, tol, s);
     launch_list<T, false, false>(C->gl_dlx, Dsh, Dsb, Ddb, T(1), T(0), s);
-    deluxe_transpose_kernel<T><<<C->n_dlx, 256, 0, s>>>(C->dlx_n.p, C->dlx_ld.p, C->dlx_off.p, Ddb,
+    deluxe_transpose_kernel<T><<<gb, 256, 0, s>>>(C->dlx_n.p, C->dlx_ld.p, C->dlx_off.p, Ddb,
                                                         reinterpret_cast<T*>(C->Deb.p));
     CB_LAUNCH();
   }
@@ -1377,11 +1394,14 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
     launch_list<T, false, false>(C->gl_T, Y, Wf, Sw, T(-1), T(1), s);
     launch_list<T, false, false>(C->gl_PhiA, Y, G, Phi, T(1), T(0), s);
   }
-  // 5. vertex columns of Phi and the identity block
-  phi_vertex_kernel<T><<<dim3(cdiv((int64_t)C->maxG * C->maxC, 256), nsub), 256, 0, s>>>(
-      C->d_nG.p, C->d_nr.p, C->d_nv.p, C->d_nc.p, C->d_offS.p, C->d_ldS.p, C->d_offPhi.p, C->d_ldPhi.p,
-      Sw, Phi);
-  CB_LAUNCH();
+  // 5. vertex columns of Phi and the identity block (no primal constraint
+  //    anywhere: Phi has no columns)
+  if (C->maxC > 0) {
+    phi_vertex_kernel<T><<<dim3(cdiv((int64_t)C->maxG * C->maxC, 256), nsub), 256, 0, s>>>(
+        C->d_nG.p, C->d_nr.p, C->d_nv.p, C->d_nc.p, C->d_offS.p, C->d_ldS.p, C->d_offPhi.p, C->d_ldPhi.p,
+        Sw, Phi);
+    CB_LAUNCH();
+  }
   // 6. local coarse matrices Phi^T S Phi and the FP64 coarse inverse
   if (C->n_pi > 0) {
     launch_list<T, false, false>(C->gl_SPhi, Aloc, Phi, SPhi, T(1), T(0), s);
@@ -1453,7 +1473,7 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
     restrict_kernel<<<cdiv(C->totG, 256), 256, 0, s>>>(C->gam_if.p, C->Dg.p, C->totG, w.gI, w.gl);
     CB_LAUNCH();
     if (C->n_dlx > 0) {  // deluxe: g_i = D_b^T g on each class
-      deluxe_apply_kernel<T, true><<<dim3(C->n_dlx, cdiv(C->maxDn, DLX_COLS)), DLX_COLS, smD, s>>>(
+      deluxe_apply_kernel<T, true><<<dim3(C->n_dlx, cdiv(C->maxDn, DLX_COLS)), DLX_COLS * DLX_RG, smD, s>>>(
           C->dlx_n.p, C->dlx_sub.p, C->dlx_ld.p, C->dlx_poff.p, C->dlx_pos.p, C->dlx_off.p, C->d_offGam.p,
           C->gam_if.p, reinterpret_cast<const T*>(C->Ddb.p), w.gI, w.gl);
       CB_LAUNCH();
@@ -1492,7 +1512,7 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
     const double* yavg = w.yG;
     if (C->n_dlx > 0) {  // deluxe: the class part of y_i becomes D_b y_i
       CB_CUDA(cudaMemcpyAsync(w.yD, w.yG, (size_t)C->totG * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      deluxe_apply_kernel<T, false><<<dim3(C->n_dlx, cdiv(C->maxDn, DLX_COLS)), DLX_COLS, smD, s>>>(
+      deluxe_apply_kernel<T, false><<<dim3(C->n_dlx, cdiv(C->maxDn, DLX_COLS)), DLX_COLS * DLX_RG, smD, s>>>(
           C->dlx_n.p, C->dlx_sub.p, C->dlx_ld.p, C->dlx_poff.p, C->dlx_pos.p, C->dlx_off.p, C->d_offGam.p,
           C->gam_if.p, reinterpret_cast<const T*>(C->Deb.p), w.yG, w.yD);
       CB_LAUNCH();
