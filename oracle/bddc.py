@@ -226,13 +226,21 @@ class BDDC:
     classes, fine level of a two-level method only: the rotations need node
     coordinates, and a coarse node of the multilevel method carries 3 DoFs).
     ``scaling``: "counting" or "deluxe" on this level (a level-2 method
-    takes its own from ``level2["scaling"]``, counting by default)."""
+    takes its own from ``level2["scaling"]``, counting by default).
+    ``coarse``: "galerkin" uses the one basis Phi (minimum energy for A) on
+    both sides of the coarse problem, Phi^T A Phi; "petrov" is the
+    nonsymmetric BDDC with a left basis Psi, the same construction for A^T:
+    coarse matrix Psi^T A Phi and coarse right-hand side Psi^T g_i (the two
+    agree for a symmetric tangent)."""
 
     def __init__(self, fe, Ke=None, Kf=None, primal="V", classification=None, level2=None,
-                 scaling="counting"):
+                 scaling="counting", coarse="galerkin"):
         if scaling not in ("counting", "deluxe"):
             raise ValueError("scaling is 'counting' or 'deluxe'")
+        if coarse not in ("galerkin", "petrov"):
+            raise ValueError("coarse is 'galerkin' or 'petrov'")
         self.scaling = scaling
+        self.coarse_kind = coarse
         level = fe if isinstance(fe, CoarseLevel) else FineLevel(fe, Ke, Kf)
         self.level = level
         cl = classification or Classification(level)
@@ -330,14 +338,29 @@ class BDDC:
                 sol = lu_sad.solve(rhs)
                 Phi[ldofR, :] = sol[:ldofR.size]
                 gP = np.concatenate([gV, np.array(gA, dtype=np.int64)])
-                Sc = Phi.T @ (A @ Phi)
+                Psi = Phi
+                if coarse == "petrov":
+                    # left basis: the same saddle problem for A^T
+                    AT = A.T.tocsr()
+                    sadT = sp.bmat([[AT[ldofR][:, ldofR], Cr.T], [Cr, None]], format="csc") \
+                        if na else AT[ldofR][:, ldofR].tocsc()
+                    rhsT = np.zeros((ldofR.size + na, nc))
+                    Psi = np.zeros((3 * nloc, nc))
+                    if nv:
+                        rhsT[:ldofR.size, :nv] = -AT[ldofR][:, ldofV].toarray()
+                        Psi[ldofV, np.arange(nv)] = 1.0
+                    if na:
+                        rhsT[ldofR.size:, nv:] = np.eye(na)
+                    Psi[ldofR, :] = spla.splu(sadT).solve(rhsT)[:ldofR.size]
+                Sc = Psi.T @ (A @ Phi)
             else:
                 gP = np.zeros(0, dtype=np.int64)
                 Sc = np.zeros((0, 0))
+                Psi = Phi
             Sc_list.append(Sc)
             AII = A[ldofI][:, ldofI].tocsc()
             sub = dict(nodes=nodes, A=A, gdof=gdof, ldofI=ldofI, ldofG=ldofG,
-                       ldofR=ldofR, Dg=Dg, lu_sad=lu_sad, na=na, Phi=Phi,
+                       ldofR=ldofR, Dg=Dg, lu_sad=lu_sad, na=na, Phi=Phi, Psi=Psi,
                        gP=gP, Sc=Sc,
                        luII=spla.splu(AII) if ldofI.size else None,
                        AGI=A[ldofG][:, ldofI], AIG=A[ldofI][:, ldofG])
@@ -352,7 +375,8 @@ class BDDC:
                                  Sc_list, level2["part"], level2["n_parts"])
             self.coarse = BDDC(clevel, primal=level2.get("primal", "VEF"),
                                level2=level2.get("level2"),
-                               scaling=level2.get("scaling", "counting"))
+                               scaling=level2.get("scaling", "counting"),
+                               coarse=level2.get("coarse", coarse))
             self.S_pipi = None
         else:
             S = np.zeros((self.n_pi, self.n_pi))
@@ -436,7 +460,7 @@ class BDDC:
             f[sub["ldofG"]] = fG
             w = self._local_solve(sub, f)
             if sub["gP"].size:
-                np.add.at(c, sub["gP"], sub["Phi"].T @ f)
+                np.add.at(c, sub["gP"], sub["Psi"].T @ f)
             ws.append(w)
         uc = self.coarse_solve(c)
         zG = np.zeros_like(r)

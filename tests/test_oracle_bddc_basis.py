@@ -13,7 +13,11 @@ For a symmetric tangent both forms are the same operator (the dense
 matrices agree to rounding), for every primal space (vertices, edge and
 face averages, rigid-body rotations) and for counting and deluxe scaling.
 The tangent is symmetric without follower pressure: the active stress is
-the derivative of gamma |F f|."""
+the derivative of gamma |F f|.  With follower pressure the tangent is
+nonsymmetric; eliminating the dual DoFs of S~ then gives the coarse
+problem with a right basis from S and a left basis from S^T, which is the
+oracle's "petrov" coarse space, and not its one-basis Galerkin coarse
+space."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -140,16 +144,13 @@ def _change_of_basis_inverse(fe, subs, cl, primal, deluxe, gamma_dofs):
     return left @ np.linalg.solve(St, right)
 
 
-@pytest.mark.parametrize("primal", ["V", "VE", "VEF", "EF", "VER", "EFR"])
-@pytest.mark.parametrize("scaling", ["counting", "deluxe"])
-def test_lagrange_form_equals_change_of_basis(primal, scaling):
-    prob = slab_problem(4, 4, 3, parts=(2, 2, 1), jitter=0.15, pressure=0.0, gamma=3e4)
+def _dense_pair(pressure, primal, scaling, coarse="galerkin"):
+    prob = slab_problem(4, 4, 3, parts=(2, 2, 1), jitter=0.15, pressure=pressure, gamma=3e4)
     fe = FEProblem(prob)
     d = 2e-3 * np.random.default_rng(7).standard_normal(fe.n_free)
     K, (Ke, Kf) = fe.tangent(d, 1.0)
     Kd = K.toarray()
-    assert np.abs(Kd - Kd.T).max() <= 1e-12 * np.abs(Kd).max()
-    pc = BDDC(fe, Ke, Kf, primal, scaling=scaling)
+    pc = BDDC(fe, Ke, Kf, primal, scaling=scaling, coarse=coarse)
     cl = pc.cl
     free_nodes = np.nonzero(fe.node_to_free >= 0)[0]
     gnodes = free_nodes[cl.count[free_nodes] >= 2]
@@ -161,4 +162,23 @@ def test_lagrange_form_equals_change_of_basis(primal, scaling):
         r[gdof] = 1.0
         M_oracle[:, j] = pc.apply(r)[gamma]
     M_basis = _change_of_basis_inverse(fe, pc.subs, cl, primal, scaling == "deluxe", gamma)
+    return Kd, M_oracle, M_basis
+
+
+@pytest.mark.parametrize("primal", ["V", "VE", "VEF", "EF", "VER", "EFR"])
+@pytest.mark.parametrize("scaling", ["counting", "deluxe"])
+def test_lagrange_form_equals_change_of_basis(primal, scaling):
+    Kd, M_oracle, M_basis = _dense_pair(0.0, primal, scaling)
+    assert np.abs(Kd - Kd.T).max() <= 1e-12 * np.abs(Kd).max()
     assert np.abs(M_oracle - M_basis).max() <= 1e-10 * np.abs(M_basis).max()
+
+
+@pytest.mark.parametrize("primal", ["VE", "VEF", "EFR"])
+@pytest.mark.parametrize("scaling", ["counting", "deluxe"])
+def test_nonsymmetric_petrov_coarse_equals_change_of_basis(primal, scaling):
+    Kd, M_petrov, M_basis = _dense_pair(2e3, primal, scaling, coarse="petrov")
+    asym = np.abs(Kd - Kd.T).max() / np.abs(Kd).max()
+    assert asym > 1e-6                      # follower pressure: nonsymmetric
+    assert np.abs(M_petrov - M_basis).max() <= 1e-10 * np.abs(M_basis).max()
+    _, M_galerkin, _ = _dense_pair(2e3, primal, scaling)
+    assert np.abs(M_galerkin - M_basis).max() > 1e-8 * np.abs(M_basis).max()
