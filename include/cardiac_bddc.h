@@ -212,6 +212,13 @@ enum { CBDDC_FP64 = 0, CBDDC_FP32 = 1 };      /* local operator precision */
    step from the local Schur complements (dense, in the local operator
    precision) and applies to the first level of a multilevel method. */
 enum { CBDDC_SCALING_COUNTING = 0, CBDDC_SCALING_DELUXE = 1 };
+/* Coarse space.  GALERKIN: one basis Phi (the minimum-energy extension of
+   the primal constraints for S_i) on both sides, coarse matrix
+   sum Phi_i^T S_i Phi_i.  PETROV: the nonsymmetric BDDC, with a left basis
+   Psi built the same way for S_i^T: coarse matrix sum Psi_i^T S_i Phi_i and
+   coarse right-hand side sum Psi_i^T g_i (equal to GALERKIN for a
+   symmetric tangent).  A multilevel method uses it on every level. */
+enum { CBDDC_COARSE_GALERKIN = 0, CBDDC_COARSE_PETROV = 1 };
 enum { CBDDC_PRIMAL_V = 1, CBDDC_PRIMAL_E = 2, CBDDC_PRIMAL_F = 4, CBDDC_PRIMAL_R = 8 };
 /* CBDDC_PRIMAL_R adds, to every edge (E) or face (F) class, constraints on
    the infinitesimal rotations about the class centroid (the rigid motions,
@@ -248,6 +255,7 @@ typedef struct {
   int scaling;       /* CBDDC_SCALING_COUNTING (0) or CBDDC_SCALING_DELUXE;
                         deluxe allows at most 65535 edge and face classes,
                         of at most 1024 nodes each (CBDDC_EINVAL otherwise) */
+  int coarse;        /* CBDDC_COARSE_GALERKIN (0) or CBDDC_COARSE_PETROV */
 } bddc_options;
 
 typedef struct bddc_ctx bddc_ctx;
@@ -342,6 +350,7 @@ typedef struct {
   int primal2;
   int precision2;
   int scaling;         /* as in bddc_options                                 */
+  int coarse;          /* as in bddc_options                                 */
 } solve_options;
 
 #define CBDDC_MAX_RECORDS 512

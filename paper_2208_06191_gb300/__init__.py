@@ -19,6 +19,7 @@ from . import _build
 __all__ = [
     "build", "load_library", "Problem", "BDDC", "SolveOptions", "CBDDCError",
     "FP64", "FP32", "SCALING_COUNTING", "SCALING_DELUXE", "scaling_code",
+    "COARSE_GALERKIN", "COARSE_PETROV", "coarse_code",
     "PRIMAL_V", "PRIMAL_E", "PRIMAL_F", "PRIMAL_R", "primal_mask",
     "EXPORTED_SYMBOLS",
 ]
@@ -28,6 +29,7 @@ HEX_Q1, HEX_Q2, TET_P1, TET_P2 = 1, 2, 3, 4
 FIBER_SLAB_HELIX, FIBER_NODAL = 1, 2
 FP64, FP32 = 0, 1
 SCALING_COUNTING, SCALING_DELUXE = 0, 1
+COARSE_GALERKIN, COARSE_PETROV = 0, 1
 PRIMAL_V, PRIMAL_E, PRIMAL_F, PRIMAL_R = 1, 2, 4, 8
 MAX_RECORDS = 512
 
@@ -56,6 +58,13 @@ def scaling_code(spec):
     if isinstance(spec, int):
         return spec
     return {"counting": SCALING_COUNTING, "deluxe": SCALING_DELUXE}[spec]
+
+
+def coarse_code(spec):
+    """'galerkin' / 'petrov' (or the code itself) -> CBDDC_COARSE_* code."""
+    if isinstance(spec, int):
+        return spec
+    return {"galerkin": COARSE_GALERKIN, "petrov": COARSE_PETROV}[spec]
 
 
 class CBDDCError(RuntimeError):
@@ -99,7 +108,8 @@ class _Tangent(ctypes.Structure):
 class _BddcOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("primal", ctypes.c_int), ("pivot_tol", ctypes.c_double),
                 ("levels", ctypes.c_int), ("n_parts2", ctypes.c_int), ("part2", _i32p),
-                ("primal2", ctypes.c_int), ("precision2", ctypes.c_int), ("scaling", ctypes.c_int)]
+                ("primal2", ctypes.c_int), ("precision2", ctypes.c_int), ("scaling", ctypes.c_int),
+                ("coarse", ctypes.c_int)]
 
 
 class _BddcInfo(ctypes.Structure):
@@ -123,7 +133,7 @@ class _SolveOptions(ctypes.Structure):
         ("max_gmres", ctypes.c_int), ("newton_rtol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
         ("pivot_tol", ctypes.c_double), ("levels", ctypes.c_int), ("n_parts2", ctypes.c_int),
         ("part2", _i32p), ("primal2", ctypes.c_int), ("precision2", ctypes.c_int),
-        ("scaling", ctypes.c_int),
+        ("scaling", ctypes.c_int), ("coarse", ctypes.c_int),
     ]
 
 
@@ -249,11 +259,13 @@ class SolveOptions:
     """Options of the Newton-GMRES-BDDC solve (see solve_options in the header).
     Multilevel BDDC: levels=3 with part2 (level-2 subdomain of every
     subdomain), n_parts2, primal2 and precision2 (level-2 local operators).
-    scaling: "counting" or "deluxe" (first level)."""
+    scaling: "counting" or "deluxe" (first level); coarse: "galerkin" or
+    "petrov" (left coarse basis from the transposed local problems)."""
 
     def __init__(self, precision=FP64, primal="V", load_steps=4, max_newton=25, max_halvings=6,
                  restart=100, max_gmres=1000, newton_rtol=1e-8, gmres_rtol=1e-8, pivot_tol=1e-13,
-                 levels=2, part2=None, n_parts2=0, primal2="VEF", precision2=FP64, scaling="counting"):
+                 levels=2, part2=None, n_parts2=0, primal2="VEF", precision2=FP64, scaling="counting",
+                 coarse="galerkin"):
         self.precision = precision
         self.primal = primal if isinstance(primal, int) else primal_mask(primal)
         self.load_steps = load_steps
@@ -270,12 +282,13 @@ class SolveOptions:
         self.primal2 = primal2 if isinstance(primal2, int) else primal_mask(primal2)
         self.precision2 = precision2
         self.scaling = scaling_code(scaling)
+        self.coarse = coarse_code(coarse)
 
     def c(self):
         return _SolveOptions(self.precision, self.primal, self.load_steps, self.max_newton,
                              self.max_halvings, self.restart, self.max_gmres, self.newton_rtol,
                              self.gmres_rtol, self.pivot_tol, self.levels, self.n_parts2,
-                             self._part2_ptr, self.primal2, self.precision2, self.scaling)
+                             self._part2_ptr, self.primal2, self.precision2, self.scaling, self.coarse)
 
 
 def _record_dict(r):
@@ -455,14 +468,14 @@ class BDDC:
     """BDDC preconditioner context (bddc_ctx) for a problem."""
 
     def __init__(self, problem, precision=FP64, primal="V", pivot_tol=1e-13, levels=2, part2=None,
-                 n_parts2=0, primal2="VEF", precision2=FP64, scaling="counting"):
+                 n_parts2=0, primal2="VEF", precision2=FP64, scaling="counting", coarse="galerkin"):
         self.problem = problem
         self._h = ctypes.c_void_p()
         self._part2, p2 = _part2_arg(part2)
         self._opt = _BddcOptions(precision, primal if isinstance(primal, int) else primal_mask(primal),
                                  pivot_tol, levels, int(n_parts2), p2,
                                  primal2 if isinstance(primal2, int) else primal_mask(primal2),
-                                 precision2, scaling_code(scaling))
+                                 precision2, scaling_code(scaling), coarse_code(coarse))
 
     @classmethod
     def _wrap(cls, h, problem):

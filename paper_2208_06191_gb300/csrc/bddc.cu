@@ -357,6 +357,29 @@ __global__ void phi_vertex_kernel(const int* __restrict__ nG, const int* __restr
   }
 }
 
+// Left coarse basis of the Petrov coarse space, apart from the vertex
+// columns of the r rows (a GEMM writes -(S_vr T)^T there):
+// Psi[0:nr, nv:nc] = Wf[:, 0:nr]^T = (G^-1 C M_rr^-1)^T, the constraint
+// columns of the constrained problem for S^T; Psi[nr:nG, :] = [I 0].
+template <typename T>
+__global__ void psi_fill_kernel(const int* __restrict__ nG, const int* __restrict__ nr,
+                                const int* __restrict__ nv, const int* __restrict__ nc,
+                                const int64_t* __restrict__ offZ, const int* __restrict__ ldS,
+                                const int64_t* __restrict__ offPhi, const int* __restrict__ ldPhi,
+                                const T* __restrict__ Wf, T* __restrict__ Psi) {
+  const int s = blockIdx.y;
+  const int ncs = nc[s], ng = nG[s], nrs = nr[s], nvs = nv[s];
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ng * ncs) return;
+  const int row = (int)(t / ncs), c = (int)(t % ncs);
+  T* dst = Psi + offPhi[s] + (int64_t)row * ldPhi[s] + c;
+  if (row < nrs) {
+    if (c >= nvs) *dst = Wf[offZ[s] + (int64_t)(c - nvs) * ldS[s] + row];
+  } else {
+    *dst = (c == row - nrs) ? T(1) : T(0);
+  }
+}
+
 __global__ void coarse_assemble_kernel_f(const int* __restrict__ key, const int* __restrict__ ptr,
                                          const int* __restrict__ src, int64_t n,
                                          const float* __restrict__ Kc, double* __restrict__ S) {
@@ -786,6 +809,9 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
            "bad scaling");
   C->scaling = opt->scaling;
   const bool deluxe = opt->scaling == CBDDC_SCALING_DELUXE;
+  CB_CHECK(opt->coarse == CBDDC_COARSE_GALERKIN || opt->coarse == CBDDC_COARSE_PETROV, CBDDC_EINVAL,
+           "bad coarse space");
+  C->coarse = opt->coarse;
   // deluxe classes: every edge and face (vertex nodes keep counting)
   std::vector<const std::vector<int>*> dcls;
   std::vector<int> node_dcls(nn, -1);
@@ -1160,6 +1186,19 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   C->gl_PhiA.set(gPA, es);
   C->gl_SPhi.set(gSP, es);
   C->gl_Kc.set(gKc, es, true);
+  if (C->coarse == CBDDC_COARSE_PETROV) {
+    // Psi[0:nr, 0:nv] = -T^T S_vr^T (T: constrained inverse in Sw's rr
+    // block; S_vr: vertex rows, r columns of the Schur complement in Aloc)
+    std::vector<GemmProb> gPV;
+    for (int s = 0; s < nsub; ++s) {
+      const int cI = (int)round_up(C->nI[s], 4);
+      const int64_t aGG = C->offA[s] + (int64_t)C->nI[s] * C->ldA[s] + cI;
+      gPV.push_back(GemmProb{C->nr[s], C->nv[s], C->nr[s], C->ldS[s], C->ldA[s], C->ldPhi[s], C->offS[s],
+                             aGG + (int64_t)C->nr[s] * C->ldA[s], C->offPhi[s]});
+    }
+    C->gl_PsiV.set(gPV, es, true);
+    C->Psi.alloc(sized(C->offPhi[nsub]));
+  }
 
   C->gprim_h = gprim;
   // coarse matrix entries (two-level: dense FP64 coarse inverse)
@@ -1279,6 +1318,7 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     o2.primal = C->primal2;
     o2.pivot_tol = C->pivot_tol;
     o2.levels = 2;
+    o2.coarse = C->coarse;
     C->next.reset(new bddc_ctx);
     bddc_create(C->coarse_prob.get(), &o2, C->next.get());
     fl += C->next->setup_flops;
@@ -1402,10 +1442,21 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
         Sw, Phi);
     CB_LAUNCH();
   }
-  // 6. local coarse matrices Phi^T S Phi and the FP64 coarse inverse
+  // 5b. Petrov coarse space: the left basis Psi
+  T* Psi = reinterpret_cast<T*>(C->Psi.p);
+  if (C->coarse == CBDDC_COARSE_PETROV && C->maxC > 0) {
+    psi_fill_kernel<T><<<dim3(cdiv((int64_t)C->maxG * C->maxC, 256), nsub), 256, 0, s>>>(
+        C->d_nG.p, C->d_nr.p, C->d_nv.p, C->d_nc.p, C->d_offZ.p, C->d_ldS.p, C->d_offPhi.p, C->d_ldPhi.p,
+        Wf, Psi);
+    CB_LAUNCH();
+    launch_list<T, true, true>(C->gl_PsiV, Sw, Aloc, Psi, T(-1), T(0), s);
+  }
+  // 6. local coarse matrices Psi^T S Phi (Psi = Phi: Galerkin) and the FP64
+  //    coarse inverse
   if (C->n_pi > 0) {
     launch_list<T, false, false>(C->gl_SPhi, Aloc, Phi, SPhi, T(1), T(0), s);
-    launch_list<T, true, false>(C->gl_Kc, Phi, SPhi, Kc, T(1), T(0), s);
+    launch_list<T, true, false>(C->gl_Kc, C->coarse == CBDDC_COARSE_PETROV ? Psi : Phi, SPhi, Kc, T(1),
+                                T(0), s);
     if (C->next) {
       // multilevel: the local coarse matrices become the element matrices of
       // the coarse problem, which the level-2 BDDC sets up in FP64
@@ -1450,6 +1501,7 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
   const T* Aloc = reinterpret_cast<const T*>(C->Aloc.p);
   const T* Sw = reinterpret_cast<const T*>(C->Sw.p);
   const T* Phi = reinterpret_cast<const T*>(C->Phi.p);
+  const T* Psi = reinterpret_cast<const T*>(C->Psi.p);
   const size_t smI = (size_t)round_up(std::max(C->maxI, 4), 4) * sizeof(T);
   const size_t smD = (size_t)round_up(std::max(C->maxDn, 4), 4) * sizeof(T);
   gather_kernel<<<cdiv(std::max<int64_t>(C->totI, 1), 256), 256, 0, s>>>(C->gdofI.p, C->totI, r, w.xI);
@@ -1488,7 +1540,8 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
       const int nch = (int)cdiv(C->maxG, PHIT_ROWS);
       if (C->n_itP > 0) {
         apply_phit_kernel<T><<<C->n_itP, 256, 0, s>>>(C->itP.p, C->d_nG.p, C->d_nc.p, C->d_offPhi.p,
-                                                            C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p, Phi,
+                                                            C->d_ldPhi.p, C->d_offGam.p, C->d_offC.p,
+                                                            C->coarse == CBDDC_COARSE_PETROV ? Psi : Phi,
                                                             w.gl, w.cl, nch);
         CB_LAUNCH();
       }
@@ -1621,6 +1674,6 @@ int64_t bddc_ctx::device_bytes() const {
                    Sc.bytes() + ScX.bytes() + ScY.bytes() + ScP.bytes() + u0.bytes() + hG.bytes() +
                    gI.bytes() + wG.bytes() + cl.bytes() + rc.bytes() + uc.bytes() + yG.bytes() + gl.bytes() + xI.bytes() + zl.bytes() +
                    Dsb.bytes() + Ddb.bytes() + Deb.bytes() + Dsh.bytes() + DX.bytes() + DY.bytes() + DP.bytes() +
-                   yD.bytes()) +
+                   yD.bytes() + Psi.bytes()) +
          (next ? next->device_bytes() + coarse_prob->device_bytes() : 0);
 }

@@ -53,6 +53,11 @@ struct bddc_ctx {
   // block of s's Schur complement), D_b = Shat_K^-1 S_b (Shat_K = sum of
   // the class's S_b, inverted in place) and E_b = D_b^T share the offsets
   int scaling = CBDDC_SCALING_COUNTING;
+  // Petrov coarse space: left basis Psi (layout of Phi), its vertex columns
+  // -(S_vr T)^T by one grouped GEMM per setup
+  int coarse = CBDDC_COARSE_GALERKIN;
+  cbddc::DVec<unsigned char> Psi;
+  cbddc::GemmList gl_PsiV;
   int n_dlx = 0, n_dcls = 0, maxDn = 0, stepsd = 0;
   cbddc::DVec<int> dlx_n, dlx_sub, dlx_ld, dlx_pos, dcls_ptr, dcls_blk;
   cbddc::DVec<int64_t> dlx_poff, dlx_off, dcls_off;

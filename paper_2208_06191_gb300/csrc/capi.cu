@@ -113,6 +113,7 @@ static void ensure_ctx(fem_problem* P, const solve_options* opt, bddc_ctx** C) {
   bo.primal2 = opt->primal2;
   bo.precision2 = opt->precision2;
   bo.scaling = opt->scaling;
+  bo.coarse = opt->coarse;
   bddc_ctx* c = new bddc_ctx;
   try {
     bddc_create(P, &bo, c);
@@ -318,7 +319,8 @@ int bddc_setup(fem_problem* P, const fem_tangent* K, const bddc_options* opt, bd
     } else {
       bddc_ctx* c = *inout;
       CB_CHECK(c->P == P && c->precision == opt->precision && c->primal == opt->primal &&
-                   c->levels == (opt->levels >= 3 ? 3 : 2) && c->scaling == opt->scaling,
+                   c->levels == (opt->levels >= 3 ? 3 : 2) && c->scaling == opt->scaling &&
+                   c->coarse == opt->coarse,
                CBDDC_EINVAL, "context was created for another problem or options");
     }
     bddc_run_setup(*inout, s);
