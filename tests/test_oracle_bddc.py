@@ -189,3 +189,48 @@ def test_multilevel_symmetric_case():
     ev = np.linalg.eigvals(Minv @ K.toarray())
     assert np.abs(ev.imag).max() <= 1e-8 * np.abs(ev).max()
     assert ev.real.min() >= 1.0 - 1e-9
+
+
+def _pcg(matvec, b, precond, tol, maxiter=500):
+    """Textbook preconditioned conjugate gradients; returns the true relative
+    residual after every iteration."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = precond(r)
+    p = z.copy()
+    rz = r @ z
+    hist = []
+    for _ in range(maxiter):
+        Ap = matvec(p)
+        alpha = rz / (p @ Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        hist.append(np.linalg.norm(b - matvec(x)) / np.linalg.norm(b))
+        if hist[-1] <= tol:
+            break
+        z = precond(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, hist
+
+
+@pytest.mark.parametrize("primal", ["V", "VE"])
+def test_symmetric_case_pcg_and_gmres_agree(primal):
+    # SPD tangent (no follower pressure) and symmetric BDDC: right-
+    # preconditioned GMRES minimises ||b - A x_k|| over the same affine
+    # Krylov space PCG's x_k lies in, so GMRES never needs more iterations
+    # than PCG for the same residual tolerance; PCG needs only a few more.
+    prob = slab_problem(6, 6, 4, parts=(2, 2, 2), jitter=0.1, pressure=0.0, gamma=3e4)
+    fe, K, Ke, Kf = _setup(prob, 1e-3)
+    pc = BDDC(fe, Ke, Kf, primal)
+    b = np.random.default_rng(9).standard_normal(fe.n_free)
+    x_g, its_g, hist_g = gmres(lambda v: K @ v, b, pc.apply, tol=1e-9)
+    x_c, hist_c = _pcg(lambda v: K @ v, b, pc.apply, tol=1e-9)
+    its_c = len(hist_c)
+    assert its_g <= its_c <= its_g + 3
+    # after every step k, GMRES's residual (hist_g[k]; hist_g[0] = 1) is no
+    # larger than PCG's (hist_c[k - 1])
+    k = min(its_g, its_c)
+    assert np.all(np.array(hist_g[1:k + 1]) <= np.array(hist_c[:k]) * (1 + 1e-6) + 1e-14)
+    assert np.linalg.norm(x_g - x_c) <= 1e-7 * np.linalg.norm(x_c)
