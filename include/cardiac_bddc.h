@@ -1,15 +1,19 @@
 /*
  * cardiac_bddc.h -- C ABI of the GB300 Newton-GMRES-BDDC tangent solver.
  *
- * The library solves the quasi-static cardiac mechanics problem of
- * Barnafi, Pavarino & Scacchi, "A comparative study of scalable multilevel
- * preconditioners for cardiac mechanics" (arXiv 2208.06191):
+ * The library solves the cardiac mechanics problem of Barnafi, Pavarino &
+ * Scacchi, "A comparative study of scalable multilevel preconditioners for
+ * cardiac mechanics" (arXiv 2208.06191):
  *   - Section 2: Guccione passive law, active stress gamma (Ff)(x)f/|Ff|,
  *     follower endocardial pressure -p J F^{-T} N (Eq. bc endo), weak form
- *     (Eq. mechanics time discrete, without the inertia term), Newton on
- *     the tangent problem (Eq. tangent problem);
- *   - Section 3.2: two-level BDDC with vertex / edge-average / face-average
- *     primal constraints and counting scaling, as preconditioner of GMRES.
+ *     (Eq. mechanics time discrete; the inertia term and the generalized
+ *     Robin condition through fem_set_time_state), Newton on the tangent
+ *     problem (Eq. tangent problem);
+ *   - Section 3.2: two-level and multilevel BDDC with vertex /
+ *     edge-average / face-average primal constraints, counting or deluxe
+ *     scaling, as preconditioner of GMRES; Section 4: rigid motions as
+ *     primal constraints; a Petrov (left and right basis) coarse space for
+ *     the nonsymmetric tangent.
  *
  * Conventions shared by every call:
  *   - Return value: 0 (CBDDC_OK) or one of the CBDDC_E* codes below; the
