@@ -49,3 +49,23 @@ def test_reference_arm_is_silent_off_rank_zero(capsys):
         steps, warmup, gpus, oracle_budget_s = 1, 0, 2, 1.0
     bench.run_reference(Args(), 2, 1)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_the_contract_line(capsys):
+    # one real oracle Newton step of the default workload (about 20 s)
+    import json
+
+    import bench
+
+    class Args:
+        steps, warmup, gpus, oracle_budget_s = 1, 3, 1, 300.0
+    bench.run_reference(Args(), 1, 0)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is False and d["steps"] == 1 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert 10 <= d["config"]["gmres_its"][0] <= 200
