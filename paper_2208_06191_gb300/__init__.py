@@ -296,7 +296,29 @@ def _record_dict(r):
 
 
 class Problem:
-    """A discretised problem on the current CUDA device (fem_problem)."""
+    """A discretised problem on the current CUDA device (fem_problem).
+
+    ``prob`` is a dict (the generators in ``workloads`` build them):
+
+    * ``elem_type``: "Q1", "Q2" (hexahedra; local node a + (k+1)(b +
+      (k+1)c) at reference position (a, b, c)/k) or "P1", "P2" (tetrahedra:
+      4 corners, then the mid-nodes of edges 01, 12, 02, 03, 13, 23);
+    * ``coords`` (n_nodes, 3) reference coordinates; ``elems`` (n_el, n_en)
+      node ids; ``elem_part`` (n_el,) subdomain of every element and
+      ``n_parts``;
+    * ``dirichlet_nodes``: clamped nodes (all three components);
+    * ``pressure_faces`` (n, 2): (element, local face) pairs carrying the
+      follower pressure ``pressure`` (Pa, scaled by the load factor);
+    * ``fibers``: {"kind": "slab_helix", "z0", "z1", "alpha0", "alpha1"}
+      (angle rising linearly in z, degrees) or {"kind": "nodal", "f", "n"}
+      (fibre and sheet-normal directions per node, (n_nodes, 3) each);
+    * ``material``: Guccione constants C, bff, bss, bnn, bfs, bfn, bsn and
+      the bulk modulus B (Pa); ``gamma``: active tension (Pa, scaled by the
+      load factor);
+    * optional, for the time-dependent model: ``rho`` (density),
+      ``robin_faces`` (n, 3) rows (element, local face, parameter set 0/1)
+      and ``robin``, two dicts with k_perp, k_par, c_perp, c_par.
+    """
 
     def __init__(self, prob):
         lib = load_library()
