@@ -296,8 +296,7 @@ CBDDC_API void bddc_destroy(bddc_ctx* C);
    memory while they run: code that is not allowed to call cudaMalloc
    (which synchronises the device and may fail or stall once another
    allocator has reserved the memory), and setups whose memory was
-   budgeted up front.  The paper has no counterpart; it is a deployment
-   variant of the apply of Section 3.2.
+   budgeted up front.  The paper has no counterpart.
    The per-apply work vectors live in one static device array of 4 MiB
    (524288 doubles), held by every device that loads the library until the
    process exits.  A context whose work vectors need more than that is
@@ -317,7 +316,7 @@ CBDDC_API int bddc_get_info(const bddc_ctx* C, bddc_info* info);
 /* ---------------------------------------------------- GMRES and Newton */
 
 typedef struct {
-  int restart;         /* Krylov dimension per cycle (default 100)          */
+  int restart;         /* Krylov dimension per cycle (default 100, <= 1023) */
   int max_iters;       /* total iteration cap                               */
   double rtol;         /* stop when ||b - K x|| <= rtol ||b||               */
 } gmres_options;
@@ -343,7 +342,7 @@ typedef struct {
   int load_steps;      /* lambda_k = k / load_steps                          */
   int max_newton;      /* Newton iterations per load step                    */
   int max_halvings;    /* load-increment halvings before giving up           */
-  int restart;         /* GMRES restart                                      */
+  int restart;         /* GMRES restart (default 100, at most 1023)          */
   int max_gmres;       /* GMRES iteration cap per Newton step                */
   double newton_rtol;  /* ||F(d)|| <= newton_rtol ||F(d^{n,0})||             */
   double gmres_rtol;   /* relative residual of each tangent solve            */
@@ -365,6 +364,7 @@ typedef struct {
   double res;          /* ||F(d)|| before the step                           */
   double res0;         /* ||F(d^{n,0})|| of the load step                    */
   float ms_assemble, ms_setup, ms_gmres, ms_total; /* CUDA-event times       */
+  double gmres_relres; /* ||b - K delta|| / ||b|| of the tangent solve at exit */
 } newton_record;
 
 typedef struct {
@@ -409,23 +409,51 @@ CBDDC_API uint64_t cbddc_kernel_launches(void);
 /* Kernel classes that the launch timer can follow. */
 enum {
   CBDDC_TIMER_OFF = 0,
-  CBDDC_TIMER_SWEEP_GEMM = 1, /* trailing updates of the Gauss-Jordan sweeps */
+  CBDDC_TIMER_SWEEP_GEMM = 1, /* FP32 setup GEMMs: trailing updates of the
+                                 Gauss-Jordan sweeps and the E, S, constraint
+                                 and coarse-basis products (tensor cores)     */
   CBDDC_TIMER_ELEMENT = 2,    /* element residual/tangent kernel              */
   CBDDC_TIMER_APPLY = 3,      /* one whole BDDC apply (all its launches)      */
   CBDDC_TIMER_SPMV = 4,       /* BSR SpMV                                     */
-  CBDDC_TIMER_ORTH = 5        /* one GMRES orthogonalisation (CGS2, Givens,
+  CBDDC_TIMER_ORTH = 5,       /* one GMRES orthogonalisation (CGS2, Givens,
                                  normalisation)                               */
+  CBDDC_TIMER_SETUP = 6,      /* one whole BDDC setup (all levels)            */
+  CBDDC_TIMER_LEVEL2_SETUP = 7, /* setup of the level-2 BDDC (multilevel)     */
+  CBDDC_TIMER_LEVEL2_APPLY = 8, /* apply of the level-2 BDDC (multilevel)     */
+  CBDDC_TIMER_COARSE_SETUP = 9, /* coarsest level: FP64 coarse assembly and
+                                   dense inverse                              */
+  CBDDC_TIMER_COARSE_APPLY = 10, /* coarsest level: dense FP64 coarse solve   */
+  CBDDC_TIMER_SETUP_GEMM_F64 = 11 /* FP64 setup GEMMs (FP64 local operators
+                                     and the coarse inverse)                  */
 };
 
-/* Starts recording CUDA events around every launch of the given class, on
-   the stream the launch uses (at most 65536 launches are recorded).  Each
+/* Selects the kernel of the FP32 setup GEMMs for every BDDC setup run
+   afterwards in this process: 1 (the default) = tcgen05 tensor cores with
+   the three-term TF32 split (FP32-level accuracy), 0 = FP32 CUDA-core
+   kernels.  Returns the previous setting.  Host-side state, not thread
+   safe; a diagnostic and comparison switch, the results agree to FP32
+   rounding. */
+CBDDC_API int cbddc_set_tensor_cores(int enable);
+
+/* Starts recording CUDA events around every launch of the given class (and
+   stops recording every other class), on the stream the launch uses (at
+   most 32768 launches per class are recorded).  Each
    recorded launch also adds its algorithmic flops and bytes.  Host-side
    state, not thread safe. */
 CBDDC_API int cbddc_timer_start(int kernel_class);
 
-/* Stops recording, waits for the recorded events and returns the summed
-   device time (ms), the number of launches and their algorithmic flops and
-   bytes. */
+/* Records one more kernel class alongside those already recorded (its
+   totals start at zero). */
+CBDDC_API int cbddc_timer_enable(int kernel_class);
+
+/* Waits for the events recorded so far for one enabled class and returns
+   its summed device time (ms), launches, algorithmic flops and bytes. */
+CBDDC_API int cbddc_timer_result(int kernel_class, double* total_ms, int64_t* launches, double* flops,
+                                 double* bytes);
+
+/* Stops recording every class, waits for the recorded events and returns
+   the totals of the class given to cbddc_timer_start: summed device time
+   (ms), the number of launches and their algorithmic flops and bytes. */
 CBDDC_API int cbddc_timer_stop(double* total_ms, int64_t* launches, double* flops, double* bytes);
 
 /* Message for the last non-zero status returned on this thread. */

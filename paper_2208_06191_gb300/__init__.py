@@ -39,9 +39,11 @@ EXPORTED_SYMBOLS = [
     "bddc_setup", "bddc_apply", "bddc_apply_noalloc", "bddc_destroy", "bddc_get_info",
     "gmres_solve", "newton_step", "newton_step_host", "newton_gmres_solve",
     "cbddc_kernel_launches", "cbddc_timer_start", "cbddc_timer_stop",
-    "cbddc_last_error",
+    "cbddc_set_tensor_cores", "cbddc_timer_enable", "cbddc_timer_result", "cbddc_last_error",
 ]
-TIMER_OFF, TIMER_SWEEP_GEMM, TIMER_ELEMENT, TIMER_APPLY, TIMER_SPMV, TIMER_ORTH = range(6)
+(TIMER_OFF, TIMER_SWEEP_GEMM, TIMER_ELEMENT, TIMER_APPLY, TIMER_SPMV, TIMER_ORTH, TIMER_SETUP,
+ TIMER_LEVEL2_SETUP, TIMER_LEVEL2_APPLY, TIMER_COARSE_SETUP, TIMER_COARSE_APPLY,
+ TIMER_SETUP_GEMM_F64) = range(12)
 
 
 def primal_mask(spec):
@@ -142,6 +144,7 @@ class _Record(ctypes.Structure):
         ("load", ctypes.c_double), ("newton", ctypes.c_int), ("gmres_its", ctypes.c_int),
         ("res", ctypes.c_double), ("res0", ctypes.c_double), ("ms_assemble", ctypes.c_float),
         ("ms_setup", ctypes.c_float), ("ms_gmres", ctypes.c_float), ("ms_total", ctypes.c_float),
+        ("gmres_relres", ctypes.c_double),
     ]
 
 
@@ -196,6 +199,10 @@ def load_library():
         "newton_gmres_solve": (c_int, [vp, ctypes.POINTER(_SolveOptions), vp, ctypes.POINTER(_Report), vp]),
         "cbddc_last_error": (ctypes.c_char_p, []),
         "cbddc_kernel_launches": (ctypes.c_uint64, []),
+        "cbddc_set_tensor_cores": (c_int, [c_int]),
+        "cbddc_timer_enable": (c_int, [c_int]),
+        "cbddc_timer_result": (c_int, [c_int, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
         "cbddc_timer_start": (c_int, [c_int]),
         "cbddc_timer_stop": (c_int, [ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
@@ -206,6 +213,12 @@ def load_library():
         f.argtypes = args
     _LIB = lib
     return lib
+
+
+def set_tensor_cores(enable):
+    """FP32 setup GEMMs on the tcgen05 tensor cores (True, the default) or
+    on the FP32 CUDA cores (False); returns the previous setting."""
+    return bool(load_library().cbddc_set_tensor_cores(1 if enable else 0))
 
 
 def kernel_launches():
@@ -224,6 +237,20 @@ def timer_stop():
     fl, by = ctypes.c_double(), ctypes.c_double()
     _check(load_library().cbddc_timer_stop(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl),
                                            ctypes.byref(by)))
+    return {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
+
+
+def timer_enable(kernel_class):
+    """Also record the launches of another kernel class."""
+    _check(load_library().cbddc_timer_enable(int(kernel_class)))
+
+
+def timer_result(kernel_class):
+    """dict(ms, launches, flops, bytes) of one recorded class so far."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    fl, by = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().cbddc_timer_result(int(kernel_class), ctypes.byref(ms), ctypes.byref(n),
+                                             ctypes.byref(fl), ctypes.byref(by)))
     return {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
 
 

@@ -1330,6 +1330,21 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   C->setup_flops = fl;
   C->local_bytes = lb;
   C->apply_flops = (double)lb / (double)C->esize * 2.0;
+  // FP32 contexts: one scratch buffer for the split operands of the
+  // tensor-core GEMMs, shared by every list (they run one after another on
+  // the setup stream)
+  if (C->esize == 4) {
+    std::vector<GemmList*> lists{&C->gl_E, &C->gl_S, &C->gl_W, &C->gl_T, &C->gl_PhiA, &C->gl_SPhi, &C->gl_Kc,
+                                 &C->gl_PsiV, &C->gl_dlx};
+    for (auto* v : {&C->gl_sw1, &C->gl_sw2, &C->gl_swg, &C->gl_swd})
+      for (auto& g : *v) lists.push_back(&g);
+    int64_t need = 0;
+    for (auto* g : lists) need = std::max(need, g->tc_floats());
+    if (need > 0) {
+      C->tc_scratch.alloc((size_t)need);
+      for (auto* g : lists) g->bind_tc(C->tc_scratch.p, P->status.p);
+    }
+  }
 }
 
 // ------------------------------------------------------------------- setup
@@ -1464,11 +1479,14 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
       kc_to_blocks_kernel<T><<<dim3(cdiv((int64_t)C->maxC * C->maxC, 256), nsub), 256, 0, s>>>(
           C->d_nc.p, C->d_offKc.p, C->d_ldPhi.p, C->d_cbase.p, Kc, CP->contrib.p);
       CB_LAUNCH();
+      timer_begin(CBDDC_TIMER_LEVEL2_SETUP, s);
       bddc_run_setup(C->next.get(), s);
+      timer_end(CBDDC_TIMER_LEVEL2_SETUP, s, C->next->setup_flops, 0.0);
       or_status_kernel<<<1, 1, 0, s>>>(CP->status.p, status);
       CB_LAUNCH();
       return;
     }
+    timer_begin(CBDDC_TIMER_COARSE_SETUP, s);
     CB_CUDA(cudaMemsetAsync(C->Sc.p, 0, C->Sc.bytes(), s));
     if (sizeof(T) == 4)
       coarse_assemble_kernel_f<<<cdiv(C->n_ce, 256), 256, 0, s>>>(
@@ -1479,12 +1497,15 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
     CB_LAUNCH();
     run_sweep<double>(C->swc, 1, C->gl_swc, C->n_pi, C->n_pi, C->Sc.p, C->ScX.p, C->ScY.p, C->ScP.p,
                       status, tol, s);
+    timer_end(CBDDC_TIMER_COARSE_SETUP, s, 2.0 * (double)C->n_pi * C->n_pi * C->n_pi, 0.0);
   }
 }
 
 void bddc_run_setup(bddc_ctx* C, cudaStream_t s) {
+  timer_begin(CBDDC_TIMER_SETUP, s);
   if (C->precision == CBDDC_FP32) setup_impl<float>(C, s);
   else setup_impl<double>(C, s);
+  timer_end(CBDDC_TIMER_SETUP, s, C->setup_flops, 0.0);
 }
 
 // ------------------------------------------------------------------- apply
@@ -1493,6 +1514,8 @@ namespace {
 struct ApplyWork {
   double *u0, *hG, *gI, *gl, *wG, *cl, *rc, *uc, *yG, *xI, *zl, *yD;
 };
+
+void apply_untimed(bddc_ctx* C, const double* r, double* z, cudaStream_t s);
 
 // z = M^-1 r with caller-chosen work vectors (the context's own, or the
 // static array of bddc_apply_noalloc).
@@ -1549,11 +1572,18 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
                                                            C->cnch.p, w.rc);
       CB_LAUNCH();
       if (C->next) {
-        // the level-2 context uses its own work vectors, allocated at setup
-        bddc_run_apply(C->next.get(), w.rc, w.uc, s);
+        // the level-2 context uses its own work vectors, allocated at setup;
+        // its apply is not timed on its own (an enclosing bddc_run_apply
+        // times the whole recursion, and bddc_apply_noalloc times nothing)
+        timer_begin(CBDDC_TIMER_LEVEL2_APPLY, s);
+        apply_untimed(C->next.get(), w.rc, w.uc, s);
+        timer_end(CBDDC_TIMER_LEVEL2_APPLY, s, C->next->apply_flops, (double)C->next->local_bytes);
       } else {
+        timer_begin(CBDDC_TIMER_COARSE_APPLY, s);
         dense_gemv_kernel<<<cdiv((int64_t)C->n_pi * 32, 256), 256, 0, s>>>(C->Sc.p, C->n_pi, w.rc, w.uc);
         CB_LAUNCH();
+        timer_end(CBDDC_TIMER_COARSE_APPLY, s, 2.0 * (double)C->n_pi * C->n_pi,
+                  8.0 * (double)C->n_pi * C->n_pi);
       }
     }
     if (C->n_itR > 0) {
@@ -1591,12 +1621,17 @@ void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
   apply_with_work<T>(C, r, z, w, s);
 }
 
+// The apply with the context's own work vectors, outside the kernel timer.
+void apply_untimed(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
+  if (C->precision == CBDDC_FP32) apply_impl<float>(C, r, z, s);
+  else apply_impl<double>(C, r, z, s);
+}
+
 }  // namespace
 
 void bddc_run_apply(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
   timer_begin(CBDDC_TIMER_APPLY, s);
-  if (C->precision == CBDDC_FP32) apply_impl<float>(C, r, z, s);
-  else apply_impl<double>(C, r, z, s);
+  apply_untimed(C, r, z, s);
   timer_end(CBDDC_TIMER_APPLY, s, C->apply_flops, (double)C->local_bytes);
 }
 

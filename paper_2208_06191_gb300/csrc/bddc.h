@@ -27,6 +27,7 @@ struct bddc_ctx {
   cbddc::DVec<int> perm;
   // local operators (element type float or double, raw storage)
   cbddc::DVec<unsigned char> Aloc, Sw, Phi, Y, Zf, Wf, G, SPhi, Kc, Xp, Yp, Pd, Et;
+  cbddc::DVec<float> tc_scratch;            // split operands of the tensor-core GEMMs (FP32)
   // apply maps
   cbddc::DVec<int> gdofI, gdofG, gam_if, if_dof, if_ptr, if_src;
   cbddc::DVec<double> Dg;

@@ -19,48 +19,82 @@ void set_last_error(const std::string& msg) { g_last_error = msg; }
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-// Launch timer: event pairs recorded on the launching stream.
+static std::atomic<bool> g_tensor_cores{true};
+bool tensor_cores_enabled() { return g_tensor_cores.load(std::memory_order_relaxed); }
+
+// Launch timer: event pairs recorded on the launching stream, one pool per
+// kernel class; several classes can be recorded at the same time.
 namespace {
-struct Timer {
-  int kernel_class = 0;
+constexpr int kTimerClasses = 16;
+struct ClassTimer {
+  bool on = false;
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
-  int depth = 0;      // nesting of begin/end of the timed class (multilevel apply)
+  int depth = 0;      // nesting of begin/end of this class (multilevel recursion)
   bool open = false;  // the outermost begin recorded an event
   int64_t launches = 0;
   double flops = 0.0, bytes = 0.0;
   static constexpr size_t kMax = 65536;
-} g_timer;
+  void reset() {
+    used = 0;
+    depth = 0;
+    open = false;
+    launches = 0;
+    flops = bytes = 0.0;
+  }
+};
+ClassTimer g_timers[kTimerClasses];
+int g_timer_primary = 0;  // the class passed to cbddc_timer_start
 }  // namespace
 
-bool timer_active(int kernel_class) { return g_timer.kernel_class == kernel_class && kernel_class != 0; }
+bool timer_active(int kernel_class) {
+  return kernel_class > 0 && kernel_class < kTimerClasses && g_timers[kernel_class].on;
+}
 
-// Only the outermost begin/end pair of the timed class is recorded: the
-// multilevel apply runs the level-2 apply inside the level-1 one, and its
-// work is already counted in the outer call's flops and bytes.
+// Only the outermost begin/end pair of a class is recorded: the multilevel
+// apply runs the level-2 apply inside the level-1 one, and its work is
+// already counted in the outer call's flops and bytes.
 void timer_begin(int kernel_class, cudaStream_t s) {
   if (!timer_active(kernel_class)) return;
-  if (g_timer.depth++ > 0) return;
-  g_timer.open = false;
-  if (g_timer.used + 2 > Timer::kMax) return;
-  while (g_timer.pool.size() < g_timer.used + 2) {
+  ClassTimer& t = g_timers[kernel_class];
+  if (t.depth++ > 0) return;
+  t.open = false;
+  if (t.used + 2 > ClassTimer::kMax) return;
+  while (t.pool.size() < t.used + 2) {
     cudaEvent_t e;
     CB_CUDA(cudaEventCreate(&e));
-    g_timer.pool.push_back(e);
+    t.pool.push_back(e);
   }
-  CB_CUDA(cudaEventRecord(g_timer.pool[g_timer.used], s));
-  g_timer.open = true;
+  CB_CUDA(cudaEventRecord(t.pool[t.used], s));
+  t.open = true;
 }
 
 void timer_end(int kernel_class, cudaStream_t s, double flops, double bytes) {
-  if (!timer_active(kernel_class) || g_timer.depth == 0) return;
-  if (--g_timer.depth > 0 || !g_timer.open) return;
-  CB_CUDA(cudaEventRecord(g_timer.pool[g_timer.used + 1], s));
-  g_timer.open = false;
-  g_timer.used += 2;
-  g_timer.launches += 1;
-  g_timer.flops += flops;
-  g_timer.bytes += bytes;
+  if (!timer_active(kernel_class)) return;
+  ClassTimer& t = g_timers[kernel_class];
+  if (t.depth == 0) return;
+  if (--t.depth > 0 || !t.open) return;
+  CB_CUDA(cudaEventRecord(t.pool[t.used + 1], s));
+  t.open = false;
+  t.used += 2;
+  t.launches += 1;
+  t.flops += flops;
+  t.bytes += bytes;
+}
+
+static void timer_totals(int kernel_class, double* total_ms, int64_t* launches, double* flops, double* bytes) {
+  const ClassTimer& t = g_timers[kernel_class];
+  double ms = 0.0;
+  for (size_t i = 0; i + 1 < t.used; i += 2) {
+    CB_CUDA(cudaEventSynchronize(t.pool[i + 1]));
+    float v = 0.f;
+    CB_CUDA(cudaEventElapsedTime(&v, t.pool[i], t.pool[i + 1]));
+    ms += v;
+  }
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = t.launches;
+  if (flops) *flops = t.flops;
+  if (bytes) *bytes = t.bytes;
 }
 
 template <typename F>
@@ -167,6 +201,7 @@ static int newton_step_impl(fem_problem* P, bddc_ctx** Cp, const solve_options* 
   bddc_run_setup(C, s);
   CB_CUDA(cudaEventRecord(ev.e[3], s));
   const int st2 = take_status(P, s);
+  CB_CHECK(!(st2 & DEV_TIMEOUT), CBDDC_ETIMEOUT, "a tensor-core setup kernel timed out on a device wait");
   CB_CHECK(!(st2 & DEV_PIVOT), CBDDC_EPIVOT, "tiny pivot in a local factorisation");
   axpby(-1.0, C->nw_r.p, 0.0, C->nw_r.p, C->nw_b.p, n, s);
   int its = 0;
@@ -185,6 +220,7 @@ static int newton_step_impl(fem_problem* P, bddc_ctx** Cp, const solve_options* 
     rec->ms_setup = ev.ms(2, 3);
     rec->ms_gmres = ev.ms(3, 4);
     rec->ms_total = ev.ms(0, 4);
+    rec->gmres_relres = rel;
   }
   return gst;
 }
@@ -325,6 +361,7 @@ int bddc_setup(fem_problem* P, const fem_tangent* K, const bddc_options* opt, bd
     }
     bddc_run_setup(*inout, s);
     const int st = take_status(P, s);
+    CB_CHECK(!(st & DEV_TIMEOUT), CBDDC_ETIMEOUT, "a tensor-core setup kernel timed out on a device wait");
     CB_CHECK(!(st & DEV_PIVOT), CBDDC_EPIVOT, "tiny pivot in a local factorisation");
   });
 }
@@ -487,35 +524,56 @@ const char* cbddc_last_error(void) { return g_last_error.c_str(); }
 
 uint64_t cbddc_kernel_launches(void) { return g_launches.load(); }
 
+int cbddc_set_tensor_cores(int enable) {
+  const bool prev = g_tensor_cores.exchange(enable != 0);
+  return prev ? 1 : 0;
+}
+
 int cbddc_timer_start(int kernel_class) {
   return guard([&] {
-    CB_CHECK(kernel_class >= 0 && kernel_class <= CBDDC_TIMER_ORTH, CBDDC_EINVAL, "bad kernel class");
-    g_timer.kernel_class = kernel_class;
-    g_timer.used = 0;
-    g_timer.depth = 0;
-    g_timer.open = false;
-    g_timer.launches = 0;
-    g_timer.flops = g_timer.bytes = 0.0;
+    CB_CHECK(kernel_class >= 0 && kernel_class <= CBDDC_TIMER_SETUP_GEMM_F64, CBDDC_EINVAL, "bad kernel class");
+    for (auto& t : g_timers) {
+      t.on = false;
+      t.reset();
+    }
+    g_timer_primary = kernel_class;
+    if (kernel_class > 0) g_timers[kernel_class].on = true;
+  });
+}
+
+int cbddc_timer_enable(int kernel_class) {
+  return guard([&] {
+    CB_CHECK(kernel_class > 0 && kernel_class <= CBDDC_TIMER_SETUP_GEMM_F64, CBDDC_EINVAL, "bad kernel class");
+    ClassTimer& t = g_timers[kernel_class];
+    if (!t.on) {
+      t.reset();
+      t.on = true;
+    }
+  });
+}
+
+int cbddc_timer_result(int kernel_class, double* total_ms, int64_t* launches, double* flops, double* bytes) {
+  return guard([&] {
+    CB_CHECK(kernel_class > 0 && kernel_class <= CBDDC_TIMER_SETUP_GEMM_F64, CBDDC_EINVAL, "bad kernel class");
+    timer_totals(kernel_class, total_ms, launches, flops, bytes);
   });
 }
 
 int cbddc_timer_stop(double* total_ms, int64_t* launches, double* flops, double* bytes) {
   return guard([&] {
-    double ms = 0.0;
-    for (size_t i = 0; i + 1 < g_timer.used; i += 2) {
-      CB_CUDA(cudaEventSynchronize(g_timer.pool[i + 1]));
-      float v = 0.f;
-      CB_CUDA(cudaEventElapsedTime(&v, g_timer.pool[i], g_timer.pool[i + 1]));
-      ms += v;
+    if (g_timer_primary > 0) {
+      timer_totals(g_timer_primary, total_ms, launches, flops, bytes);
+    } else {
+      if (total_ms) *total_ms = 0.0;
+      if (launches) *launches = 0;
+      if (flops) *flops = 0.0;
+      if (bytes) *bytes = 0.0;
     }
-    if (total_ms) *total_ms = ms;
-    if (launches) *launches = g_timer.launches;
-    if (flops) *flops = g_timer.flops;
-    if (bytes) *bytes = g_timer.bytes;
-    g_timer.kernel_class = 0;
-    g_timer.used = 0;
-    g_timer.depth = 0;
-    g_timer.open = false;
+    for (auto& t : g_timers) {
+      t.on = false;
+      t.reset();
+    }
+    g_timer_primary = 0;
   });
 }
 

@@ -52,7 +52,8 @@ void timer_end(int kernel_class, cudaStream_t s, double flops, double bytes);
 enum : int {
   DEV_INVERTED = 1,  // J <= 0 at a quadrature point
   DEV_PIVOT = 2,     // tiny or non-finite pivot
-  DEV_NONFINITE = 4  // NaN / Inf found
+  DEV_NONFINITE = 4, // NaN / Inf found
+  DEV_TIMEOUT = 8    // a bounded device-side wait expired
 };
 
 // Owning device allocation (no copy; move only).

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "common.h"
+#include "tc_gemm.cuh"
 
 namespace cbddc {
 
@@ -27,6 +28,10 @@ struct GemmProb {
   int lda, ldb, ldc;
   int64_t a, b, c;  // element offsets from the kernel's base pointers
 };
+
+// FP32 setup GEMMs run on the tensor cores (tcgen05, 3xTF32) unless this is
+// cleared (cbddc_set_tensor_cores); the FP64 path always uses the SIMT kernels.
+bool tensor_cores_enabled();
 
 template <typename T> struct GemmCfg;
 template <> struct GemmCfg<float> { static constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8; };
@@ -285,12 +290,24 @@ static_assert(GemmCfg<float>::BM == 128 && GemmCfg<float>::BN == 128 && 32 * Vec
 static_assert(GemmCfg<double>::BM == 64 && GemmCfg<double>::BN == 64 && 32 * VecT<double>::W == 64, "tile");
 
 // A list of grouped GEMM problems with its output tiles and host-side totals.
+// FP32 lists also carry the plan of the tensor-core path: every problem's
+// first row in the split operand arrays (op(A): M rows, op(B)^T: N rows, K
+// padded to Kp), and, once bound to a scratch buffer, the four TMA maps.
 struct GemmList {
   DVec<GemmProb> d;
   DVec<int4> tiles;  // {problem, tile row, tile column, 0}
   int n = 0, ntiles = 0;
   double flops = 0.0, bytes = 0.0;
   bool fast = true;  // every problem meets the vector-load alignment
+  // tensor-core plan (FP32 only)
+  bool tc_planned = false, tc_bound = false;
+  int Kp = 0, maxM = 0, maxN = 0;
+  int64_t rowsA = 0, rowsB = 0;
+  DVec<tc::TcProb> tcp;
+  DVec<tc::SplitProb> spa, spb;
+  float* tc_base = nullptr;
+  int* tc_status = nullptr;
+  CUtensorMap maps[4];
   void set(const std::vector<GemmProb>& v, size_t esize, bool ta = false) {
     n = (int)v.size();
     flops = bytes = 0.0;
@@ -310,8 +327,70 @@ struct GemmList {
     ntiles = (int)t.size();
     d.upload(v);
     tiles.upload(t);
+    tc_planned = tc_bound = false;
+    if (esize == 4 && ntiles > 0 && n <= 65535) plan_tc(v);
+  }
+  void plan_tc(const std::vector<GemmProb>& v) {
+    std::vector<tc::TcProb> tp(n);
+    std::vector<tc::SplitProb> sa(n), sb(n);
+    int kmax = 0;
+    rowsA = rowsB = 0;
+    maxM = maxN = 0;
+    for (int i = 0; i < n; ++i) {
+      const GemmProb& q = v[i];
+      const int M = std::max(q.M, 0), N = std::max(q.N, 0), K = std::max(q.K, 0);
+      tp[i] = tc::TcProb{M, N, K, q.ldc, q.c, (int)rowsA, (int)rowsB};
+      sa[i] = tc::SplitProb{K > 0 ? M : 0, K, q.lda, q.a, (int)rowsA};
+      sb[i] = tc::SplitProb{K > 0 ? N : 0, K, q.ldb, q.b, (int)rowsB};
+      rowsA += M;
+      rowsB += N;
+      kmax = std::max(kmax, K);
+      maxM = std::max(maxM, M);
+      maxN = std::max(maxN, N);
+    }
+    if (rowsA >= INT32_MAX || rowsB >= INT32_MAX) return;
+    Kp = (int)round_up(std::max(kmax, 1), tc::BKC);
+    tcp.upload(tp);
+    spa.upload(sa);
+    spb.upload(sb);
+    tc_planned = true;
+  }
+  // floats of split operands this list needs
+  int64_t tc_floats() const { return tc_planned ? 2 * (rowsA + rowsB) * (int64_t)Kp : 0; }
+  void bind_tc(float* base, int* status) {
+    if (!tc_planned) return;
+    tc_base = base;
+    tc_status = status;
+    maps[0] = tc::encode_kmajor(base, rowsA, Kp);
+    maps[1] = tc::encode_kmajor(base + rowsA * Kp, rowsA, Kp);
+    maps[2] = tc::encode_kmajor(base + 2 * rowsA * Kp, rowsB, Kp);
+    maps[3] = tc::encode_kmajor(base + 2 * rowsA * Kp + rowsB * Kp, rowsB, Kp);
+    tc_bound = true;
   }
 };
+
+// C = alpha op(A) op(B) + beta C for a bound FP32 list on the tensor cores:
+// split both operands into the list's K-major hi/lo arrays, then one
+// tcgen05 CTA per output tile.
+template <bool TA, bool TB>
+void launch_tc(const GemmList& g, const float* A, const float* B, float* C, float alpha, float beta,
+               cudaStream_t s) {
+  float* Ah = g.tc_base;
+  float* Al = Ah + g.rowsA * g.Kp;
+  float* Bh = Al + g.rowsA * g.Kp;
+  float* Bl = Bh + g.rowsB * g.Kp;
+  const dim3 ga(cdiv(g.maxM, 32) * (unsigned)(g.Kp / 32), g.n), gb(cdiv(g.maxN, 32) * (unsigned)(g.Kp / 32), g.n);
+  // op(A) rows are A's rows unless TA; op(B)^T rows are B's rows when TB
+  tc::tc_split_kernel<!TA><<<ga, 256, 0, s>>>(g.spa.p, g.Kp, A, Ah, Al);
+  CB_LAUNCH();
+  tc::tc_split_kernel<TB><<<gb, 256, 0, s>>>(g.spb.p, g.Kp, B, Bh, Bl);
+  CB_LAUNCH();
+  tc::set_smem_attr();
+  tc::tc_gemm_kernel<tc::STAGES><<<g.ntiles, tc::THREADS, tc::SMEM_BYTES, s>>>(g.tiles.p, g.tcp.p, g.maps[0], g.maps[1],
+                                                                     g.maps[2], g.maps[3], C, alpha, beta,
+                                                                     g.tc_status);
+  CB_LAUNCH();
+}
 
 template <typename T, bool TA, bool TB>
 void launch_gemm(const int4* tiles, int ntiles, const GemmProb* probs, const T* A, const T* B, T* C,
@@ -328,13 +407,22 @@ void launch_gemm(const int4* tiles, int ntiles, const GemmProb* probs, const T* 
   CB_LAUNCH();
 }
 
-// Launch of a whole list (timed as a setup GEMM when the timer follows them).
+// Launch of a whole list (timed as a setup GEMM when the timer follows
+// them: FP32 lists in class SETUP_GEMM, FP64 ones in SETUP_GEMM_F64).
 template <typename T, bool TA, bool TB>
 void launch_list(const GemmList& g, const T* A, const T* B, T* C, T alpha, T beta, cudaStream_t s) {
   if (g.ntiles == 0) return;
-  timer_begin(CBDDC_TIMER_SWEEP_GEMM, s);
+  const int cls = sizeof(T) == 4 ? CBDDC_TIMER_SWEEP_GEMM : CBDDC_TIMER_SETUP_GEMM_F64;
+  timer_begin(cls, s);
+  if constexpr (sizeof(T) == 4) {
+    if (g.tc_bound && tensor_cores_enabled()) {
+      launch_tc<TA, TB>(g, A, B, C, alpha, beta, s);
+      timer_end(cls, s, g.flops, g.bytes);
+      return;
+    }
+  }
   launch_gemm<T, TA, TB>(g.tiles.p, g.ntiles, g.d.p, A, B, C, alpha, beta, s, g.fast);
-  timer_end(CBDDC_TIMER_SWEEP_GEMM, s, g.flops, g.bytes);
+  timer_end(cls, s, g.flops, g.bytes);
 }
 
 // --------------------------------------------------------------- sweeps

@@ -1044,36 +1044,45 @@ void assemble(fem_problem* P, const double* d, double lam, double* residual, boo
   }
 }
 
-// y = K x, 3x3 BSR, one warp per block row.  Lane L < 24 owns row
-// r = L % 3 of the blocks k, k + 8, k + 16, ... (k = L / 3): each value costs
-// one FP64 FMA (FP64 issue is the scarce resource here), loads stay within
-// the row's contiguous value segment, and three shuffle steps (12, 6, 3)
-// sum the eight partial rows.
-__global__ void bsr_spmv_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
-                                const double* __restrict__ vals, const double* __restrict__ x,
-                                double* __restrict__ y, int nrows) {
+// y = K x, one warp per block row.  FP64 issue is the roof here (GB300 runs
+// about two FP64 FMAs per SM and clock), so every lane keeps one fixed
+// entry e = lane % 9 (row r = e / 3, column c = e % 3) of the 3 x 3 blocks
+// and takes block 3 t + lane / 9 at step t: 27 lanes read 27 consecutive
+// values of the row's contiguous block run (coalesced) and issue one FMA
+// each.  The row's column indices are read once (coalesced, 32 at a time)
+// and passed by shuffle, so the x gathers do not wait on a dependent load.
+// Partial sums: lanes with equal e, then the three e of each r.
+__global__ void __launch_bounds__(256)
+bsr_spmv_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col, const double* __restrict__ vals,
+                const double* __restrict__ x, double* __restrict__ y, int nrows) {
   const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= nrows) return;
-  const int b0 = row_ptr[row], nb = row_ptr[row + 1] - b0;
-  const int r = lane % 3, k = lane / 3;
+  const int b0 = __ldg(row_ptr + row), nb = __ldg(row_ptr + row + 1) - b0;
+  const int e = lane % 9, q = lane / 9, c = e % 3;
+  const bool active = lane < 27;
+  const double* v = vals + (int64_t)b0 * 9;
   double acc = 0.0;
-  if (lane < 24) {
-    const double* v = vals + (int64_t)b0 * 9 + r * 3;
-    const int* c = col + b0;
+  for (int base = 0; base < nb; base += 32) {
+    // column indices of blocks base .. base + 31 of this row
+    const int cl = (base + lane < nb) ? __ldg(col + b0 + base + lane) : 0;
+    const int nbc = min(32, nb - base);
 #pragma unroll 4
-    for (int b = k; b < nb; b += 8) {
-      const double* vb = v + (int64_t)b * 9;
-      const double* xb = x + (int64_t)__ldg(c + b) * 3;
-      acc = fma(__ldcs(vb + 0), __ldg(xb + 0), acc);
-      acc = fma(__ldcs(vb + 1), __ldg(xb + 1), acc);
-      acc = fma(__ldcs(vb + 2), __ldg(xb + 2), acc);
+    for (int t = 0; t < 11; ++t) {      // 11 steps of 3 blocks cover 32 blocks
+      const int bl = 3 * t + q;           // block within this chunk of 32
+      const int cb = __shfl_sync(0xffffffffu, cl, bl & 31);
+      if (3 * t >= nbc) break;
+      if (active && bl < nbc)
+        acc = fma(__ldcs(v + (int64_t)(base + bl) * 9 + e), __ldg(x + (int64_t)cb * 3 + c), acc);
     }
   }
-  acc += __shfl_down_sync(0xffffffffu, acc, 12);
-  acc += __shfl_down_sync(0xffffffffu, acc, 6);
-  acc += __shfl_down_sync(0xffffffffu, acc, 3);
-  if (lane < 3) y[(int64_t)row * 3 + lane] = acc;
+  // lanes 0..8: entry e summed over the lanes e, e + 9, e + 18; then lanes
+  // 0, 3, 6: the three entries of row r = lane / 3
+  const double s = acc + __shfl_sync(0xffffffffu, acc, (lane + 9) & 31) +
+                   __shfl_sync(0xffffffffu, acc, (lane + 18) & 31);
+  const double s1 = __shfl_sync(0xffffffffu, s, (lane + 1) & 31);
+  const double s2 = __shfl_sync(0xffffffffu, s, (lane + 2) & 31);
+  if (lane < 9 && lane % 3 == 0) y[(int64_t)row * 3 + lane / 3] = s + s1 + s2;
 }
 
 void bsr_spmv(const fem_problem* P, const double* x, double* y, cudaStream_t s) {

@@ -23,7 +23,8 @@ namespace {
 
 constexpr int DOT_THREADS = 256;
 constexpr int64_t kCoopMaxN = 1000000;  // longest vector for the cooperative orthogonalisation
-constexpr int MAXV = 128;       // maximum Krylov vectors per dot launch
+constexpr int MAXV = 128;       // Krylov vectors of the cooperative orthogonalisation
+constexpr int MAXR = 1024;      // Krylov vectors per cycle (restart <= MAXR - 1)
 
 __device__ inline double wsum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -47,10 +48,13 @@ struct DotArgs {
   int64_t n;
   const double* hin;    // if non-null: w -= V hin before the dots
   int self_norm;        // dots of w with itself instead of with V
-  double* partial;      // [gridDim.x][MAXV]
+  double* partial;      // [gridDim.x][pstride]
+  int pstride;          // row stride of partial (>= nvec)
   unsigned* ticket;     // zero on entry, reset by the last CTA
   double* out;          // [nvec] (or [1] for the norm)
   const int* done;      // skip everything once GMRES has converged
+  const int* gate;      // if non-null: skip unless *gate != 0
+  int also_norm;        // dots with V plus out[nvec] = ||w||^2 (before any update)
 };
 
 __device__ inline void last_block_sum(const DotArgs& a, int nout) {
@@ -62,23 +66,28 @@ __device__ inline void last_block_sum(const DotArgs& a, int nout) {
   __syncthreads();
   if (!last) return;
   // two threads per output: CTAs [0, G/2) and [G/2, G), four accumulators
-  // each in a fixed order, then the halves added in a fixed order
-  const int j = threadIdx.x & (MAXV - 1), side = threadIdx.x >> 7;
+  // each in a fixed order, then the halves added in a fixed order; outputs
+  // in chunks of 128
+  const int jl = threadIdx.x & (MAXV - 1), side = threadIdx.x >> 7;
   const unsigned G = gridDim.x, mid = G / 2;
   const unsigned c0 = side ? mid : 0u, c1 = side ? G : mid;
-  double s4[4] = {0.0, 0.0, 0.0, 0.0};
-  if (j < nout) {
-    unsigned c = c0;
-    for (; c + 4 <= c1; c += 4) {
+  for (int j0 = 0; j0 < nout; j0 += MAXV) {
+    const int j = j0 + jl;
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    if (j < nout) {
+      unsigned c = c0;
+      for (; c + 4 <= c1; c += 4) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) s4[q] += __ldcg(a.partial + (int64_t)(c + q) * MAXV + j);
+        for (int q = 0; q < 4; ++q) s4[q] += __ldcg(a.partial + (int64_t)(c + q) * a.pstride + j);
+      }
+      for (; c < c1; ++c) s4[0] += __ldcg(a.partial + (int64_t)c * a.pstride + j);
     }
-    for (; c < c1; ++c) s4[0] += __ldcg(a.partial + (int64_t)c * MAXV + j);
+    const double sum = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+    if (side == 1 && j < nout) half[jl] = sum;
+    __syncthreads();
+    if (side == 0 && j < nout) a.out[j] = sum + half[jl];
+    __syncthreads();
   }
-  const double sum = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-  if (side == 1 && j < nout) half[j] = sum;
-  __syncthreads();
-  if (side == 0 && j < nout) a.out[j] = sum + half[j];
   if (threadIdx.x == 0) *a.ticket = 0u;
   __threadfence();
 }
@@ -86,9 +95,10 @@ __device__ inline void last_block_sum(const DotArgs& a, int nout) {
 template <int RPT>
 __global__ void __launch_bounds__(DOT_THREADS) fused_dots_kernel(DotArgs a) {
   if (a.done && *a.done) return;
+  if (a.gate && !*a.gate) return;
   constexpr int TILE = DOT_THREADS * RPT;
   __shared__ double ws[TILE];
-  __shared__ double hs[MAXV];
+  __shared__ double hs[MAXR];
   __shared__ double red[DOT_THREADS / 32];
   const int64_t r0 = (int64_t)blockIdx.x * TILE;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -118,7 +128,20 @@ __global__ void __launch_bounds__(DOT_THREADS) fused_dots_kernel(DotArgs a) {
       if (q < rows) a.w[r0 + q] = x[t];
     }
   }
-  const int nout = a.self_norm ? 1 : a.nvec;
+  const int nout = a.self_norm ? 1 : a.nvec + (a.also_norm ? 1 : 0);
+  if (a.also_norm && !a.self_norm) {
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) acc += x[t] * x[t];
+    acc = wsum(acc);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double sm = 0.0;
+      for (int q = 0; q < DOT_THREADS / 32; ++q) sm += red[q];
+      a.partial[(int64_t)blockIdx.x * a.pstride + a.nvec] = sm;
+    }
+  }
   if (a.self_norm) {
     double acc = 0.0;
 #pragma unroll
@@ -129,7 +152,7 @@ __global__ void __launch_bounds__(DOT_THREADS) fused_dots_kernel(DotArgs a) {
     if (tid == 0) {
       double sm = 0.0;
       for (int q = 0; q < DOT_THREADS / 32; ++q) sm += red[q];
-      a.partial[(int64_t)blockIdx.x * MAXV] = sm;
+      a.partial[(int64_t)blockIdx.x * a.pstride] = sm;
     }
   } else {
 #pragma unroll
@@ -142,7 +165,7 @@ __global__ void __launch_bounds__(DOT_THREADS) fused_dots_kernel(DotArgs a) {
       for (int q = lane; q < TILE; q += 32)
         if (q < rows) acc += Vj[q] * ws[q];
       acc = wsum(acc);
-      if (lane == 0) a.partial[(int64_t)blockIdx.x * MAXV + j] = acc;
+      if (lane == 0) a.partial[(int64_t)blockIdx.x * a.pstride + j] = acc;
     }
   }
   last_block_sum(a, nout);
@@ -312,21 +335,49 @@ __global__ void scale_kernel(const double* __restrict__ w, double* __restrict__ 
   if (i < n) v[i] = w[i] * scal[idx];
 }
 
-// y = R^-1 g (upper triangular, k columns), single thread
-__global__ void backsolve_kernel(const double* __restrict__ H, int m, const int* __restrict__ kp,
-                                 const double* __restrict__ g, double* __restrict__ y) {
+// y = R^-1 g (upper triangular, k columns), one CTA: column-oriented back
+// substitution, y_i = s_i / R_ii and then s_r -= R_ri y_i for all r < i in
+// parallel (one barrier per column)
+__global__ void __launch_bounds__(256)
+backsolve_kernel(const double* __restrict__ H, int m, const int* __restrict__ kp,
+                 const double* __restrict__ g, double* __restrict__ y) {
+  __shared__ double sv[MAXR];
+  __shared__ double yi;
   const int k = *kp;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sv[i] = g[i];
+  __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int c = i + 1; c < k; ++c) s -= H[(int64_t)c * (m + 1) + i] * y[c];
-    y[i] = s / H[(int64_t)i * (m + 1) + i];
+    const double* col = H + (int64_t)i * (m + 1);
+    if (threadIdx.x == 0) {
+      yi = sv[i] / col[i];
+      y[i] = yi;
+    }
+    __syncthreads();
+    const double v = yi;
+    for (int r = threadIdx.x; r < i; r += blockDim.x) sv[r] -= col[r] * v;
+    __syncthreads();
+  }
+}
+
+// Second Gram-Schmidt pass needed?  reorth = (||w - V h1||^2 < ||w||^2 / 2)
+// with ||w||^2 in h1[nvec]; without it h2 = 0.  count[0] counts the passes.
+__global__ void dgks_kernel(const double* __restrict__ h1, int nvec, const double* __restrict__ wn2,
+                            double* __restrict__ h2, int* __restrict__ reorth, int* __restrict__ count,
+                            const int* __restrict__ done) {
+  if (*done) return;
+  const bool again = !(wn2[0] >= 0.5 * h1[nvec]);
+  if (!again)
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) h2[i] = 0.0;
+  if (threadIdx.x == 0) {
+    *reorth = again ? 1 : 0;
+    if (again) *count += 1;
   }
 }
 
 // x += Z y  (k = number of columns)
 __global__ void combine_kernel(const double* __restrict__ Z, int64_t ldz, const int* __restrict__ kp,
                                const double* __restrict__ y, double* __restrict__ x, int64_t n) {
-  __shared__ double ys[MAXV];
+  __shared__ double ys[MAXR];
   const int k = *kp;
   for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
   __syncthreads();
@@ -363,12 +414,15 @@ __global__ void cycle_start_kernel(const double* __restrict__ rn2, double* __res
 void Gmres::ensure_small(int64_t n_) {
   if (partial.p && nchunks == (int)cdiv(n_, DOT_THREADS)) return;
   nchunks = (int)cdiv(n_, DOT_THREADS);   // CTAs at one row per thread (the most)
-  partial.alloc((size_t)nchunks * MAXV);
+  pstride = MAXV;
+  partial.alloc((size_t)nchunks * pstride);
   ticket.alloc(1);
   CB_CUDA(cudaMemset(ticket.p, 0, sizeof(unsigned)));
-  h.alloc(3 * MAXV);
+  hstride = MAXV;
+  h.alloc(3 * hstride);
   scal.alloc(8);
   flags.alloc(4);
+  CB_CUDA(cudaMemset(flags.p, 0, 4 * sizeof(int)));
   if (!host_scal) CB_CUDA(cudaMallocHost(&host_scal, 64));
   if (!host_flags) CB_CUDA(cudaMallocHost(&host_flags, 16));
 }
@@ -393,9 +447,18 @@ void Gmres::ensure(int64_t n_, int m_) {
                                           : 0;
     if (coop_grid > 0) cpart.alloc((size_t)3 * coop_grid * MAXV);
   }
-  CB_CHECK(m_ >= 1 && m_ < MAXV, CBDDC_EINVAL, "restart must be in [1, 127]");
+  CB_CHECK(m_ >= 1 && m_ < MAXR, CBDDC_EINVAL, "restart must be in [1, 1023]");
   n = n_;
   m = m_;
+  // partial sums and Hessenberg columns for up to m + 1 Krylov vectors
+  if (m + 1 > pstride) {
+    pstride = (int)round_up(m + 1, 32);
+    partial.alloc((size_t)nchunks * pstride);
+  }
+  if (m + 1 > hstride) {
+    hstride = (int)round_up(m + 1, 32);
+    h.alloc(3 * (size_t)hstride);
+  }
   V.alloc((size_t)(m + 1) * n);
   Zb.alloc((size_t)m * n);
   w.alloc(n);
@@ -415,8 +478,9 @@ Gmres::~Gmres() {
 // out = V^T w over nvec columns (stride ldv), optionally after w -= V hin,
 // or out[0] = ||w||^2 with self_norm; one launch with a last-block reduction.
 static void fused_dots(Gmres& G, const double* V, int64_t ldv, int nvec, double* w, int64_t n,
-                       const double* hin, int self_norm, double* out, const int* done, cudaStream_t s) {
-  DotArgs a{V, ldv, nvec, w, n, hin, self_norm, G.partial.p, G.ticket.p, out, done};
+                       const double* hin, int self_norm, double* out, const int* done, cudaStream_t s,
+                       const int* gate = nullptr, int also_norm = 0) {
+  DotArgs a{V, ldv, nvec, w, n, hin, self_norm, G.partial.p, G.pstride, G.ticket.p, out, done, gate, also_norm};
   // rows per thread: the largest of 16, 8, 4, 2, 1 that still gives two
   // CTAs per SM (fewer CTAs also shorten the last CTA's reduction)
   const int64_t sms2 = 2 * 152;
@@ -477,10 +541,10 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
       // classical Gram-Schmidt, twice: h1 = V^T w; w -= V h1 and h2 = V^T w;
       // w -= V h2 and ||w||^2 (three launches)
       double* h1 = G.h.p;
-      double* h2 = G.h.p + MAXV;
-      double* wn2 = G.h.p + 2 * MAXV;
+      double* h2 = G.h.p + G.hstride;
+      double* wn2 = G.h.p + 2 * G.hstride;
       timer_begin(CBDDC_TIMER_ORTH, s);
-      if (G.coop_grid > 0) {
+      if (G.coop_grid > 0 && j + 1 <= MAXV) {
         CgsArgs ca{G.V.p, n, j + 1, G.w.p, G.V.p + (int64_t)(j + 1) * n, G.cpart.p, j, m,
                    G.H.p, G.cs.p, G.sn.p, G.g.p, G.scal.p, rtol, done, kcount};
         void* args[] = {&ca};
@@ -488,26 +552,35 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
                                             dim3(DOT_THREADS), args, 0, s));
         CB_LAUNCH();
       } else {
-        fused_dots(G, G.V.p, n, j + 1, G.w.p, n, nullptr, 0, h1, done, s);
-        fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h1, 0, h2, done, s);
-        fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h2, 1, wn2, done, s);
+        // classical Gram-Schmidt with a second pass only where the first
+        // one lost more than half of ||w||^2 (Daniel-Gragg-Kaufman-Stewart
+        // criterion, eta = 1/sqrt(2)): h1 = V^T w with ||w||^2; w -= V h1
+        // with the new ||w||^2; then, gated on the device, h2 = V^T w and
+        // w -= V h2 with its norm
+        int* reorth = G.flags.p + 2;
+        fused_dots(G, G.V.p, n, j + 1, G.w.p, n, nullptr, 0, h1, done, s, nullptr, 1);
+        fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h1, 1, wn2, done, s);
+        dgks_kernel<<<1, 256, 0, s>>>(h1, j + 1, wn2, h2, reorth, G.flags.p + 3, done);
+        CB_LAUNCH();
+        fused_dots(G, G.V.p, n, j + 1, G.w.p, n, nullptr, 0, h2, done, s, reorth);
+        fused_dots(G, G.V.p, n, j + 1, G.w.p, n, h2, 1, wn2, done, s, reorth);
         givens_kernel<<<1, 1, 0, s>>>(j, m, G.H.p, G.cs.p, G.sn.p, G.g.p, h1, h2, wn2, G.scal.p, rtol,
                                       done, kcount);
         CB_LAUNCH();
         scale_kernel<<<nb, 256, 0, s>>>(G.w.p, G.V.p + (int64_t)(j + 1) * n, n, G.scal.p, 1, done);
         CB_LAUNCH();
       }
-      // algorithmic traffic: V read three times (dots, update + dots,
-      // update), w read 3x / written 2x, v_{j+1} written
-      timer_end(CBDDC_TIMER_ORTH, s, 6.0 * (j + 1) * (double)n,
-                8.0 * (double)n * (3.0 * (j + 1) + 6.0));
+      // algorithmic traffic of one Gram-Schmidt pass (the second pass, when
+      // taken, is not counted): V read twice (dots, update), w read twice
+      // and written once, v_{j+1} written
+      timer_end(CBDDC_TIMER_ORTH, s, 4.0 * (j + 1) * (double)n, 8.0 * (double)n * (2.0 * (j + 1) + 4.0));
       CB_CUDA(cudaMemcpyAsync(hflags, done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
       CB_CUDA(cudaStreamSynchronize(s));
       ++total;
       if (hflags[0]) { ++j; break; }
     }
     // x += Z y over the columns built in this cycle
-    backsolve_kernel<<<1, 1, 0, s>>>(G.H.p, m, kcount, G.g.p, G.y.p);
+    backsolve_kernel<<<1, 256, 0, s>>>(G.H.p, m, kcount, G.g.p, G.y.p);
     CB_LAUNCH();
     combine_kernel<<<nb, 256, 0, s>>>(G.Zb.p, n, kcount, G.y.p, x, n);
     CB_LAUNCH();

@@ -10,6 +10,8 @@ struct Gmres {
   int64_t n = 0;
   int m = 0;
   int nchunks = 0;
+  int pstride = 0;           // row stride of the per-CTA partial sums
+  int hstride = 0;           // stride of the three CGS coefficient vectors in h
   DVec<double> V, Zb, w, r, H, cs, sn, g, y, h, partial, scal;
   DVec<int> flags;
   DVec<unsigned> ticket;

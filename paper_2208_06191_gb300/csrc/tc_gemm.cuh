@@ -1,0 +1,404 @@
+// Grouped FP32 GEMM on the fifth-generation tensor cores (tcgen05,
+// kind::tf32), for the dense contractions of the BDDC setup (the Gauss-Jordan
+// sweep updates, E = A_II^-1 A_IG, S = A_GG - A_GI E, the constraint and
+// coarse-basis products of Section 3.2).
+//
+// Precision: a TF32 operand keeps 10 mantissa bits, too few for explicit
+// inverses of local matrices whose condition numbers reach 1e4.  Every
+// operand x is therefore split into x_hi = tf32(x) and x_lo = tf32(x - x_hi)
+// and the product is accumulated in FP32 as
+//     A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// which drops only A_lo B_lo (relative size 2^-22), i.e. FP32-level accuracy
+// with three tensor-core passes.
+//
+// Data flow of C = alpha op(A) op(B) + beta C for a list of problems:
+//   1. split kernels write op(A) (M x K) and op(B)^T (N x K) as K-major
+//      hi/lo arrays into a scratch buffer, one row range per problem, K
+//      zero-padded to a multiple of 32;
+//   2. one CTA per 128 x 128 output tile: a TMA producer thread streams
+//      K chunks of 32 (one 128-byte swizzled row per tile row; A_hi, A_lo,
+//      B_hi, B_lo = 64 KB per stage, 3 stages) into shared memory; one
+//      thread issues 3 x 4 tcgen05.mma (M = N = 128, K = 8) per chunk into a
+//      128-column TMEM accumulator and frees the stage with tcgen05.commit;
+//      after the last chunk the four warps read their 32 TMEM lanes
+//      (tcgen05.ld) and apply alpha / beta to C in global memory.
+// Rows past a problem's M (or N) read other problems' rows or the
+// zero fill beyond the array; they only reach accumulator rows (columns)
+// that are never stored.
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel sets DEV_TIMEOUT
+// in the status word, waits (bounded) for the copies it issued, frees its
+// TMEM and returns.
+#pragma once
+#include <cuda.h>
+#include <stdint.h>
+
+#include "common.h"
+
+namespace cbddc {
+namespace tc {
+
+constexpr int BM = 128, BN = 128;             // output tile
+constexpr int BKC = 32;                       // K per chunk: 32 x 4 B = one 128-byte swizzle row
+constexpr int STAGES = 3;
+constexpr int OPND_BYTES = BM * BKC * 4;      // one operand tile of a chunk (16 KB)
+constexpr int STAGE_BYTES = 4 * OPND_BYTES;   // A_hi, A_lo, B_hi, B_lo
+constexpr int THREADS = 128;
+constexpr int TMEM_COLS = 128;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr uint32_t kWaitLimit = 1u << 25;     // polls of one mbarrier before giving up
+
+// Instruction descriptor of kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
+// (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout that TMA writes: rows of 128 B, 8-row atoms of 1 KB
+// stacked along M/N (stride byte offset 1024), descriptor version 1
+// (bits 46-47), layout type 2 = 128-byte swizzle (bits 61-63).  The leading
+// byte offset is unused for this layout.  Advancing K by 8 TF32 elements
+// inside the atom adds 32 bytes to the start address.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrives on bar once every tcgen05.mma issued so far by this thread is done.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes (one row per thread).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+      "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+      "[%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// TF32 rounding (round to nearest, ties away from zero); the low 13
+// mantissa bits of the result are zero.
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  return __uint_as_float(h);
+}
+
+// Problem of a tensor-core list: sizes, C placement and the first rows of
+// its operands in the split arrays.
+struct TcProb {
+  int M, N, K, ldc;
+  int64_t c;
+  int ar, br;
+};
+
+// The 128 x 128 tile (problem tl.x, tile row tl.y, tile column tl.z) of
+// C = alpha A B + beta C from the split operands.
+template <int NST>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_gemm_kernel(const int4* __restrict__ tiles, const TcProb* __restrict__ probs,
+               const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+               float* __restrict__ C, float alpha, float beta, int* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte aligned operand stages (the swizzle pattern repeats every 1 KB)
+  const uint32_t base = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + ((1024u - (base & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * STAGE_BYTES);
+  uint64_t* empty = full + NST;
+  uint64_t* accum = empty + NST;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int4 tl = tiles[blockIdx.x];
+  const TcProb p = probs[tl.x];
+  const int m0 = tl.y * BM, n0 = tl.z * BN;
+  const int nk = (p.K + BKC - 1) / BKC;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;  // chunks whose copies the producer issued
+  if (warp == 0 && lane == 0 && nk > 0) {
+    // TMA producer
+    for (int c = 0; c < nk; ++c) {
+      const int s = c % NST;
+      if (c >= NST && !mbar_wait(&empty[s], ((c / NST) - 1) & 1)) {
+        atomicExch(abort_flag, 1);
+        break;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint8_t* st = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_2d(st, &mAh, c * BKC, p.ar + m0, &full[s]);
+      tma_load_2d(st + OPND_BYTES, &mAl, c * BKC, p.ar + m0, &full[s]);
+      tma_load_2d(st + 2 * OPND_BYTES, &mBh, c * BKC, p.br + n0, &full[s]);
+      tma_load_2d(st + 3 * OPND_BYTES, &mBl, c * BKC, p.br + n0, &full[s]);
+      issued = c + 1;
+    }
+  } else if (warp == 1 && lane == 0 && nk > 0) {
+    // MMA issuer: 4 K-steps of 8 per chunk, three products per step
+    for (int c = 0; c < nk; ++c) {
+      const int s = c % NST;
+      if (!mbar_wait(&full[s], (c / NST) & 1)) {
+        atomicExch(abort_flag, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+      for (int k = 0; k < BKC / 8; ++k) {
+        const uint64_t ah = sw128_desc(st + 32 * k);
+        const uint64_t al = sw128_desc(st + OPND_BYTES + 32 * k);
+        const uint64_t bh = sw128_desc(st + 2 * OPND_BYTES + 32 * k);
+        const uint64_t bl = sw128_desc(st + 3 * OPND_BYTES + 32 * k);
+        mma_tf32(tmem, al, bh, (c > 0 || k > 0) ? 1u : 0u);
+        mma_tf32(tmem, ah, bl, 1u);
+        mma_tf32(tmem, ah, bh, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(accum);
+  }
+  __syncwarp();
+
+  // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31
+  bool ok = nk > 0 && mbar_wait(accum, 0);
+  if (!ok) atomicExch(abort_flag, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  const bool aborted = *(volatile int*)abort_flag != 0;
+  if (!aborted) {
+    const int row = m0 + warp * 32 + lane;
+    float* crow = C + p.c + (int64_t)row * p.ldc;
+    const bool vec = ((p.c & 3) == 0) && ((p.ldc & 3) == 0);
+#pragma unroll 1
+    for (int cc = 0; cc < BN / 32; ++cc) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
+      const int nb = n0 + cc * 32;
+      if (row < p.M && nb < p.N) {
+        if (vec && nb + 32 <= p.N) {
+          float4* c4 = reinterpret_cast<float4*>(crow + nb);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float4 o;
+            if (beta != 0.f) {
+              const float4 old = c4[q];
+              o = make_float4(alpha * v[4 * q] + beta * old.x, alpha * v[4 * q + 1] + beta * old.y,
+                              alpha * v[4 * q + 2] + beta * old.z, alpha * v[4 * q + 3] + beta * old.w);
+            } else {
+              o = make_float4(alpha * v[4 * q], alpha * v[4 * q + 1], alpha * v[4 * q + 2], alpha * v[4 * q + 3]);
+            }
+            c4[q] = o;
+          }
+        } else {
+          for (int q = 0; q < 32 && nb + q < p.N; ++q) {
+            float* cp = crow + nb + q;
+            *cp = (beta != 0.f) ? alpha * v[q] + beta * *cp : alpha * v[q];
+          }
+        }
+      }
+    }
+  } else if (threadIdx.x == 0 && nk > 0) {
+    atomicOr(status, DEV_TIMEOUT);
+  }
+  // an aborted producer's copies may still be in flight: wait (bounded) for
+  // the stages it filled before the shared memory is released
+  if (aborted && warp == 0 && lane == 0) {
+    for (int c = (issued > NST ? issued - NST : 0); c < issued; ++c)
+      (void)mbar_wait(&full[c % NST], (c / NST) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// Split of one operand into the K-major hi/lo arrays: output row r (< rows)
+// of problem q holds op(X)(r, 0:K) zero-padded to Kp, where op(X)(r, k) is
+// X[off + r ld + k] (KMAJ) or X[off + k ld + r] (the transposed read goes
+// through a 32 x 33 shared tile so that both sides stay coalesced).
+// Grid: (row tiles of 32 x K tiles of 32 flattened, problems); 32 x 8 threads.
+struct SplitProb {
+  int rows, K, ld;
+  int64_t off;
+  int r0;  // first output row
+};
+
+template <bool KMAJ>
+__global__ void __launch_bounds__(256)
+tc_split_kernel(const SplitProb* __restrict__ probs, int Kp, const float* __restrict__ X,
+                float* __restrict__ hi, float* __restrict__ lo) {
+  __shared__ float t[32][33];
+  const SplitProb q = probs[blockIdx.y];
+  const int nkt = Kp / 32;
+  const int rt = blockIdx.x / nkt, kt = blockIdx.x % nkt;
+  const int rb = rt * 32, kb = kt * 32;
+  if (rb >= q.rows) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (KMAJ) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = rb + ty + 8 * i, k = kb + tx;
+      t[ty + 8 * i][tx] = (r < q.rows && k < q.K) ? X[q.off + (int64_t)r * q.ld + k] : 0.f;
+    }
+  } else {
+    // read X[k][r] with r contiguous, store transposed
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = kb + ty + 8 * i, r = rb + tx;
+      t[tx][ty + 8 * i] = (r < q.rows && k < q.K) ? X[q.off + (int64_t)k * q.ld + r] : 0.f;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = rb + ty + 8 * i, k = kb + tx;
+    if (r < q.rows) {
+      const float x = t[ty + 8 * i][tx];
+      const float h = tf32_round(x);
+      const int64_t o = (int64_t)(q.r0 + r) * Kp + k;
+      hi[o] = h;
+      lo[o] = tf32_round(x - h);
+    }
+  }
+}
+
+}  // namespace tc
+}  // namespace cbddc
+
+// ------------------------------------------------------------------ host
+namespace cbddc {
+namespace tc {
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependence on libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CB_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    CB_CHECK(q == cudaDriverEntryPointSuccess && p != nullptr, CBDDC_ECUDA,
+             "cuTensorMapEncodeTiled is not available from the driver");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D map of a K-major [rows][Kp] FP32 array: boxes of 32 (K) x 128 rows,
+// 128-byte swizzle, zero fill outside the array.
+inline CUtensorMap encode_kmajor(const float* base, int64_t rows, int Kp) {
+  CB_CHECK(Kp % BKC == 0 && Kp > 0 && rows > 0, CBDDC_EINVAL, "tensor map: bad K-major array shape");
+  CB_CHECK(((uintptr_t)base & 15) == 0, CBDDC_EINVAL, "tensor map: base not 16-byte aligned");
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)BKC, (cuuint32_t)BM};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides,
+                                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CB_CHECK(r == CUDA_SUCCESS, CBDDC_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return m;
+}
+
+inline void set_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    CB_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    done = true;
+  }
+}
+
+}  // namespace tc
+}  // namespace cbddc

@@ -59,7 +59,11 @@ _ENUMS = {
     "PRIMAL_R": "CBDDC_PRIMAL_R", "SCALING_COUNTING": "CBDDC_SCALING_COUNTING",
     "SCALING_DELUXE": "CBDDC_SCALING_DELUXE", "COARSE_GALERKIN": "CBDDC_COARSE_GALERKIN",
     "COARSE_PETROV": "CBDDC_COARSE_PETROV", "FIBER_SLAB_HELIX": "CBDDC_FIBER_SLAB_HELIX",
-    "FIBER_NODAL": "CBDDC_FIBER_NODAL",
+    "FIBER_NODAL": "CBDDC_FIBER_NODAL", "TIMER_SWEEP_GEMM": "CBDDC_TIMER_SWEEP_GEMM",
+    "TIMER_APPLY": "CBDDC_TIMER_APPLY", "TIMER_SETUP": "CBDDC_TIMER_SETUP",
+    "TIMER_LEVEL2_SETUP": "CBDDC_TIMER_LEVEL2_SETUP", "TIMER_LEVEL2_APPLY": "CBDDC_TIMER_LEVEL2_APPLY",
+    "TIMER_COARSE_SETUP": "CBDDC_TIMER_COARSE_SETUP", "TIMER_COARSE_APPLY": "CBDDC_TIMER_COARSE_APPLY",
+    "TIMER_SETUP_GEMM_F64": "CBDDC_TIMER_SETUP_GEMM_F64",
 }
 
 
