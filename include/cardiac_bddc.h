@@ -365,6 +365,7 @@ typedef struct {
   double res0;         /* ||F(d^{n,0})|| of the load step                    */
   float ms_assemble, ms_setup, ms_gmres, ms_total; /* CUDA-event times       */
   double gmres_relres; /* ||b - K delta|| / ||b|| of the tangent solve at exit */
+  int gmres_reorth;    /* Arnoldi steps that took a second Gram-Schmidt pass */
 } newton_record;
 
 typedef struct {

@@ -144,7 +144,7 @@ class _Record(ctypes.Structure):
         ("load", ctypes.c_double), ("newton", ctypes.c_int), ("gmres_its", ctypes.c_int),
         ("res", ctypes.c_double), ("res0", ctypes.c_double), ("ms_assemble", ctypes.c_float),
         ("ms_setup", ctypes.c_float), ("ms_gmres", ctypes.c_float), ("ms_total", ctypes.c_float),
-        ("gmres_relres", ctypes.c_double),
+        ("gmres_relres", ctypes.c_double), ("gmres_reorth", ctypes.c_int),
     ]
 
 

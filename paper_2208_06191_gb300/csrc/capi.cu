@@ -221,6 +221,7 @@ static int newton_step_impl(fem_problem* P, bddc_ctx** Cp, const solve_options* 
     rec->ms_gmres = ev.ms(3, 4);
     rec->ms_total = ev.ms(0, 4);
     rec->gmres_relres = rel;
+    rec->gmres_reorth = C->gm.reorth;
   }
   return gst;
 }

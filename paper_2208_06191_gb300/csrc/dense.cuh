@@ -386,9 +386,15 @@ void launch_tc(const GemmList& g, const float* A, const float* B, float* C, floa
   tc::tc_split_kernel<TB><<<gb, 256, 0, s>>>(g.spb.p, g.Kp, B, Bh, Bl);
   CB_LAUNCH();
   tc::set_smem_attr();
-  tc::tc_gemm_kernel<tc::STAGES><<<g.ntiles, tc::THREADS, tc::SMEM_BYTES, s>>>(g.tiles.p, g.tcp.p, g.maps[0], g.maps[1],
-                                                                     g.maps[2], g.maps[3], C, alpha, beta,
-                                                                     g.tc_status);
+  // rank-64 sweep updates (two K chunks) are bound by C's traffic: one
+  // operand stage and two C buffers; longer K: two stages, one C buffer
+  const int grid = tc::tc_grid(g.ntiles);
+  if (g.Kp <= 2 * tc::BKC)
+    tc::tc_gemm_kernel<1, 2><<<grid, tc::TC_THREADS, tc::TcSmem<1, 2>::bytes, s>>>(
+        g.tiles.p, g.ntiles, g.tcp.p, g.maps[0], g.maps[1], g.maps[2], g.maps[3], C, alpha, beta, g.tc_status);
+  else
+    tc::tc_gemm_kernel<2, 1><<<grid, tc::TC_THREADS, tc::TcSmem<2, 1>::bytes, s>>>(
+        g.tiles.p, g.ntiles, g.tcp.p, g.maps[0], g.maps[1], g.maps[2], g.maps[3], C, alpha, beta, g.tc_status);
   CB_LAUNCH();
 }
 

@@ -510,6 +510,7 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
   int total = 0;
   bool first = true;
   int* hflags = G.host_flags;
+  CB_CUDA(cudaMemsetAsync(G.flags.p + 3, 0, sizeof(int), s));  // second Gram-Schmidt passes
   bool converged = false;
   while (true) {
     // r = b - K x
@@ -526,7 +527,7 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
     scale_kernel<<<nb, 256, 0, s>>>(G.r.p, G.V.p, n, G.scal.p, 1, nullptr);
     CB_LAUNCH();
     CB_CUDA(cudaMemcpyAsync(G.host_scal, G.scal.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CB_CUDA(cudaMemcpyAsync(hflags, done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CB_CUDA(cudaMemcpyAsync(hflags, done, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CB_CUDA(cudaStreamSynchronize(s));
     first = false;
     *relres_out = G.host_scal[0];
@@ -574,7 +575,7 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
       // taken, is not counted): V read twice (dots, update), w read twice
       // and written once, v_{j+1} written
       timer_end(CBDDC_TIMER_ORTH, s, 4.0 * (j + 1) * (double)n, 8.0 * (double)n * (2.0 * (j + 1) + 4.0));
-      CB_CUDA(cudaMemcpyAsync(hflags, done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CB_CUDA(cudaMemcpyAsync(hflags, done, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
       CB_CUDA(cudaStreamSynchronize(s));
       ++total;
       if (hflags[0]) { ++j; break; }
@@ -599,6 +600,7 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
     // next cycle (or final check) recomputes the true residual
   }
   *iters_out = total;
+  G.reorth = hflags[3];
   return converged ? CBDDC_OK : CBDDC_ENOCONV;
 }
 

@@ -12,6 +12,7 @@ struct Gmres {
   int nchunks = 0;
   int pstride = 0;           // row stride of the per-CTA partial sums
   int hstride = 0;           // stride of the three CGS coefficient vectors in h
+  int reorth = 0;            // second Gram-Schmidt passes of the last solve
   DVec<double> V, Zb, w, r, H, cs, sn, g, y, h, partial, scal;
   DVec<int> flags;
   DVec<unsigned> ticket;

@@ -17,11 +17,15 @@
 //      zero-padded to a multiple of 32;
 //   2. one CTA per 128 x 128 output tile: a TMA producer thread streams
 //      K chunks of 32 (one 128-byte swizzled row per tile row; A_hi, A_lo,
-//      B_hi, B_lo = 64 KB per stage, 3 stages) into shared memory; one
+//      B_hi, B_lo = 64 KB per stage, 2 stages) into shared memory; one
 //      thread issues 3 x 4 tcgen05.mma (M = N = 128, K = 8) per chunk into a
 //      128-column TMEM accumulator and frees the stage with tcgen05.commit;
-//      after the last chunk the four warps read their 32 TMEM lanes
-//      (tcgen05.ld) and apply alpha / beta to C in global memory.
+//      meanwhile (beta != 0) the four warps copy the C tile into shared
+//      memory with 16-byte asynchronous copies, so its DRAM latency hides
+//      behind the operand loads and the MMAs; after the last chunk each
+//      warp reads its 32 TMEM lanes (tcgen05.ld), combines them with the
+//      staged C rows, and writes its rows back with warp-wide 512-byte
+//      stores.  The rank-64 sweep updates are bound by this C traffic.
 // Rows past a problem's M (or N) read other problems' rows or the
 // zero fill beyond the array; they only reach accumulator rows (columns)
 // that are never stored.
@@ -33,6 +37,8 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "common.h"
 
 namespace cbddc {
@@ -40,12 +46,12 @@ namespace tc {
 
 constexpr int BM = 128, BN = 128;             // output tile
 constexpr int BKC = 32;                       // K per chunk: 32 x 4 B = one 128-byte swizzle row
-constexpr int STAGES = 3;
 constexpr int OPND_BYTES = BM * BKC * 4;      // one operand tile of a chunk (16 KB)
 constexpr int STAGE_BYTES = 4 * OPND_BYTES;   // A_hi, A_lo, B_hi, B_lo
-constexpr int THREADS = 128;
-constexpr int TMEM_COLS = 128;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr int TC_THREADS = 192;               // GEMM: producer, MMA and four epilogue warps
+constexpr int TMEM_COLS = 128;                // one accumulator; the kernel holds two
+constexpr int CLD = BN + 4;                   // row pitch (floats) of the C tile in shared memory
+constexpr int C_BYTES = BM * CLD * 4;         // 67,584 B
 constexpr uint32_t kWaitLimit = 1u << 25;     // polls of one mbarrier before giving up
 
 // Instruction descriptor of kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
@@ -155,11 +161,29 @@ struct TcProb {
   int ar, br;
 };
 
-// The 128 x 128 tile (problem tl.x, tile row tl.y, tile column tl.z) of
-// C = alpha A B + beta C from the split operands.
-template <int NST>
-__global__ void __launch_bounds__(THREADS, 1)
-tc_gemm_kernel(const int4* __restrict__ tiles, const TcProb* __restrict__ probs,
+// Shared-memory footprint of the persistent kernel with NST operand stages
+// and NCB C-tile buffers.
+template <int NST, int NCB>
+struct TcSmem {
+  static constexpr int bytes = NST * STAGE_BYTES + NCB * C_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+};
+
+// Persistent grouped GEMM: CTA b takes the tiles b, b + gridDim.x, ... of the
+// list ({problem, tile row, tile column}), each C = alpha A B + beta C.
+// Warp roles (192 threads):
+//   warp 0, one lane: TMA producer of the operand chunks (NST-stage ring);
+//   warp 1, one lane: MMA issuer into one of two 128-column TMEM
+//     accumulators (tile i uses accumulator i % 2, so the MMAs of tile i + 1
+//     run while tile i is written back);
+//   warps 2-5: epilogue; warp w owns TMEM lanes (tile rows) 32 (w % 4) ..
+//     + 31.  It stages the C rows of tile i + 1 in shared memory with
+//     16-byte asynchronous copies (NCB = 2 buffers) while it combines and
+//     stores tile i, so C's DRAM traffic overlaps the rest.
+// Barriers: full/empty per operand stage, tmem_full/tmem_empty per
+// accumulator (tmem_empty counts the four epilogue warps).
+template <int NST, int NCB>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_gemm_kernel(const int4* __restrict__ tiles, int ntiles, const TcProb* __restrict__ probs,
                const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
                float* __restrict__ C, float alpha, float beta, int* __restrict__ status) {
@@ -167,31 +191,32 @@ tc_gemm_kernel(const int4* __restrict__ tiles, const TcProb* __restrict__ probs,
   // 1024-byte aligned operand stages (the swizzle pattern repeats every 1 KB)
   const uint32_t base = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (base & 1023u)) & 1023u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * STAGE_BYTES);
+  float* Cbuf = reinterpret_cast<float*>(smem + NST * STAGE_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * STAGE_BYTES + NCB * C_BYTES);
   uint64_t* empty = full + NST;
-  uint64_t* accum = empty + NST;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* tfull = empty + NST;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-
-  const int4 tl = tiles[blockIdx.x];
-  const TcProb p = probs[tl.x];
-  const int m0 = tl.y * BM, n0 = tl.z * BN;
-  const int nk = (p.K + BKC - 1) / BKC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntl = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(2 * TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -200,68 +225,125 @@ tc_gemm_kernel(const int4* __restrict__ tiles, const TcProb* __restrict__ probs,
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  int issued = 0;  // chunks whose copies the producer issued
-  if (warp == 0 && lane == 0 && nk > 0) {
-    // TMA producer
-    for (int c = 0; c < nk; ++c) {
-      const int s = c % NST;
-      if (c >= NST && !mbar_wait(&empty[s], ((c / NST) - 1) & 1)) {
-        atomicExch(abort_flag, 1);
-        break;
+  int issued = 0;  // operand chunks whose copies the producer issued
+  if (warp == 0) {
+    if (lane == 0) {
+      int g = 0;
+      for (int i = 0; i < ntl && !*(volatile int*)abort_flag; ++i) {
+        const int4 tl = tiles[blockIdx.x + i * gridDim.x];
+        const TcProb p = probs[tl.x];
+        const int nk = (p.K + BKC - 1) / BKC;
+        const int ya = p.ar + tl.y * BM, yb = p.br + tl.z * BN;
+        for (int c = 0; c < nk; ++c, ++g) {
+          const int s = g % NST;
+          if (g >= NST && !mbar_wait(&empty[s], ((g / NST) - 1) & 1)) {
+            atomicExch(abort_flag, 1);
+            break;
+          }
+          uint8_t* st = smem + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_2d(st, &mAh, c * BKC, ya, &full[s]);
+          tma_load_2d(st + OPND_BYTES, &mAl, c * BKC, ya, &full[s]);
+          tma_load_2d(st + 2 * OPND_BYTES, &mBh, c * BKC, yb, &full[s]);
+          tma_load_2d(st + 3 * OPND_BYTES, &mBl, c * BKC, yb, &full[s]);
+          issued = g + 1;
+        }
       }
-      if (*(volatile int*)abort_flag) break;
-      uint8_t* st = smem + s * STAGE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_2d(st, &mAh, c * BKC, p.ar + m0, &full[s]);
-      tma_load_2d(st + OPND_BYTES, &mAl, c * BKC, p.ar + m0, &full[s]);
-      tma_load_2d(st + 2 * OPND_BYTES, &mBh, c * BKC, p.br + n0, &full[s]);
-      tma_load_2d(st + 3 * OPND_BYTES, &mBl, c * BKC, p.br + n0, &full[s]);
-      issued = c + 1;
     }
-  } else if (warp == 1 && lane == 0 && nk > 0) {
-    // MMA issuer: 4 K-steps of 8 per chunk, three products per step
-    for (int c = 0; c < nk; ++c) {
-      const int s = c % NST;
-      if (!mbar_wait(&full[s], (c / NST) & 1)) {
-        atomicExch(abort_flag, 1);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int g = 0;
+      for (int i = 0; i < ntl && !*(volatile int*)abort_flag; ++i) {
+        const int4 tl = tiles[blockIdx.x + i * gridDim.x];
+        const int nk = (probs[tl.x].K + BKC - 1) / BKC;
+        const int a = i & 1;
+        if (i >= 2 && !mbar_wait(&tempty[a], ((i >> 1) - 1) & 1)) {
+          atomicExch(abort_flag, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(a * TMEM_COLS);
+        bool ok = true;
+        for (int c = 0; c < nk; ++c, ++g) {
+          const int s = g % NST;
+          if (!mbar_wait(&full[s], (g / NST) & 1)) {
+            atomicExch(abort_flag, 1);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
 #pragma unroll
-      for (int k = 0; k < BKC / 8; ++k) {
-        const uint64_t ah = sw128_desc(st + 32 * k);
-        const uint64_t al = sw128_desc(st + OPND_BYTES + 32 * k);
-        const uint64_t bh = sw128_desc(st + 2 * OPND_BYTES + 32 * k);
-        const uint64_t bl = sw128_desc(st + 3 * OPND_BYTES + 32 * k);
-        mma_tf32(tmem, al, bh, (c > 0 || k > 0) ? 1u : 0u);
-        mma_tf32(tmem, ah, bl, 1u);
-        mma_tf32(tmem, ah, bh, 1u);
+          for (int k = 0; k < BKC / 8; ++k) {
+            const uint64_t ah = sw128_desc(st + 32 * k);
+            const uint64_t al = sw128_desc(st + OPND_BYTES + 32 * k);
+            const uint64_t bh = sw128_desc(st + 2 * OPND_BYTES + 32 * k);
+            const uint64_t bl = sw128_desc(st + 3 * OPND_BYTES + 32 * k);
+            mma_tf32(acc, al, bh, (c > 0 || k > 0) ? 1u : 0u);
+            mma_tf32(acc, ah, bl, 1u);
+            mma_tf32(acc, ah, bh, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(&tfull[a]);  // also after an abort: the epilogue must not wait forever
+        if (!ok) break;
       }
-      mma_commit(&empty[s]);
     }
-    mma_commit(accum);
-  }
-  __syncwarp();
-
-  // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31
-  bool ok = nk > 0 && mbar_wait(accum, 0);
-  if (!ok) atomicExch(abort_flag, 1);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncthreads();
-  const bool aborted = *(volatile int*)abort_flag != 0;
-  if (!aborted) {
-    const int row = m0 + warp * 32 + lane;
-    float* crow = C + p.c + (int64_t)row * p.ldc;
-    const bool vec = ((p.c & 3) == 0) && ((p.ldc & 3) == 0);
+  } else {
+    // epilogue warps
+    const int wq = warp & 3;
+    const int wrow0 = 32 * wq;
+    auto prefetch = [&](int i) {
+      const int4 tl = tiles[blockIdx.x + i * gridDim.x];
+      const TcProb p = probs[tl.x];
+      if (beta == 0.f || (p.c & 3) || (p.ldc & 3)) return;
+      float* Cs = Cbuf + (i % NCB) * (BM * CLD);
+      const int m0 = tl.y * BM, n0 = tl.z * BN;
+      for (int r = 0; r < 32; ++r) {
+        const int lr = wrow0 + r, gr = m0 + lr, gc = n0 + 4 * lane;
+        const int valid = (gr < p.M) ? max(0, min(4, p.N - gc)) : 0;
+        const float* src = valid > 0 ? C + p.c + (int64_t)gr * p.ldc + gc : C;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(Cs + lr * CLD + 4 * lane)),
+                     "l"(src), "r"(valid * 4)
+                     : "memory");
+      }
+    };
+    if (ntl > 0) prefetch(0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int i = 0; i < ntl; ++i) {
+      const bool ahead = NCB == 2 && i + 1 < ntl;
+      const int4 tl = tiles[blockIdx.x + i * gridDim.x];
+      const TcProb p = probs[tl.x];
+      const int m0 = tl.y * BM, n0 = tl.z * BN;
+      const int a = i & 1;
+      const bool cvec = ((p.c & 3) == 0) && ((p.ldc & 3) == 0);
+      // the next tile's C rows go to the other buffer (NCB = 2) while this
+      // one is finished; with one buffer they are fetched after the stores
+      if (ahead) {
+        prefetch(i + 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
+      const bool ok = mbar_wait(&tfull[a], (i >> 1) & 1);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // this tile's C rows have landed (only the next tile's copies may
+      // still be pending)
+      if (ahead) asm volatile("cp.async.wait_group 1;" ::: "memory");
+      else asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncwarp();
+      if (!ok || *(volatile int*)abort_flag) {
+        atomicExch(abort_flag, 1);
+        break;
+      }
+      const uint32_t acc = tmem + (uint32_t)(a * TMEM_COLS) + ((uint32_t)wrow0 << 16);
+      float* Cs = Cbuf + (i % NCB) * (BM * CLD);
+      const int lr = wrow0 + lane;
+      if (cvec) {
+        float* crow_s = Cs + lr * CLD;
 #pragma unroll 1
-    for (int cc = 0; cc < BN / 32; ++cc) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
-      const int nb = n0 + cc * 32;
-      if (row < p.M && nb < p.N) {
-        if (vec && nb + 32 <= p.N) {
-          float4* c4 = reinterpret_cast<float4*>(crow + nb);
+        for (int cc = 0; cc < BN / 32; ++cc) {
+          float v[32];
+          tmem_ld32(acc + (uint32_t)(cc * 32), v);
+          float4* c4 = reinterpret_cast<float4*>(crow_s + cc * 32);
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             float4 o;
@@ -270,32 +352,71 @@ tc_gemm_kernel(const int4* __restrict__ tiles, const TcProb* __restrict__ probs,
               o = make_float4(alpha * v[4 * q] + beta * old.x, alpha * v[4 * q + 1] + beta * old.y,
                               alpha * v[4 * q + 2] + beta * old.z, alpha * v[4 * q + 3] + beta * old.w);
             } else {
-              o = make_float4(alpha * v[4 * q], alpha * v[4 * q + 1], alpha * v[4 * q + 2], alpha * v[4 * q + 3]);
+              o = make_float4(alpha * v[4 * q], alpha * v[4 * q + 1], alpha * v[4 * q + 2],
+                              alpha * v[4 * q + 3]);
             }
             c4[q] = o;
           }
-        } else {
-          for (int q = 0; q < 32 && nb + q < p.N; ++q) {
-            float* cp = crow + nb + q;
-            *cp = (beta != 0.f) ? alpha * v[q] + beta * *cp : alpha * v[q];
+        }
+      } else {
+        // unaligned C: each thread updates its own row in global memory
+        const int row = m0 + lr;
+        float* crow = C + p.c + (int64_t)row * p.ldc;
+#pragma unroll 1
+        for (int cc = 0; cc < BN / 32; ++cc) {
+          float v[32];
+          tmem_ld32(acc + (uint32_t)(cc * 32), v);
+          const int nb = n0 + cc * 32;
+          if (row < p.M && nb < p.N) {
+            for (int q = 0; q < 32 && nb + q < p.N; ++q) {
+              float* cp = crow + nb + q;
+              *cp = (beta != 0.f) ? alpha * v[q] + beta * *cp : alpha * v[q];
+            }
           }
         }
       }
+      // accumulator a is free once this warp's TMEM reads are done
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[a])) : "memory");
+      if (cvec) {
+        for (int r = 0; r < 32; ++r) {
+          const int lr2 = wrow0 + r, gr = m0 + lr2, gc = n0 + 4 * lane;
+          if (gr >= p.M || gc >= p.N) continue;
+          float* dst = C + p.c + (int64_t)gr * p.ldc + gc;
+          const float4 o = *reinterpret_cast<const float4*>(Cs + lr2 * CLD + 4 * lane);
+          if (gc + 4 <= p.N) {
+            *reinterpret_cast<float4*>(dst) = o;
+          } else {
+            dst[0] = o.x;
+            if (gc + 1 < p.N) dst[1] = o.y;
+            if (gc + 2 < p.N) dst[2] = o.z;
+          }
+        }
+      }
+      __syncwarp();
+      if (NCB == 1 && i + 1 < ntl) {
+        prefetch(i + 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
     }
-  } else if (threadIdx.x == 0 && nk > 0) {
-    atomicOr(status, DEV_TIMEOUT);
+    asm volatile("cp.async.wait_all;" ::: "memory");
   }
-  // an aborted producer's copies may still be in flight: wait (bounded) for
-  // the stages it filled before the shared memory is released
-  if (aborted && warp == 0 && lane == 0) {
-    for (int c = (issued > NST ? issued - NST : 0); c < issued; ++c)
-      (void)mbar_wait(&full[c % NST], (c / NST) & 1);
+  __syncwarp();
+  if (*(volatile int*)abort_flag != 0) {
+    if (threadIdx.x == 0) atomicOr(status, DEV_TIMEOUT);
+    // copies the producer issued may still be in flight: wait (bounded)
+    // for the stages it filled before the shared memory is released
+    if (warp == 0 && lane == 0)
+      for (int g = (issued > NST ? issued - NST : 0); g < issued; ++g)
+        (void)mbar_wait(&full[g % NST], (g / NST) & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS)
+                 : "memory");
   }
 }
 
@@ -395,9 +516,23 @@ inline CUtensorMap encode_kmajor(const float* base, int64_t rows, int Kp) {
 inline void set_smem_attr() {
   static bool done = false;
   if (!done) {
-    CB_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    CB_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TcSmem<1, 2>::bytes));
+    CB_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TcSmem<2, 1>::bytes));
     done = true;
   }
+}
+
+// Persistent CTAs: one per SM (one fits), never more than tiles.
+inline int tc_grid(int ntiles) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    CB_CUDA(cudaGetDevice(&dev));
+    CB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return std::max(1, std::min(ntiles, sms));
 }
 
 }  // namespace tc
