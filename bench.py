@@ -1,18 +1,21 @@
 #!/usr/bin/env python
 """Newton-step BDDC-GMRES solve time on one GB300, FP32-local vs FP64.
 
-Workload: the 48x48x12 trilinear (Q1) hexahedral slab [0,4]x[0,4]x[0,1]
-(86,436 free DoFs) cut into 4x4x4 = 64 box subdomains, vertex + edge-average
-primal space, Guccione + active stress at half the peak activation and a
-1 kPa follower pressure on the top face, z = 0 clamped, 4 load steps.
+Default workload: the idealised left ventricle with quadratic P2 tetrahedra
+(3,004,479 free DoFs), 4096 uneven level-1 subdomains (2048 surface patches
+x 2 transmural slabs, sizes +-30%) nested in 64 level-2 subdomains,
+three-level BDDC with primal space VEF on both levels and an FP64 coarsest
+solve, Guccione + active stress, follower endocardial pressure, clamped
+base, 8 load steps.
 
 A step is one Newton step of the solve (residual and tangent assembly,
-BDDC setup, GMRES to 1e-8 relative residual, update).  The timed steps
-replay, in order, the Newton states of a full solve computed untimed
-beforehand, so the mean over a full cycle is the mean time per Newton step
-of the whole solve.  The primary value uses FP32 local operators (FP64
-assembly, GMRES, vectors and coarse solve); the FP64 path is timed beside
-it.
+BDDC setup, FGMRES to 1e-8 relative residual, update).  The timed steps
+replay, in order and cyclically, the Newton states of the first load steps
+of a solve computed untimed beforehand (which load steps is part of the
+workload description printed in ``config``).  The primary value uses FP32
+local operators (FP64 assembly, GMRES, vectors and coarsest solve); the
+FP64 path is timed on a subset of the same states, and the speedup pairs
+the two precisions state by state.
 
 Multi-GPU: the path does not shard across GPUs in this build; N ranks run N
 independent replicas (weak scaling) and the time is the max over ranks.
@@ -23,6 +26,7 @@ host cores instead, on a bounded sample of the same workload.
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -35,36 +39,15 @@ if ROOT not in sys.path:
 
 METRIC = "Newton-step BDDC-GMRES solve time, FP32-local vs FP64, at 1e-8 rel residual"
 UNIT = "ms/Newton step"
-WORKLOAD = "slab48_q1"
+WORKLOAD = "lv_p2"
 
-# name -> (description, problem builder, BDDC levels, level-2 groups, load
-# steps whose Newton states are replayed (None: all), FP64 steps timed
-# (None: one per replayed state, so both precisions see the same states))
-WORKLOADS = {
-    "slab48_q1": ("48x48x12 Q1 hex slab [0,4]x[0,4]x[0,1], 64 box subdomains (4x4x4), primal VE, "
-                  "n_free=86436, follower pressure 1 kPa + activation 30 kPa, 4 load steps",
-                  lambda: __import__("workloads").slab_config("slab48_q1"), 2, None, None, 3),
-    "slab24_q2": ("24x24x6 Q2 hex slab [0,4]x[0,4]x[0,1], 64 box subdomains (8x4x2), primal VEF, "
-                  "n_free=86436, follower pressure 1 kPa + activation 30 kPa, 4 load steps",
-                  lambda: __import__("workloads").slab_config("slab24_q2"), 2, None, None, 3),
-    "lv_p1": ("left-ventricle shell, P1 tets, ~1.0M free DoFs, 512 uneven subdomains (+-30%), "
-              "primal VEF, two-level (dense FP64 coarse), endocardial pressure 2 kPa + activation "
-              "15 kPa over 8 load steps; Newton states of the first load step",
-              lambda: __import__("workloads").lv_config("lv_p1"), 2, None, 1, None),
-    "lv_p1_ml": ("left-ventricle shell, P1 tets, ~1.0M free DoFs, 512 uneven subdomains (+-30%) "
-                 "nested in 16 level-2 subdomains, three-level BDDC, primal VEF/VEF, pressure 2 kPa "
-                 "+ activation 15 kPa over 8 load steps; Newton states of the first load step",
-                 lambda: __import__("workloads").lv_config("lv_p1", n_parts2=16), 3, 16, 1, None),
-    "lv_p2": ("left-ventricle shell, P2 tets, ~3.0M free DoFs, 4096 uneven subdomains (2048 "
-              "surface patches x 2 slabs) nested in 64 level-2 subdomains, three-level BDDC, "
-              "primal VEF/VEF, FP64 coarsest solve, pressure 2 kPa + activation 15 kPa over 8 "
-              "load steps; Newton states of the first load step",
-              lambda: __import__("workloads").lv_config("lv_p2"), 3, 64, 1, None),
-}
-WORKLOADS["slab48_q1_ver"] = ("48x48x12 Q1 hex slab as slab48_q1 with primal VE plus the rotations "
-                              "of every edge (rigid-body primal constraints)",
-                              lambda: __import__("workloads").slab_config("slab48_q1", primal="VER"),
-                              2, None, None, 3)
+
+def _slab(name, **kw):
+    return lambda: __import__("workloads").slab_config(name, **kw)
+
+
+def _lv(name, **kw):
+    return lambda: __import__("workloads").lv_config(name, **kw)
 
 
 def _with_scaling(build, scaling):
@@ -75,24 +58,58 @@ def _with_scaling(build, scaling):
     return f
 
 
-WORKLOADS["slab48_q1_dlx"] = ("48x48x12 Q1 hex slab as slab48_q1 (primal VE) with deluxe scaling",
-                              _with_scaling(WORKLOADS["slab48_q1"][1], "deluxe"), 2, None, None, 3)
-WORKLOADS["lv_p1_dlx"] = (WORKLOADS["lv_p1"][0] + "; deluxe scaling",
-                          _with_scaling(WORKLOADS["lv_p1"][1], "deluxe"), 2, None, 1, None)
-# reduced ventricles (same generator, 5 x 64 x 32 rings, 64 subdomains) for
-# profiler captures that must stay a few GB on the device
-WORKLOADS["lv_p1_small"] = ("left-ventricle shell, P1 tets, 5 x 64 x 32 rings, 64 subdomains",
-                            lambda: __import__("workloads").lv_problem(
-                                nt=5, ntheta=64, nu=32, order=1, n_parts=64, load_steps=8,
-                                gamma=0.25 * 6.0e4), 2, None, 1, 1)
-WORKLOADS["lv_p2_small"] = ("left-ventricle shell, P2 tets, 5 x 64 x 32 rings, 128 subdomains "
-                            "(64 patches x 2 slabs) in 8 level-2 subdomains",
-                            lambda: __import__("workloads").lv_problem(
-                                nt=5, ntheta=64, nu=32, order=2, n_parts=128, n_parts2=8,
-                                n_layers=2, load_steps=8, gamma=0.25 * 6.0e4), 3, 8, 1, 1)
-WORKLOADS["lv_p1_small_dlx"] = (WORKLOADS["lv_p1_small"][0] + "; deluxe scaling",
-                                _with_scaling(WORKLOADS["lv_p1_small"][1], "deluxe"), 2, None, 1, 1)
-WORKLOAD_DESC = WORKLOADS[WORKLOAD][0]
+# name -> workload: description, problem builder, BDDC levels, GMRES restart,
+# load steps whose Newton states are replayed (None: all), FP64 states timed
+W = {}
+W["lv_p2"] = dict(
+    desc="left-ventricle shell, P2 tets, 3,004,479 free DoFs, 4096 uneven subdomains (2048 surface "
+         "patches x 2 slabs, +-30%) nested in 64 level-2 subdomains, three-level BDDC, primal VEF/VEF, "
+         "FP64 coarsest solve, endocardial follower pressure 2 kPa + activation 15 kPa over 8 load "
+         "steps; the Newton states of load steps 1-2 (load 1/8 and 2/8) replayed",
+    build=_lv("lv_p2"), levels=3, restart=1000, n_load=2, fp64_states=4, n_parts=4096, its_ref=300)
+W["lv_p1"] = dict(
+    desc="left-ventricle shell, P1 tets, 1,007,235 free DoFs, 512 uneven subdomains (+-30%), primal "
+         "VEF, two-level (dense FP64 coarse), endocardial pressure 2 kPa + activation 15 kPa over 8 load "
+         "steps; the Newton states of load steps 1-2 replayed",
+    build=_lv("lv_p1"), levels=2, restart=1000, n_load=2, fp64_states=4, n_parts=512, its_ref=150)
+W["slab48_q1"] = dict(
+    desc="48x48x12 Q1 hex slab [0,4]x[0,4]x[0,1], 64 box subdomains (4x4x4), primal VE, n_free=86436, "
+         "follower pressure 1 kPa + activation 30 kPa, 4 load steps; every Newton state of the solve",
+    build=_slab("slab48_q1"), levels=2, restart=100, n_load=None, fp64_states=None)
+W["slab24_q2"] = dict(
+    desc="24x24x6 Q2 hex slab [0,4]x[0,4]x[0,1], 64 box subdomains (8x4x2), primal VEF, n_free=86436, "
+         "follower pressure 1 kPa + activation 30 kPa, 4 load steps; every Newton state of the solve",
+    build=_slab("slab24_q2"), levels=2, restart=100, n_load=None, fp64_states=None)
+W["lv_p1_ml"] = dict(
+    desc="left-ventricle shell, P1 tets, 1,007,235 free DoFs, 512 uneven subdomains nested in 16 level-2 "
+         "subdomains, three-level BDDC, primal VEF/VEF; Newton states of load steps 1-2",
+    build=_lv("lv_p1", n_parts2=16), levels=3, restart=1000, n_load=2, fp64_states=4, n_parts=512,
+    its_ref=150)
+W["slab48_q1_ver"] = dict(
+    desc="48x48x12 Q1 hex slab as slab48_q1 with primal VE plus the rotations of every edge",
+    build=_slab("slab48_q1", primal="VER"), levels=2, restart=100, n_load=None, fp64_states=3)
+W["slab48_q1_dlx"] = dict(
+    desc="48x48x12 Q1 hex slab as slab48_q1 (primal VE) with deluxe scaling",
+    build=_with_scaling(_slab("slab48_q1"), "deluxe"), levels=2, restart=100, n_load=None, fp64_states=3)
+W["lv_p2_dlx"] = dict(
+    desc=W["lv_p2"]["desc"] + "; deluxe scaling on level 1",
+    build=_with_scaling(_lv("lv_p2"), "deluxe"), levels=3, restart=1000, n_load=2, fp64_states=2,
+    n_parts=4096, its_ref=300)
+# reduced ventricles (same generator) for profiler captures that must stay a
+# few GB on the device
+W["lv_p1_small"] = dict(
+    desc="left-ventricle shell, P1 tets, 5 x 64 x 32 rings, 64 subdomains",
+    build=lambda: __import__("workloads").lv_problem(nt=5, ntheta=64, nu=32, order=1, n_parts=64,
+                                                     load_steps=8, gamma=0.25 * 6.0e4),
+    levels=2, restart=300, n_load=1, fp64_states=1, n_parts=64, its_ref=90)
+W["lv_p2_small"] = dict(
+    desc="left-ventricle shell, P2 tets, 5 x 64 x 32 rings, 128 subdomains (64 patches x 2 slabs) in 8 "
+         "level-2 subdomains",
+    build=lambda: __import__("workloads").lv_problem(nt=5, ntheta=64, nu=32, order=2, n_parts=128,
+                                                     n_parts2=8, n_layers=2, load_steps=8,
+                                                     gamma=0.25 * 6.0e4),
+    levels=3, restart=300, n_load=1, fp64_states=1, n_parts=128, its_ref=90)
+WORKLOADS = W
 
 
 def _parse():
@@ -101,11 +118,12 @@ def _parse():
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-states", type=int, default=None,
+                    help="FP64 states timed (default: the workload's setting)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-budget-s", type=float, default=150.0)
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--max-gmres", type=int, default=1000)
+    ap.add_argument("--max-gmres", type=int, default=3000)
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
                     help="kernels: one BDDC setup and a few applies and SpMVs of the workload "
                          "(a short program for profiler captures)")
@@ -178,12 +196,8 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
+            if len(parts) >= 9:
                 rows.append(parts)
-            except Exception:
-                pass
         os.unlink(self.path)
         if not rows:
             return None
@@ -204,101 +218,188 @@ def _peaks():
         return {}
 
 
-def _oracle_step_seconds(timeout):
-    """One oracle Newton step (d = 0, lambda = 1/4) of the workload, in a
-    fresh single-threaded Python process; returns (seconds, gmres its)."""
-    code = r"""
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+# ------------------------------------------------------- the oracle on the CPU
+#
+# Slabs: one full oracle Newton step of the workload (d = 0, first load
+# level) in a fresh process.  Ventricles (far too large for the oracle): a
+# sample of 16 level-1 subdomains of the workload that touch the clamped
+# base, with their elements, loads and clamped nodes (workloads.
+# lv_part_problem), through the oracle's assembly, BDDC setup and three
+# GMRES iterations; the Newton step of the whole workload is extrapolated as
+# (subdomains / 16) x (assembly + setup + iterations x time per iteration),
+# with the GMRES iterations of the GPU's FP32 path.  Linear scaling in the
+# number of subdomains favours the CPU (the oracle's setup and apply grow
+# faster than that), and so does leaving out its coarse levels.
+
+SAMPLE_PARTS = 16
+
+_ORACLE_STEP = r"""
 import json, sys, time
-sys.path.insert(0, %r)
+sys.path.insert(0, %(root)r)
 import numpy as np
-from workloads import slab_config
+import workloads
 from oracle.assembly import FEProblem
 from oracle.bddc import BDDC, Classification
 from oracle.krylov import gmres
-prob = slab_config(%r)
+name, first = %(name)r, %(first)d
+if name.startswith("slab"):
+    prob = workloads.slab_config(name)
+    maxit = 3000
+else:
+    full = workloads.lv_config(name)
+    cp = workloads.clamped_parts(full)
+    parts = [cp[(first + i) %% len(cp)] for i in range(%(nparts)d)]
+    prob = workloads.lv_part_problem(full, parts)
+    maxit = 3
+t0 = time.perf_counter()
 fe = FEProblem(prob)
 cl = Classification(fe, prob["elem_part"], prob["n_parts"])
 d = np.zeros(fe.n_free)
 lam = 1.0 / prob["load_steps"]
-t0 = time.perf_counter()
+t1 = time.perf_counter()
 r = fe.residual(d, lam)
 K, (Ke, Kf) = fe.tangent(d, lam)
+t2 = time.perf_counter()
 pc = BDDC(fe, Ke, Kf, prob["primal"], cl)
-x, its, _ = gmres(lambda v: K @ v, -r, pc.apply, tol=1e-8)
+t3 = time.perf_counter()
+x, its, _ = gmres(lambda v: K @ v, -r, pc.apply, tol=1e-8, restart=1000, maxiter=maxit)
 d = d + x
-t1 = time.perf_counter()
-print(json.dumps({"seconds": t1 - t0, "its": its}))
-""" % (ROOT, WORKLOAD)
+t4 = time.perf_counter()
+print(json.dumps({"prep": t1 - t0, "assemble": t2 - t1, "setup": t3 - t2, "gmres": t4 - t3,
+                  "its": its, "n_free": fe.n_free}))
+"""
+
+
+def _oracle_proc(name, first, threads):
+    code = _ORACLE_STEP % {"root": ROOT, "name": name, "first": first, "nparts": SAMPLE_PARTS}
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=timeout)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    out = json.loads(r.stdout.strip().splitlines()[-1])
-    return out["seconds"], out["its"]
+        env[k] = str(threads)
+    return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                            text=True, env=env)
+
+
+def _collect(proc, timeout):
+    out, err = proc.communicate(timeout=timeout)
+    if proc.returncode != 0:
+        raise RuntimeError(err[-2000:])
+    return json.loads(out.strip().splitlines()[-1])
+
+
+def _extrapolate(name, s, its):
+    """ms per Newton step of the whole workload from one sample."""
+    if name.startswith("slab"):
+        return 1000.0 * (s["assemble"] + s["setup"] + s["gmres"])
+    n_parts = int(WORKLOADS[name]["n_parts"])
+    per_it = s["gmres"] / max(1, s["its"])
+    return 1000.0 * (n_parts / SAMPLE_PARTS) * (s["assemble"] + s["setup"] + its * per_it)
+
+
+def _sample_text(name, s, its):
+    if name.startswith("slab"):
+        return ("one full oracle Newton step of %s at d=0, load 1/4 (%d GMRES its), single-threaded, "
+                "fresh process" % (name, s["its"]))
+    n_parts = int(WORKLOADS[name]["n_parts"])
+    return ("oracle assembly, BDDC setup and %d GMRES iterations (d=0, load 1/8) on %d clamped level-1 "
+            "subdomains of %s (%d free DoFs), extrapolated x%d to the workload's %d subdomains with %.0f "
+            "GMRES iterations per Newton step; linear in the subdomain count and without the oracle's "
+            "coarse levels (both favour the CPU)"
+            % (s["its"], SAMPLE_PARTS, name, s["n_free"], n_parts // SAMPLE_PARTS, n_parts, its))
+
+
+def oracle_baseline(name, its, all_cores=True, timeout=900):
+    """(single-thread ms/Newton step, all-cores ms/Newton step, cores used,
+    sample description) of the oracle on the workload."""
+    ncpu = os.cpu_count() or 1
+    s = _collect(_oracle_proc(name, 0, 1), timeout)
+    single = _extrapolate(name, s, its)
+    sample = _sample_text(name, s, its)
+    allc, cores = None, 1
+    if all_cores and ncpu > 1:
+        # all host cores: independent samples (different subdomains) in
+        # parallel, one process per core; the per-subdomain loops of the
+        # oracle's setup and apply parallelise the same way
+        procs = [_oracle_proc(name, SAMPLE_PARTS * i, 1) for i in range(ncpu)]
+        t0 = time.perf_counter()
+        res = [_collect(p, timeout) for p in procs]
+        wall = time.perf_counter() - t0
+        work = sum(r["prep"] + r["assemble"] + r["setup"] + r["gmres"] for r in res)
+        eff = work / (ncpu * wall)
+        allc = single / (ncpu * eff)
+        cores = ncpu
+        sample += ("; all cores: %d samples in parallel, one per core, parallel efficiency %.2f"
+                   % (ncpu, eff))
+    return single, allc, cores, sample
 
 
 def run_reference(args, world, rank):
-    """The oracle on the host cores: each step is one full oracle Newton step
-    of the workload at d = 0, lambda = 1/4; the number of timed steps is
+    """The oracle on the host cores: each step is one oracle sample of the
+    workload (see oracle_baseline), single-threaded, extrapolated with the
+    workload's recorded GMRES iteration count; the number of timed steps is
     capped so that the run stays within the time budget."""
     if rank != 0:
         return
-    times, its = [], []
+    spec = WORKLOADS[args.workload]
+    its = spec.get("its_ref", 0)
+    times = []
+    sample = ""
     t_start = time.perf_counter()
     while len(times) < max(1, args.steps):
-        s, i = _oracle_step_seconds(timeout=args.oracle_budget_s * 4)
-        times.append(s)
-        its.append(i)
-        if time.perf_counter() - t_start + s > args.oracle_budget_s:
+        t_one = time.perf_counter()
+        s = _collect(_oracle_proc(args.workload, SAMPLE_PARTS * len(times), 1), 900)
+        times.append(_extrapolate(args.workload, s, its))
+        sample = _sample_text(args.workload, s, its)
+        if time.perf_counter() - t_start + (time.perf_counter() - t_one) > args.oracle_budget_s:
             break
-    ms = 1000.0 * statistics.mean(times)
-    sample = ("full oracle Newton step (assembly, BDDC setup with SciPy LU, GMRES to 1e-8) of %s "
-              "at d=0, lambda=1/4, single-threaded, %d step(s) timed of %d requested, no warm-up "
-              "(each step runs in a fresh process)" % (WORKLOAD, len(times), args.steps))
+    ms = statistics.mean(times)
+    sample += "; %d sample(s) timed of %d steps requested, no warm-up" % (len(times), args.steps)
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
         "steps": len(times), "warmup": 0, "steps_requested": args.steps,
         "warmup_requested": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "gmres_its": its},
-        "cpu_baseline": {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": spec["desc"], "workload_name": args.workload},
+        "cpu_baseline": {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu_model": _cpu_model()},
         "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, world, rank, local):
-    import numpy as np
-    import torch
+# ------------------------------------------------------------ the GPU path
+TIMER_CLASSES = ("SWEEP_GEMM", "ELEMENT", "APPLY", "SPMV", "ORTH", "SETUP", "LEVEL2_SETUP", "LEVEL2_APPLY",
+                 "COARSE_SETUP", "COARSE_APPLY", "SETUP_GEMM_F64")
 
-    import paper_2208_06191_gb300 as pkg
 
-    if world == 1:
-        torch.cuda.set_device(local)
-    pkg.build()
-    pkg.load_library()
-    desc, build_prob, levels, _groups, n_load_rec, fp64_default = WORKLOADS[args.workload]
-    prob = build_prob()
-    P = pkg.Problem(prob)
-    n = P.n_free
+def _opts(pkg, prob, spec, precision, max_gmres):
     ml = {}
-    if levels == 3:
+    if spec["levels"] == 3:
         ml = dict(levels=3, part2=prob["part2"], n_parts2=prob["n_parts2"], primal2="VEF")
-    scaling = prob.get("scaling", "counting")
-    opts32 = pkg.SolveOptions(precision=pkg.FP32, primal=prob["primal"], max_gmres=args.max_gmres,
-                              precision2=pkg.FP32, scaling=scaling, **ml)
-    opts64 = pkg.SolveOptions(precision=pkg.FP64, primal=prob["primal"], max_gmres=args.max_gmres,
-                              precision2=pkg.FP64, scaling=scaling, **ml)
+    return pkg.SolveOptions(precision=precision, primal=prob["primal"], max_gmres=max_gmres,
+                            restart=spec["restart"], precision2=precision,
+                            scaling=prob.get("scaling", "counting"), **ml)
 
-    # untimed: Newton states of a full FP32 solve (or of its first load steps)
-    states = []
+
+def newton_states(P, prob, opts, n_load, torch):
+    """Untimed FP32 solve over the first n_load load steps (all if None):
+    every Newton state (d before the step, load factor) in order."""
+    n = P.n_free
     d = torch.zeros(n, dtype=torch.float64, device="cuda")
     r = torch.empty_like(d)
-    ctx32 = None
-    last = prob["load_steps"] if n_load_rec is None else n_load_rec
+    ctx = None
+    states = []
+    last = prob["load_steps"] if n_load is None else n_load
     for k in range(1, last + 1):
         lam = k / prob["load_steps"]
         P.residual(d, lam, r)
@@ -308,84 +409,153 @@ def run_ours(args, world, rank, local):
             if float(torch.linalg.vector_norm(r)) <= 1e-8 * r0:
                 break
             states.append((d.clone(), lam))
-            rec, ctx32 = P.newton_step(d, lam, opts32, ctx32)
+            rec, ctx = P.newton_step(d, lam, opts, ctx)
             if rec["status"] != 0:
                 raise RuntimeError("Newton step failed during the untimed solve: %r" % rec)
-    ns = len(states)
-    dw = torch.empty_like(d)
+    return states, ctx
 
-    def run_steps(count, opts, ctx, offset=0, records=None):
-        for j in range(count):
-            ds, lam = states[(offset + j) % ns]
+
+def _spread(n, k):
+    """k indices spread evenly over range(n) (all of them if k >= n)."""
+    if k >= n:
+        return list(range(n))
+    return sorted({int(round(i * (n - 1) / max(1, k - 1))) for i in range(k)})
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_2208_06191_gb300 as pkg
+
+    if world == 1:
+        torch.cuda.set_device(local)
+    pkg.build()
+    pkg.load_library()
+    spec = WORKLOADS[args.workload]
+    prob = spec["build"]()
+    P = pkg.Problem(prob)
+    n = P.n_free
+    opts32 = _opts(pkg, prob, spec, pkg.FP32, args.max_gmres)
+    opts64 = _opts(pkg, prob, spec, pkg.FP64, args.max_gmres)
+
+    states, ctx32 = newton_states(P, prob, opts32, spec["n_load"], torch)
+    ns = len(states)
+    dw = torch.empty_like(states[0][0])
+
+    def run_steps(seq, opts, ctx, records=None):
+        for j in seq:
+            ds, lam = states[j]
             dw.copy_(ds)
             rec, ctx = P.newton_step(dw, lam, opts, ctx)
             if rec["status"] != 0:
                 raise RuntimeError("Newton step did not converge: %r" % rec)
             if records is not None:
-                records.append(rec)
+                records.append(dict(rec, state=j))
         return ctx
 
     stream = torch.cuda.current_stream()
-    K, W = args.steps, args.warmup
+    K, Wm = args.steps, args.warmup
+    seq = [j % ns for j in range(K)]
     # ---- FP32 local operators (primary value)
-    ctx32 = run_steps(W, opts32, ctx32)
+    ctx32 = run_steps([j % ns for j in range(Wm)], opts32, ctx32)
     clocks = ClockSampler(local)
     clocks.start()
     recs32 = []
     launches0 = pkg.kernel_launches()
-    pkg.timer_start(pkg.TIMER_SWEEP_GEMM)
     _barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    ctx32 = run_steps(K, opts32, ctx32, 0, recs32)
+    ctx32 = run_steps(seq, opts32, ctx32, recs32)
     e1.record(stream)
     torch.cuda.synchronize()
     _barrier(world)
-    gemm = pkg.timer_stop()
     launches = pkg.kernel_launches() - launches0
     clk = clocks.stop()
     ms32 = _max_over_ranks(e0.elapsed_time(e1) / K, world)
 
-    # per-class kernel times over two more FP32 steps each (after the timed
-    # region, so the timed numbers carry no extra events)
+    # ---- kernel classes and the per-level split, over two more FP32 steps
+    # (after the timed region, so the timed numbers carry no extra events)
+    pkg.timer_start(getattr(pkg, "TIMER_" + TIMER_CLASSES[0]))
+    for c in TIMER_CLASSES[1:]:
+        pkg.timer_enable(getattr(pkg, "TIMER_" + c))
+    kseq = _spread(ns, 2)
+    krecs = []
+    ctx32 = run_steps(kseq, opts32, ctx32, krecs)
+    tt = {c: pkg.timer_result(getattr(pkg, "TIMER_" + c)) for c in TIMER_CLASSES}
+    pkg.timer_stop()
+    nk = len(kseq)
     kernels = {}
-    for name, cls in (("bddc_apply", pkg.TIMER_APPLY), ("bsr_spmv", pkg.TIMER_SPMV),
-                      ("element_kernel", pkg.TIMER_ELEMENT), ("gmres_orth", pkg.TIMER_ORTH)):
-        pkg.timer_start(cls)
-        ctx32 = run_steps(2, opts32, ctx32)
-        t = pkg.timer_stop()
+    for c, t in tt.items():
         if t["launches"]:
             ms = t["ms"] / t["launches"]
-            kernels[name] = {"launches": t["launches"], "ms_per_launch": ms,
-                             "GB_per_launch": t["bytes"] / t["launches"] / 1e9,
-                             "GBps": t["bytes"] / t["launches"] / (ms * 1e-3) / 1e9,
-                             "GFLOP_per_launch": t["flops"] / t["launches"] / 1e9}
+            kernels[c.lower()] = {"launches": t["launches"], "ms_per_launch": ms,
+                                  "ms_per_step": t["ms"] / nk,
+                                  "GB_per_launch": t["bytes"] / t["launches"] / 1e9,
+                                  "GBps": t["bytes"] / t["launches"] / (ms * 1e-3) / 1e9 if ms > 0 else None,
+                                  "GFLOP_per_launch": t["flops"] / t["launches"] / 1e9,
+                                  "TFLOPs": t["flops"] / t["launches"] / (ms * 1e-3) / 1e12 if ms > 0 else None}
 
-    # ---- FP64 local operators
-    ctx64 = run_steps(1, opts64, None)
-    recs64 = []
-    if args.workload == WORKLOAD:
-        K64 = max(1, min(K, args.fp64_steps))
+    def per_step(c):
+        return tt[c]["ms"] / nk
+
+    if spec["levels"] == 3:
+        per_level = {
+            "level1_setup_ms": per_step("SETUP") - per_step("LEVEL2_SETUP"),
+            "level2_setup_ms": per_step("LEVEL2_SETUP") - per_step("COARSE_SETUP"),
+            "coarsest_setup_ms": per_step("COARSE_SETUP"),
+            "level1_apply_ms": per_step("APPLY") - per_step("LEVEL2_APPLY"),
+            "level2_apply_ms": per_step("LEVEL2_APPLY") - per_step("COARSE_APPLY"),
+            "coarsest_apply_ms": per_step("COARSE_APPLY"),
+        }
     else:
-        K64 = ns if fp64_default is None else max(1, min(K, fp64_default))
+        per_level = {
+            "level1_setup_ms": per_step("SETUP") - per_step("COARSE_SETUP"),
+            "coarsest_setup_ms": per_step("COARSE_SETUP"),
+            "level1_apply_ms": per_step("APPLY") - per_step("COARSE_APPLY"),
+            "coarsest_apply_ms": per_step("COARSE_APPLY"),
+        }
+    per_level["gmres_spmv_ms"] = per_step("SPMV")
+    per_level["gmres_orth_ms"] = per_step("ORTH")
+    per_level["assembly_element_kernel_ms"] = per_step("ELEMENT")
+    per_level["steps_averaged"] = nk
+
+    # ---- FP64 local operators on a subset of the same states, paired
+    n64 = args.fp64_states if args.fp64_states is not None else spec["fp64_states"]
+    sel64 = _spread(ns, ns if n64 is None else n64)
+    ctx64 = run_steps(sel64[:1], opts64, None)  # context creation, untimed
+    recs64 = []
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    ctx64 = run_steps(K64, opts64, ctx64, 0, recs64)
+    ctx64 = run_steps(sel64, opts64, ctx64, recs64)
     f1.record(stream)
     torch.cuda.synchronize()
-    ms64 = _max_over_ranks(f0.elapsed_time(f1) / K64, world)
+    ms64 = _max_over_ranks(f0.elapsed_time(f1) / len(sel64), world)
+    by_state32 = {}
+    for r in recs32:
+        by_state32.setdefault(r["state"], []).append(r)
+    paired = []
+    for r64 in recs64:
+        r32 = by_state32.get(r64["state"])
+        if r32:
+            paired.append({"state": r64["state"], "load": r64["load"],
+                           "its32": r32[0]["gmres_its"], "its64": r64["gmres_its"],
+                           "ms32": statistics.mean(x["ms_total"] for x in r32), "ms64": r64["ms_total"],
+                           "relres32": max(x["gmres_relres"] for x in r32), "relres64": r64["gmres_relres"]})
+    speedup = (statistics.mean(p["ms64"] for p in paired) / statistics.mean(p["ms32"] for p in paired)
+               if paired else None)
 
     # ---- end to end through the C ABI with host buffers (pinned)
     host = torch.empty(n, dtype=torch.float64, pin_memory=True)
     host_np = host.numpy()
     states_h = [(s.cpu().numpy(), lam) for s, lam in states]
+    e2e_seq = list(range(ns)) if ns <= K else _spread(ns, K)
     torch.cuda.synchronize()
     _barrier(world)
     t0 = time.perf_counter()
-    for j in range(K):
-        ds, lam = states_h[j % ns]
+    for j in e2e_seq:
+        ds, lam = states_h[j]
         host_np[:] = ds
         rec, ctx32 = P.newton_step(host_np, lam, opts32, ctx32, host=True)
         if rec["status"] != 0:
@@ -393,69 +563,82 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     _barrier(world)
-    e2e_ms = _max_over_ranks(1000.0 * (t1 - t0) / K, world)
+    e2e_ms = _max_over_ranks(1000.0 * (t1 - t0) / len(e2e_seq), world)
 
+    # ---- roofline of the dominant kernel class of the step
     peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # FP32 FMA peak from unit counts and the maximum SM clock:
-    # 152 SMs x 128 FP32 lanes x 2 flop x f_max
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    achieved = gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm["ms"] > 0 else None
-    roofline = {
-        "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-        "frac": achieved / fp32_peak if achieved else None, "traffic": None,
-        "kernel": "gemm_grouped_kernel<float> (Gauss-Jordan sweep trailing update)",
-        "launches": gemm["launches"], "ms_per_launch": gemm["ms"] / max(1, gemm["launches"]),
-        "flops_per_launch": gemm["flops"] / max(1, gemm["launches"]),
-        "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %g MHz (unit counts and max clock)" % sm_max,
-    }
+    hbm = float(peaks.get("hbm_gbs", 6767.1))
+    bf16 = float(peaks.get("bf16_tflops", 1888.9))
+    ap, gm = kernels.get("apply"), kernels.get("sweep_gemm")
+    apply_step = ap["ms_per_step"] if ap else 0.0
+    gemm_step = gm["ms_per_step"] if gm else 0.0
+    if apply_step >= gemm_step and ap:
+        achieved = ap["GBps"]
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": None,
+                    "kernel": "BDDC apply (its batched launches, level 2 and coarsest included)",
+                    "bytes_per_launch": ap["GB_per_launch"] * 1e9, "ms_per_launch": ap["ms_per_launch"],
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                    "work": "dense local operators read once per apply (local_bytes)"}
+    else:
+        tf32 = bf16 / 2.0
+        achieved = gm["TFLOPs"]
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": tf32 / 3.0, "unit": "TFLOP/s",
+                    "frac": achieved / (tf32 / 3.0), "traffic": None,
+                    "kernel": "FP32 setup GEMMs on tcgen05 (3xTF32)",
+                    "flops_per_launch": gm["GFLOP_per_launch"] * 1e9, "ms_per_launch": gm["ms_per_launch"],
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops / 2 (TF32) / 3 (three TF32 passes "
+                                   "per FP32 product) (of measured)"}
 
-    def phase(recs, key):
+    def mean(recs, key):
         return statistics.mean(r[key] for r in recs)
 
     line = {
-        "metric": METRIC, "value": ms32, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "metric": METRIC, "value": ms32, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
         "ms_per_step": ms32, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
         "config": {
-            "workload": desc, "workload_name": args.workload, "newton_states": ns,
-            "n_free": n, "parallelism": "replicas",
-            "precision": {"local_operators": "f32", "assembly": "f64", "gmres": "f64",
-                          "coarse": "f64" if levels == 2 else "level-2 f32, coarsest f64"},
-            "l2": "inputs larger than L2 (dense local operators ~1.1 GB read per BDDC apply)",
+            "workload": spec["desc"], "workload_name": args.workload, "newton_states": ns,
+            "replay": "the %d Newton states in solve order, cyclically, one per step" % ns,
+            "n_free": n, "parallelism": "replicas", "gmres_restart": spec["restart"],
+            "precision": {"local_operators": "f32 (setup GEMMs: tcgen05 3xTF32)", "assembly": "f64",
+                          "gmres": "f64", "coarse": "f64" if spec["levels"] == 2 else "level-2 f32, coarsest f64"},
+            "l2": "inputs larger than L2 (dense local operators read per BDDC apply: %.1f GB)"
+                  % (ap["GB_per_launch"] if ap else 0.0),
         },
-        "fp64": {"ms_per_step": ms64, "steps": K64,
-                 "gmres_its_mean": statistics.mean(r["gmres_its"] for r in recs64),
-                 "ms_setup": phase(recs64, "ms_setup"), "ms_gmres": phase(recs64, "ms_gmres")},
-        "speedup_fp32_vs_fp64": ms64 / ms32,
-        "breakdown_fp32": {"ms_assemble": phase(recs32, "ms_assemble"),
-                           "ms_setup": phase(recs32, "ms_setup"),
-                           "ms_gmres": phase(recs32, "ms_gmres"),
-                           "gmres_its_mean": statistics.mean(r["gmres_its"] for r in recs32),
+        "fp64": {"ms_per_step": ms64, "states": sel64,
+                 "gmres_its_mean": mean(recs64, "gmres_its"),
+                 "ms_setup": mean(recs64, "ms_setup"), "ms_gmres": mean(recs64, "ms_gmres")},
+        "paired_states": paired,
+        "speedup_fp32_vs_fp64": speedup,
+        "its_fp32_minus_fp64_max": max((p["its32"] - p["its64"] for p in paired), default=None),
+        "breakdown_fp32": {"ms_assemble": mean(recs32, "ms_assemble"), "ms_setup": mean(recs32, "ms_setup"),
+                           "ms_gmres": mean(recs32, "ms_gmres"),
+                           "gmres_its_mean": mean(recs32, "gmres_its"),
                            "gmres_its_max": max(r["gmres_its"] for r in recs32),
+                           "gmres_relres_max": max(r["gmres_relres"] for r in recs32),
+                           "gmres_second_pass_frac": sum(r["gmres_reorth"] for r in recs32)
+                           / max(1, sum(r["gmres_its"] for r in recs32)),
                            "ms_step_median": statistics.median(r["ms_total"] for r in recs32),
                            "ms_step_max": max(r["ms_total"] for r in recs32)},
-        "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
-                "d2h_bytes_per_step": 8 * n},
+        "per_level": per_level,
+        "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+                "steps": len(e2e_seq)},
         "gpu_launches": int(launches),
         "roofline": roofline,
         "kernels": kernels,
     }
     if clk:
         line["clocks"] = clk
-    if args.workload != WORKLOAD:
-        line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "not run: reported for the default workload only"}
-    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            s, its = _oracle_step_seconds(timeout=900)
-            line["cpu_baseline"] = {
-                "value": 1000.0 * s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": "one oracle Newton step of the same workload at d=0, lambda=1/4 "
-                          "(%d GMRES its), single-threaded, fresh process" % its}
+            single, allc, cores, sample = oracle_baseline(args.workload, mean(recs32, "gmres_its"))
+            line["cpu_baseline"] = {"value": single, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": sample, "cpu_model": _cpu_model(),
+                                    "all_cores": {"value": allc, "cores": cores}}
         except Exception as exc:  # the baseline is reported, not required
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "failed: %s" % str(exc)[-200:]}
+                                    "sample": "failed: %s" % str(exc)[-300:]}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -468,14 +651,14 @@ def run_kernels(args):
 
     pkg.build()
     pkg.load_library()
-    _desc, build_prob, levels, _groups, _n, _f = WORKLOADS[args.workload]
-    prob = build_prob()
+    spec = WORKLOADS[args.workload]
+    prob = spec["build"]()
     P = pkg.Problem(prob)
     d = torch.zeros(P.n_free, dtype=torch.float64, device="cuda")
     r = torch.empty_like(d)
     P.assemble_tangent(d, 1.0 / prob["load_steps"], r)
     ml = {}
-    if levels == 3:
+    if spec["levels"] == 3:
         ml = dict(levels=3, part2=prob["part2"], n_parts2=prob["n_parts2"], primal2="VEF",
                   precision2=pkg.FP32)
     pc = pkg.BDDC(P, precision=pkg.FP32, primal=prob["primal"], scaling=prob.get("scaling", "counting"),

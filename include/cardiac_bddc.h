@@ -260,6 +260,9 @@ typedef struct {
                         deluxe allows at most 65535 edge and face classes,
                         of at most 1024 nodes each (CBDDC_EINVAL otherwise) */
   int coarse;        /* CBDDC_COARSE_GALERKIN (0) or CBDDC_COARSE_PETROV */
+  int sweep_block;   /* pivot block width of the local Gauss-Jordan sweeps:
+                        0 or 64 (default), or 128 (FP32 operators only:
+                        half the passes over each local matrix) */
 } bddc_options;
 
 typedef struct bddc_ctx bddc_ctx;
@@ -354,6 +357,7 @@ typedef struct {
   int precision2;
   int scaling;         /* as in bddc_options                                 */
   int coarse;          /* as in bddc_options                                 */
+  int sweep_block;     /* as in bddc_options                                 */
 } solve_options;
 
 #define CBDDC_MAX_RECORDS 512

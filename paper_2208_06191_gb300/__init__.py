@@ -111,7 +111,7 @@ class _BddcOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("primal", ctypes.c_int), ("pivot_tol", ctypes.c_double),
                 ("levels", ctypes.c_int), ("n_parts2", ctypes.c_int), ("part2", _i32p),
                 ("primal2", ctypes.c_int), ("precision2", ctypes.c_int), ("scaling", ctypes.c_int),
-                ("coarse", ctypes.c_int)]
+                ("coarse", ctypes.c_int), ("sweep_block", ctypes.c_int)]
 
 
 class _BddcInfo(ctypes.Structure):
@@ -135,7 +135,7 @@ class _SolveOptions(ctypes.Structure):
         ("max_gmres", ctypes.c_int), ("newton_rtol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
         ("pivot_tol", ctypes.c_double), ("levels", ctypes.c_int), ("n_parts2", ctypes.c_int),
         ("part2", _i32p), ("primal2", ctypes.c_int), ("precision2", ctypes.c_int),
-        ("scaling", ctypes.c_int), ("coarse", ctypes.c_int),
+        ("scaling", ctypes.c_int), ("coarse", ctypes.c_int), ("sweep_block", ctypes.c_int),
     ]
 
 
@@ -287,12 +287,14 @@ class SolveOptions:
     Multilevel BDDC: levels=3 with part2 (level-2 subdomain of every
     subdomain), n_parts2, primal2 and precision2 (level-2 local operators).
     scaling: "counting" or "deluxe" (first level); coarse: "galerkin" or
-    "petrov" (left coarse basis from the transposed local problems)."""
+    "petrov" (left coarse basis from the transposed local problems);
+    sweep_block: pivot block width of the local sweeps (0/64, or 128 for
+    FP32 operators)."""
 
     def __init__(self, precision=FP64, primal="V", load_steps=4, max_newton=25, max_halvings=6,
                  restart=100, max_gmres=1000, newton_rtol=1e-8, gmres_rtol=1e-8, pivot_tol=1e-13,
                  levels=2, part2=None, n_parts2=0, primal2="VEF", precision2=FP64, scaling="counting",
-                 coarse="galerkin"):
+                 coarse="galerkin", sweep_block=0):
         self.precision = precision
         self.primal = primal if isinstance(primal, int) else primal_mask(primal)
         self.load_steps = load_steps
@@ -310,12 +312,14 @@ class SolveOptions:
         self.precision2 = precision2
         self.scaling = scaling_code(scaling)
         self.coarse = coarse_code(coarse)
+        self.sweep_block = int(sweep_block)
 
     def c(self):
         return _SolveOptions(self.precision, self.primal, self.load_steps, self.max_newton,
                              self.max_halvings, self.restart, self.max_gmres, self.newton_rtol,
                              self.gmres_rtol, self.pivot_tol, self.levels, self.n_parts2,
-                             self._part2_ptr, self.primal2, self.precision2, self.scaling, self.coarse)
+                             self._part2_ptr, self.primal2, self.precision2, self.scaling, self.coarse,
+                             self.sweep_block)
 
 
 def _record_dict(r):
@@ -517,14 +521,15 @@ class BDDC:
     """BDDC preconditioner context (bddc_ctx) for a problem."""
 
     def __init__(self, problem, precision=FP64, primal="V", pivot_tol=1e-13, levels=2, part2=None,
-                 n_parts2=0, primal2="VEF", precision2=FP64, scaling="counting", coarse="galerkin"):
+                 n_parts2=0, primal2="VEF", precision2=FP64, scaling="counting", coarse="galerkin",
+                 sweep_block=0):
         self.problem = problem
         self._h = ctypes.c_void_p()
         self._part2, p2 = _part2_arg(part2)
         self._opt = _BddcOptions(precision, primal if isinstance(primal, int) else primal_mask(primal),
                                  pivot_tol, levels, int(n_parts2), p2,
                                  primal2 if isinstance(primal2, int) else primal_mask(primal2),
-                                 precision2, scaling_code(scaling), coarse_code(coarse))
+                                 precision2, scaling_code(scaling), coarse_code(coarse), int(sweep_block))
 
     @classmethod
     def _wrap(cls, h, problem):

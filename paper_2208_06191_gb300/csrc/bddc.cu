@@ -146,33 +146,43 @@ __global__ void densify_kernel(const int* __restrict__ lsub, const int* __restri
   Aloc[offA[s] + (int64_t)row * ldA[s] + col] = (T)v;
 }
 
+// Row copies between packed per-subdomain blocks: row i (< rows) of
+// dst (ld_dst) <- row i of src (ld_src), n entries per row.  One warp per
+// row, 8 rows per CTA, grid (row blocks, subdomains); 64-bit index
+// arithmetic only per row.
 template <typename T>
-__global__ void copy_schur_kernel(const int* __restrict__ nI, const int* __restrict__ nG,
-                                  const int64_t* __restrict__ offA, const int* __restrict__ ldA,
-                                  const int64_t* __restrict__ offS, const int* __restrict__ ldS,
-                                  const T* __restrict__ Aloc, T* __restrict__ Sw) {
-  const int s = blockIdx.y;
-  const int ng = nG[s], ni = nI[s];
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)ng * ng) return;
-  const int i = (int)(t / ng), j = (int)(t % ng);
-  const int cI = (int)round_up_dev(ni, 4);
-  Sw[offS[s] + (int64_t)i * ldS[s] + j] = Aloc[offA[s] + (int64_t)(ni + i) * ldA[s] + cI + j];
+__device__ __forceinline__ void copy_rows(T* __restrict__ dst, int64_t ldd, const T* __restrict__ src, int64_t lds,
+                                          int rows, int n) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (i >= rows) return;
+  const T* sr = src + (int64_t)i * lds;
+  T* dr = dst + (int64_t)i * ldd;
+  for (int j = lane; j < n; j += 32) dr[j] = sr[j];
 }
 
-// A_IG block <- E (the harmonic-extension operator A_II^-1 A_IG).
+// Sw <- S (the GG block of Aloc after the interior sweep), n_G x n_G.
 template <typename T>
-__global__ void copy_e_kernel(const int* __restrict__ nI, const int* __restrict__ nG,
-                              const int64_t* __restrict__ offA, const int* __restrict__ ldA,
-                              const int64_t* __restrict__ offE, const int* __restrict__ ldE,
-                              const T* __restrict__ Et, T* __restrict__ Aloc) {
+__global__ void __launch_bounds__(256)
+copy_schur_kernel(const int* __restrict__ nI, const int* __restrict__ nG, const int64_t* __restrict__ offA,
+                  const int* __restrict__ ldA, const int64_t* __restrict__ offS, const int* __restrict__ ldS,
+                  const T* __restrict__ Aloc, T* __restrict__ Sw) {
   const int s = blockIdx.y;
   const int ng = nG[s], ni = nI[s];
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)ni * ng) return;
-  const int i = (int)(t / ng), j = (int)(t % ng);
   const int cI = (int)round_up_dev(ni, 4);
-  Aloc[offA[s] + (int64_t)i * ldA[s] + cI + j] = Et[offE[s] + (int64_t)i * ldE[s] + j];
+  copy_rows(Sw + offS[s], ldS[s], Aloc + offA[s] + (int64_t)ni * ldA[s] + cI, ldA[s], ng, ng);
+}
+
+// A_IG block <- E (the harmonic-extension operator A_II^-1 A_IG), n_I x n_G.
+template <typename T>
+__global__ void __launch_bounds__(256)
+copy_e_kernel(const int* __restrict__ nI, const int* __restrict__ nG, const int64_t* __restrict__ offA,
+              const int* __restrict__ ldA, const int64_t* __restrict__ offE, const int* __restrict__ ldE,
+              const T* __restrict__ Et, T* __restrict__ Aloc) {
+  const int s = blockIdx.y;
+  const int ng = nG[s], ni = nI[s];
+  const int cI = (int)round_up_dev(ni, 4);
+  copy_rows(Aloc + offA[s] + cI, ldA[s], Et + offE[s], ldE[s], ni, ng);
 }
 
 // S_rr += alpha sum_q c_q c_q^T / |c_q|^2 over the constraint rows c_q
@@ -216,7 +226,8 @@ augment_kernel(const int* __restrict__ nr, const int* __restrict__ na,
   }
 }
 
-// Y[row][q] = sum_{j in q} w_j Sw[row][j], one warp per row (row < n_r).
+// Y[row][q] = sum_{j in q} w_j Sw[row][j], one warp per row (row < n_r),
+// accumulated in the operator precision.
 template <typename T>
 __global__ void cons_y_kernel(const int* __restrict__ nr, const int* __restrict__ na,
                               const int64_t* __restrict__ offCon, const int* __restrict__ cptr,
@@ -233,13 +244,14 @@ __global__ void cons_y_kernel(const int* __restrict__ nr, const int* __restrict_
   // and the row's Y entries are written together
   for (int q = lane; q < na[s]; q += 32) {
     const int64_t gq = offCon[s] + q;
-    double acc = 0.0;
-    for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += (double)Srow[cidx[j]] * cw[j];
-    Y[offY[s] + (int64_t)row * ldY[s] + q] = (T)acc;
+    T acc = T(0);
+    for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += Srow[cidx[j]] * (T)cw[j];
+    Y[offY[s] + (int64_t)row * ldY[s] + q] = acc;
   }
 }
 
-// Zf[q][col] = sum_{j in q} w_j Sw[j][col] for all n_G columns.
+// Zf[q][col] = sum_{j in q} w_j Sw[j][col] for all n_G columns (operator
+// precision).
 template <typename T>
 __global__ void cons_z_kernel(const int* __restrict__ nG, const int* __restrict__ na,
                               const int64_t* __restrict__ offCon, const int* __restrict__ cptr,
@@ -254,9 +266,9 @@ __global__ void cons_z_kernel(const int* __restrict__ nG, const int* __restrict_
   const int ld = ldS[s];
   for (int q = 0; q < na[s]; ++q) {
     const int64_t gq = offCon[s] + q;
-    double acc = 0.0;
-    for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += (double)S0[(int64_t)cidx[j] * ld + col] * cw[j];
-    Zf[offZ[s] + (int64_t)q * ld + col] = (T)acc;
+    T acc = T(0);
+    for (int j = cptr[gq]; j < cptr[gq + 1]; ++j) acc += S0[(int64_t)cidx[j] * ld + col] * (T)cw[j];
+    Zf[offZ[s] + (int64_t)q * ld + col] = acc;
   }
 }
 
@@ -794,6 +806,10 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     for (int g : C->part2) CB_CHECK(g >= 0 && g < C->n_parts2, CBDDC_EINVAL, "part2 out of range");
   }
   C->esize = opt->precision == CBDDC_FP32 ? 4 : 8;
+  CB_CHECK(opt->sweep_block == 0 || opt->sweep_block == 64 ||
+               (opt->sweep_block == 128 && opt->precision == CBDDC_FP32),
+           CBDDC_EINVAL, "sweep_block must be 0, 64, or 128 with FP32 operators");
+  C->nb = opt->sweep_block == 128 ? 128 : SWEEP_NB;
   const int nsub = P->n_parts;
   C->nsub = nsub;
   const bool useV = opt->primal & CBDDC_PRIMAL_V;
@@ -1005,7 +1021,7 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   }
 
   // packed storage layout
-  const int NB = SWEEP_NB;
+  const int NB = C->nb;
   C->ldA.assign(nsub, 0); C->ldS = C->ldPhi = C->ldY = C->ldG = C->ldA;
   C->offA.assign(nsub + 1, 0); C->offS = C->offPhi = C->offY = C->offZ = C->offG = C->offSPhi =
       C->offKc = C->offX = C->offYp = C->offP = C->offE = C->offA;
@@ -1225,12 +1241,13 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     C->ce_ptr.upload(ptr);
     C->ce_src.upload(src);
     C->Sc.alloc((size_t)C->n_pi * C->n_pi);
-    C->ScX.alloc((size_t)C->n_pi * NB);
-    C->ScY.alloc((size_t)C->n_pi * NB);
-    C->ScP.alloc((size_t)NB * NB);
+    const int NBc = SWEEP_NB;  // the FP64 coarse inverse keeps 64-wide pivot blocks
+    C->ScX.alloc((size_t)C->n_pi * NBc);
+    C->ScY.alloc((size_t)C->n_pi * NBc);
+    C->ScP.alloc((size_t)NBc * NBc);
     std::vector<SweepDesc> swc{SweepDesc{C->n_pi, C->n_pi, C->n_pi, C->n_pi, 0, 0, 0, 0}};
     C->swc.upload(swc);
-    C->stepsc = (int)cdiv(C->n_pi, NB);
+    C->stepsc = (int)cdiv(C->n_pi, NBc);
     {
       // the coarse matrix is FP64 whatever the local precision
       const int nmat = 1;
@@ -1238,8 +1255,8 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
       C->gl_swc.resize(C->stepsc);
       for (int k = 0; k < C->stepsc; ++k) {
         const SweepDesc& d = swc[0];
-        const int kb = std::max(0, std::min(NB, d.p - k * NB));
-        std::vector<GemmProb> g{GemmProb{d.rows, d.cols, kb, NB, d.ld, d.ld, d.offX, d.offY, d.off}};
+        const int kb = std::max(0, std::min(NBc, d.p - k * NBc));
+        std::vector<GemmProb> g{GemmProb{d.rows, d.cols, kb, NBc, d.ld, d.ld, d.offX, d.offY, d.off}};
         C->gl_swc[k].set(g, 8);
         (void)nmat;
       }
@@ -1334,6 +1351,26 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   // tensor-core GEMMs, shared by every list (they run one after another on
   // the setup stream)
   if (C->esize == 4) {
+    // sweep updates: operands written split by the panel kernel into
+    // Xp/Xlo ([rows][nb]) and Yp/Ylo ([columns][nb])
+    const int nb = C->nb;
+    C->Xlo.alloc(std::max<size_t>(C->Xp.bytes() / 4, 1));
+    C->Ylo.alloc(std::max<size_t>(C->Yp.bytes() / 4, 1));
+    float* xh = reinterpret_cast<float*>(C->Xp.p);
+    float* yh = reinterpret_cast<float*>(C->Yp.p);
+    const int64_t rx = (int64_t)(C->Xp.bytes() / 4) / nb, ry = (int64_t)(C->Yp.bytes() / 4) / nb;
+    for (auto* v : {&C->gl_sw1, &C->gl_sw2, &C->gl_swg})
+      for (auto& g : *v)
+        if (rx > 0 && ry > 0) g.bind_presplit(nb, xh, C->Xlo.p, rx, yh, C->Ylo.p, ry, P->status.p);
+    if (C->DX.bytes() > 0) {
+      C->DXlo.alloc(C->DX.bytes() / 4);
+      C->DYlo.alloc(C->DY.bytes() / 4);
+      const int64_t dx = (int64_t)(C->DX.bytes() / 4) / nb, dy = (int64_t)(C->DY.bytes() / 4) / nb;
+      for (auto& g : C->gl_swd)
+        if (dx > 0 && dy > 0)
+          g.bind_presplit(nb, reinterpret_cast<float*>(C->DX.p), C->DXlo.p, dx, reinterpret_cast<float*>(C->DY.p),
+                          C->DYlo.p, dy, P->status.p);
+    }
     std::vector<GemmList*> lists{&C->gl_E, &C->gl_S, &C->gl_W, &C->gl_T, &C->gl_PhiA, &C->gl_SPhi, &C->gl_Kc,
                                  &C->gl_PsiV, &C->gl_dlx};
     for (auto* v : {&C->gl_sw1, &C->gl_sw2, &C->gl_swg, &C->gl_swd})
@@ -1348,18 +1385,53 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
 }
 
 // ------------------------------------------------------------------- setup
+template <typename T, int NB, bool SPLIT>
+static void panel_launch(dim3 grid, cudaStream_t s, const SweepDesc* desc, int k, T* mat, const T* Pbuf, T* X,
+                         T* Y, T* Xlo, T* Ylo) {
+  constexpr size_t smem = panel_smem_bytes<T, NB>();
+  static bool attr = false;
+  if (!attr) {
+    CB_CUDA(cudaFuncSetAttribute(sweep_panel_kernel<T, NB, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    attr = true;
+  }
+  sweep_panel_kernel<T, NB, SPLIT><<<grid, 256, smem, s>>>(desc, k, mat, Pbuf, X, Y, Xlo, Ylo);
+  CB_LAUNCH();
+}
+
+// One sweep: per pivot block the diagonal inverse, the panels and the
+// rank-NB update.  FP32 lists bound to the tensor cores get their panels as
+// split TF32 operands (X, Xlo, Y^T, Ylo) and skip the split pass.
+template <typename T, int NB>
+static void run_sweep_nb(const DVec<SweepDesc>& desc, int nmat, const std::vector<GemmList>& lists,
+                         int maxRows, int maxCols, T* mat, T* X, T* Y, T* Pbuf, int* status, double tol,
+                         cudaStream_t s, T* Xlo, T* Ylo) {
+  for (int k = 0; k < (int)lists.size(); ++k) {
+    sweep_diag_kernel<T, NB><<<nmat, DiagThreads<NB>::value, 0, s>>>(desc.p, k, mat, Pbuf, status, tol);
+    CB_LAUNCH();
+    dim3 grid(cdiv(std::max(maxRows, maxCols), PANEL_CH), nmat);
+    const bool split = sizeof(T) == 4 && lists[k].presplit && tensor_cores_enabled();
+    if (split)
+      panel_launch<T, NB, true>(grid, s, desc.p, k, mat, Pbuf, X, Y, Xlo, Ylo);
+    else
+      panel_launch<T, NB, false>(grid, s, desc.p, k, mat, Pbuf, X, Y, nullptr, nullptr);
+    launch_list<T, false, false>(lists[k], X, Y, mat, T(-1), T(1), s);
+  }
+}
+
+// Sweep with pivot blocks of nb (64, or 128 for FP32 operators).
 template <typename T>
 static void run_sweep(const DVec<SweepDesc>& desc, int nmat, const std::vector<GemmList>& lists,
                       int maxRows, int maxCols, T* mat, T* X, T* Y, T* Pbuf, int* status, double tol,
-                      cudaStream_t s) {
-  for (int k = 0; k < (int)lists.size(); ++k) {
-    sweep_diag_kernel<T><<<nmat, DIAG_THREADS, 0, s>>>(desc.p, k, mat, Pbuf, status, tol);
-    CB_LAUNCH();
-    dim3 grid(cdiv(std::max(maxRows, maxCols), PANEL_CH), nmat);
-    sweep_panel_kernel<T><<<grid, 256, 0, s>>>(desc.p, k, mat, Pbuf, X, Y);
-    CB_LAUNCH();
-    launch_list<T, false, false>(lists[k], X, Y, mat, T(-1), T(1), s);
+                      cudaStream_t s, int nb = SWEEP_NB, T* Xlo = nullptr, T* Ylo = nullptr) {
+  if constexpr (sizeof(T) == 4) {
+    if (nb == SWEEP_NB_MAX) {
+      run_sweep_nb<T, SWEEP_NB_MAX>(desc, nmat, lists, maxRows, maxCols, mat, X, Y, Pbuf, status, tol, s, Xlo,
+                                    Ylo);
+      return;
+    }
   }
+  run_sweep_nb<T, SWEEP_NB>(desc, nmat, lists, maxRows, maxCols, mat, X, Y, Pbuf, status, tol, s, Xlo, Ylo);
 }
 
 template <typename T>
@@ -1389,12 +1461,14 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
   CB_LAUNCH();
   // 2. interior elimination: A_II^-1 by a sweep of the II block, then
   //    E = A_II^-1 A_IG and S = A_GG - A_GI E, and E stored over A_IG
-  run_sweep<T>(C->sw1, nsub, C->gl_sw1, C->maxI, C->maxI, Aloc, Xp, Yp, Pd, status, tol, s);
+  T* Xlo = reinterpret_cast<T*>(C->Xlo.p);
+  T* Ylo = reinterpret_cast<T*>(C->Ylo.p);
+  run_sweep<T>(C->sw1, nsub, C->gl_sw1, C->maxI, C->maxI, Aloc, Xp, Yp, Pd, status, tol, s, C->nb, Xlo, Ylo);
   if (C->maxG == 0) return;  // one subdomain: no interface
   launch_list<T, false, false>(C->gl_E, Aloc, Aloc, Et, T(1), T(0), s);
   launch_list<T, false, false>(C->gl_S, Aloc, Et, Aloc, T(-1), T(1), s);
   if (C->maxI > 0) {
-    copy_e_kernel<T><<<dim3(cdiv((int64_t)C->maxI * C->maxG, 256), nsub), 256, 0, s>>>(
+    copy_e_kernel<T><<<dim3(cdiv(C->maxI, 8), nsub), 256, 0, s>>>(
         C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offE.p, C->d_ldS.p, Et, Aloc);
     CB_LAUNCH();
   }
@@ -1414,14 +1488,15 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
                                                    C->dlx_off.p, C->dcls_off.p, Dsb, Dsh);
     CB_LAUNCH();
     run_sweep<T>(C->swd, C->n_dcls, C->gl_swd, C->maxDn, C->maxDn, Dsh, reinterpret_cast<T*>(C->DX.p),
-                 reinterpret_cast<T*>(C->DY.p), reinterpret_cast<T*>(C->DP.p), status, tol, s);
+                 reinterpret_cast<T*>(C->DY.p), reinterpret_cast<T*>(C->DP.p), status, tol, s, C->nb,
+                 reinterpret_cast<T*>(C->DXlo.p), reinterpret_cast<T*>(C->DYlo.p));
     launch_list<T, false, false>(C->gl_dlx, Dsh, Dsb, Ddb, T(1), T(0), s);
     deluxe_transpose_kernel<T><<<gb, 256, 0, s>>>(C->dlx_n.p, C->dlx_ld.p, C->dlx_off.p, Ddb,
                                                         reinterpret_cast<T*>(C->Deb.p));
     CB_LAUNCH();
   }
   // 3. Schur complement copy, augmentation and sweep over Gamma_r
-  copy_schur_kernel<T><<<dim3(cdiv((int64_t)C->maxG * C->maxG, 256), nsub), 256, 0, s>>>(
+  copy_schur_kernel<T><<<dim3(cdiv(C->maxG, 8), nsub), 256, 0, s>>>(
       C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offS.p, C->d_ldS.p, Aloc, Sw);
   CB_LAUNCH();
   if (C->maxA > 0) {
@@ -1429,7 +1504,7 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
                                           C->cons_idx.p, C->cons_w.p, C->d_offS.p, C->d_ldS.p, Sw);
     CB_LAUNCH();
   }
-  run_sweep<T>(C->sw2, nsub, C->gl_sw2, C->maxG, C->maxG, Sw, Xp, Yp, Pd, status, tol, s);
+  run_sweep<T>(C->sw2, nsub, C->gl_sw2, C->maxG, C->maxG, Sw, Xp, Yp, Pd, status, tol, s, C->nb, Xlo, Ylo);
   // 4. average constraints
   if (C->maxA > 0) {
     cons_y_kernel<T><<<dim3(cdiv(C->maxR, 8), nsub), 256, 0, s>>>(
@@ -1444,7 +1519,7 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
         C->d_na.p, C->d_offCon.p, C->cons_ptr.p, C->cons_idx.p, C->cons_w.p, C->d_offY.p, C->d_ldY.p,
         C->d_offG.p, C->d_ldG.p, Y, G);
     CB_LAUNCH();
-    run_sweep<T>(C->swg, nsub, C->gl_swg, C->maxA, C->maxA, G, Xp, Yp, Pd, status, tol, s);
+    run_sweep<T>(C->swg, nsub, C->gl_swg, C->maxA, C->maxA, G, Xp, Yp, Pd, status, tol, s, C->nb, Xlo, Ylo);
     launch_list<T, false, false>(C->gl_W, G, Zf, Wf, T(1), T(0), s);
     launch_list<T, false, false>(C->gl_T, Y, Wf, Sw, T(-1), T(1), s);
     launch_list<T, false, false>(C->gl_PhiA, Y, G, Phi, T(1), T(0), s);

@@ -9,6 +9,7 @@
 struct bddc_ctx {
   fem_problem* P = nullptr;
   int precision = CBDDC_FP64, primal = CBDDC_PRIMAL_V;
+  int nb = 64;                              // pivot block width of the local sweeps
   double pivot_tol = 1e-13;
   int nsub = 0;
   size_t esize = 8;  // bytes per element of the local operators
@@ -28,6 +29,7 @@ struct bddc_ctx {
   // local operators (element type float or double, raw storage)
   cbddc::DVec<unsigned char> Aloc, Sw, Phi, Y, Zf, Wf, G, SPhi, Kc, Xp, Yp, Pd, Et;
   cbddc::DVec<float> tc_scratch;            // split operands of the tensor-core GEMMs (FP32)
+  cbddc::DVec<float> Xlo, Ylo, DXlo, DYlo;  // low TF32 parts of the sweep panels (FP32)
   // apply maps
   cbddc::DVec<int> gdofI, gdofG, gam_if, if_dof, if_ptr, if_src;
   cbddc::DVec<double> Dg;

@@ -135,6 +135,8 @@ static void fill_tangent(fem_problem* P, fem_tangent* K) {
   K->nnzb = P->nnzb;
 }
 
+static int sweep_block_of(const bddc_options* opt) { return opt->sweep_block == 128 ? 128 : 64; }
+
 static void ensure_ctx(fem_problem* P, const solve_options* opt, bddc_ctx** C) {
   if (*C) return;
   bddc_options bo{};
@@ -148,6 +150,7 @@ static void ensure_ctx(fem_problem* P, const solve_options* opt, bddc_ctx** C) {
   bo.precision2 = opt->precision2;
   bo.scaling = opt->scaling;
   bo.coarse = opt->coarse;
+  bo.sweep_block = opt->sweep_block;
   bddc_ctx* c = new bddc_ctx;
   try {
     bddc_create(P, &bo, c);
@@ -357,7 +360,7 @@ int bddc_setup(fem_problem* P, const fem_tangent* K, const bddc_options* opt, bd
       bddc_ctx* c = *inout;
       CB_CHECK(c->P == P && c->precision == opt->precision && c->primal == opt->primal &&
                    c->levels == (opt->levels >= 3 ? 3 : 2) && c->scaling == opt->scaling &&
-                   c->coarse == opt->coarse,
+                   c->coarse == opt->coarse && c->nb == sweep_block_of(opt),
                CBDDC_EINVAL, "context was created for another problem or options");
     }
     bddc_run_setup(*inout, s);

@@ -300,7 +300,7 @@ struct GemmList {
   double flops = 0.0, bytes = 0.0;
   bool fast = true;  // every problem meets the vector-load alignment
   // tensor-core plan (FP32 only)
-  bool tc_planned = false, tc_bound = false;
+  bool tc_planned = false, tc_bound = false, presplit = false;
   int Kp = 0, maxM = 0, maxN = 0;
   int64_t rowsA = 0, rowsB = 0;
   DVec<tc::TcProb> tcp;
@@ -308,7 +308,9 @@ struct GemmList {
   float* tc_base = nullptr;
   int* tc_status = nullptr;
   CUtensorMap maps[4];
+  std::vector<GemmProb> h;  // host copy of the problems
   void set(const std::vector<GemmProb>& v, size_t esize, bool ta = false) {
+    h = v;
     n = (int)v.size();
     flops = bytes = 0.0;
     const int w = (int)(16 / esize);
@@ -357,6 +359,32 @@ struct GemmList {
   }
   // floats of split operands this list needs
   int64_t tc_floats() const { return tc_planned ? 2 * (rowsA + rowsB) * (int64_t)Kp : 0; }
+  // Sweep updates whose operands the panel kernel writes already split:
+  // op(A) = X at rows a / nb of the [rowsA][nb] hi/lo arrays, op(B)^T =
+  // Y^T at rows b / nb of the [rowsB][nb] ones (panel offsets are multiples
+  // of nb).
+  void bind_presplit(int nb, float* Ahi, float* Alo, int64_t rA, float* Bhi, float* Blo, int64_t rB,
+                     int* status) {
+    if (ntiles == 0 || n > 65535) return;
+    const std::vector<GemmProb>& v = h;
+    std::vector<tc::TcProb> tp(n);
+    for (int i = 0; i < n; ++i) {
+      const GemmProb& q = v[i];
+      tp[i] = tc::TcProb{std::max(q.M, 0), std::max(q.N, 0), std::max(q.K, 0), q.ldc, q.c, (int)(q.a / nb),
+                         (int)(q.b / nb)};
+    }
+    tcp.upload(tp);
+    Kp = nb;
+    rowsA = rA;
+    rowsB = rB;
+    tc_status = status;
+    maps[0] = tc::encode_kmajor(Ahi, rA, nb);
+    maps[1] = tc::encode_kmajor(Alo, rA, nb);
+    maps[2] = tc::encode_kmajor(Bhi, rB, nb);
+    maps[3] = tc::encode_kmajor(Blo, rB, nb);
+    tc_planned = false;  // no split arrays in the shared scratch
+    tc_bound = presplit = true;
+  }
   void bind_tc(float* base, int* status) {
     if (!tc_planned) return;
     tc_base = base;
@@ -375,16 +403,18 @@ struct GemmList {
 template <bool TA, bool TB>
 void launch_tc(const GemmList& g, const float* A, const float* B, float* C, float alpha, float beta,
                cudaStream_t s) {
-  float* Ah = g.tc_base;
-  float* Al = Ah + g.rowsA * g.Kp;
-  float* Bh = Al + g.rowsA * g.Kp;
-  float* Bl = Bh + g.rowsB * g.Kp;
-  const dim3 ga(cdiv(g.maxM, 32) * (unsigned)(g.Kp / 32), g.n), gb(cdiv(g.maxN, 32) * (unsigned)(g.Kp / 32), g.n);
-  // op(A) rows are A's rows unless TA; op(B)^T rows are B's rows when TB
-  tc::tc_split_kernel<!TA><<<ga, 256, 0, s>>>(g.spa.p, g.Kp, A, Ah, Al);
-  CB_LAUNCH();
-  tc::tc_split_kernel<TB><<<gb, 256, 0, s>>>(g.spb.p, g.Kp, B, Bh, Bl);
-  CB_LAUNCH();
+  if (!g.presplit) {
+    float* Ah = g.tc_base;
+    float* Al = Ah + g.rowsA * g.Kp;
+    float* Bh = Al + g.rowsA * g.Kp;
+    float* Bl = Bh + g.rowsB * g.Kp;
+    const dim3 ga(cdiv(g.maxM, 32) * (unsigned)(g.Kp / 32), g.n), gb(cdiv(g.maxN, 32) * (unsigned)(g.Kp / 32), g.n);
+    // op(A) rows are A's rows unless TA; op(B)^T rows are B's rows when TB
+    tc::tc_split_kernel<!TA><<<ga, 256, 0, s>>>(g.spa.p, g.Kp, A, Ah, Al);
+    CB_LAUNCH();
+    tc::tc_split_kernel<TB><<<gb, 256, 0, s>>>(g.spb.p, g.Kp, B, Bh, Bl);
+    CB_LAUNCH();
+  }
   tc::set_smem_attr();
   // rank-64 sweep updates (two K chunks) are bound by C's traffic: one
   // operand stage and two C buffers; longer K: two stages, one C buffer
@@ -432,7 +462,10 @@ void launch_list(const GemmList& g, const T* A, const T* B, T* C, T alpha, T bet
 }
 
 // --------------------------------------------------------------- sweeps
+// Pivot block width of the sweeps: 64 (FP64 operators, and the FP32 default)
+// or 128 (FP32; half the passes over each matrix for the same flops).
 constexpr int SWEEP_NB = 64;
+constexpr int SWEEP_NB_MAX = 128;
 
 struct SweepDesc {
   int rows, cols, ld, p;  // matrix shape, leading dimension, pivots to sweep
@@ -443,23 +476,27 @@ struct SweepDesc {
 };
 
 // P = inverse of the kb x kb diagonal block of pivot step k, by Gauss-Jordan
-// in the operator precision T.  Thread (c, g) = (tid % 64, tid / 64) keeps
-// rows [16 g, 16 g + 16) of column c in registers, so the 256 threads keep
-// all four SM sub-partitions busy (the FP64 case of the coarse matrix needs
-// every FP64 unit).  At pivot j every thread reads the old pivot column and
-// pivot row from a double-buffered shared copy, updates its entries
+// in the operator precision T.  Thread (c, g) = (tid % NB, tid / NB) keeps
+// RG rows of column c in registers (16 of 256 threads for NB = 64, 32 of
+// 512 for NB = 128), so all four SM sub-partitions stay busy (the FP64
+// coarse matrix needs every FP64 unit).  At pivot j every thread reads
+// the old pivot column and pivot row from a double-buffered shared copy,
+// updates its entries
 //   a[j][c] <- a[j][c] / p,  a[i][c] <- a[i][c] - a[i][j] a[j][c] / p (c != j),
 //   a[i][j] <- -a[i][j] / p, a[j][j] <- 1 / p,
 // and the owners of column j + 1 and row j + 1 publish them into the other
 // buffer, so one barrier per pivot suffices.
+// Threads of the diagonal-block kernel: 256 for NB = 64 (16 rows of one
+// column per thread), 512 for NB = 128 (32 rows per thread).
+template <int NB>
+struct DiagThreads { static constexpr int value = NB <= 64 ? 256 : 512; };
 constexpr int DIAG_THREADS = 256;
-template <typename T>
-__global__ void __launch_bounds__(DIAG_THREADS)
+template <typename T, int NB>
+__global__ void __launch_bounds__(DiagThreads<NB>::value)
 sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat, T* __restrict__ Pbuf,
                   int* __restrict__ status, double tol) {
-  constexpr int NB = SWEEP_NB;
-  constexpr int RG = NB / (DIAG_THREADS / NB);  // rows per thread
-  __shared__ T blk[NB][NB + 1];
+  constexpr int NT = DiagThreads<NB>::value;
+  constexpr int RG = NB / (NT / NB);  // rows per thread
   __shared__ T colb[2][NB], rowb[2][NB];
   __shared__ double piv_scale;
   __shared__ int bad;
@@ -470,15 +507,11 @@ sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat
   const int tid = threadIdx.x;
   const int c = tid % NB, r0 = (tid / NB) * RG;
   const T* A = mat + d.off + (int64_t)k0 * d.ld + k0;
-  for (int t = tid; t < NB * NB; t += DIAG_THREADS) {
-    const int i = t / NB, cc = t % NB;
-    blk[i][cc] = (i < kb && cc < kb) ? A[(int64_t)i * d.ld + cc] : T(0);
-  }
   if (tid == 0) bad = 0;
-  __syncthreads();
   T a[RG];
 #pragma unroll
-  for (int q = 0; q < RG; ++q) a[q] = blk[r0 + q][c];
+  for (int q = 0; q < RG; ++q)
+    a[q] = (r0 + q < kb && c < kb) ? A[(int64_t)(r0 + q) * d.ld + c] : T(0);
   if (c == 0) {
 #pragma unroll
     for (int q = 0; q < RG; ++q) colb[0][r0 + q] = a[q];
@@ -487,7 +520,7 @@ sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat
   // scale of the pivots: largest |diagonal| of the block
   if (tid < 32) {
     double dv = 0.0;
-    for (int i = tid; i < kb; i += 32) dv = fmax(dv, fabs((double)blk[i][i]));
+    for (int i = tid; i < kb; i += 32) dv = fmax(dv, fabs((double)A[(int64_t)i * d.ld + i]));
     for (int o = 16; o > 0; o >>= 1) dv = fmax(dv, __shfl_xor_sync(0xffffffffu, dv, o));
     if (tid == 0) piv_scale = dv;
   }
@@ -540,17 +573,32 @@ sweep_diag_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat
 // part reads pivot rows outside the pivot columns, the X part reads pivot
 // columns outside the pivot rows (the pivot block itself is read only into
 // Y entries that are replaced by P).  Narrow chunks keep many CTAs in flight
-// (a single coarse matrix still spreads over the GPU); each thread forms 4
-// rows of one Y column and gathers its 4 X entries before storing.
+// (a single coarse matrix still spreads over the GPU); each thread forms
+// NB / 16 rows of one Y column and gathers its NB / 16 X entries before
+// storing.  Shared memory (dynamic): P (NB x NB+1) and the chunk of pivot
+// rows (NB x CH+1).
 constexpr int PANEL_CH = 16;
-template <typename T>
+template <typename T, int NB>
+constexpr size_t panel_smem_bytes() {
+  return sizeof(T) * ((size_t)NB * (NB + 1) + (size_t)NB * (PANEL_CH + 1));
+}
+
+//
+// SPLIT (FP32 operators on the tensor cores): the panels are written as the
+// K-major TF32 hi/lo operands of the update GEMM instead, X_hi/X_lo (rows x
+// NB) at Xbuf/Xlo and Y^T_hi/Y^T_lo (columns x NB) at Ybuf/Ylo, with zeros
+// beyond the kb pivots of a partial last block, so the update needs no
+// separate split pass.
+template <typename T, int NB, bool SPLIT>
 __global__ void __launch_bounds__(256)
 sweep_panel_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat,
-                   const T* __restrict__ Pbuf, T* __restrict__ Xbuf, T* __restrict__ Ybuf) {
-  constexpr int NB = SWEEP_NB, CH = PANEL_CH, PER = NB * CH / 256;
-  static_assert(NB == 64 && CH == 16 && PER == 4, "4 x 1 register tiles over 256 threads");
-  __shared__ T Ps[NB][NB + 1];
-  __shared__ T col[NB][CH + 1];
+                   const T* __restrict__ Pbuf, T* __restrict__ Xbuf, T* __restrict__ Ybuf,
+                   T* __restrict__ Xlo, T* __restrict__ Ylo) {
+  constexpr int CH = PANEL_CH, PER = NB * CH / 256, RY = NB / 16;
+  static_assert(CH == 16 && NB % 16 == 0, "NB / 16 rows of one column per thread");
+  extern __shared__ __align__(16) unsigned char panel_smem[];
+  T (*Ps)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(panel_smem);
+  T (*col)[CH + 1] = reinterpret_cast<T (*)[CH + 1]>(panel_smem + sizeof(T) * NB * (NB + 1));
   const SweepDesc d = desc[blockIdx.y];
   const int k0 = k * NB;
   if (k0 >= d.p) return;
@@ -571,8 +619,8 @@ sweep_panel_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ ma
     }
     // pivot rows restricted to this column chunk (zero outside kb x cn)
     for (int t = tid; t < NB * CH; t += 256) {
-      const int r = t / CH, c = t % CH;
-      col[r][c] = (r < kb && c < cn) ? A[(int64_t)(k0 + r) * d.ld + c0 + c] : T(0);
+      const int r = t / CH, cc = t % CH;
+      col[r][cc] = (r < kb && cc < cn) ? A[(int64_t)(k0 + r) * d.ld + c0 + cc] : T(0);
     }
   }
   // X[i, :] = A[i, kk] (i outside kk), X[kk] = -I ; then A[i, kk] = 0
@@ -586,7 +634,16 @@ sweep_panel_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ ma
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int t = tid + 256 * u, r = t / NB, q = t % NB, i = c0 + r;
-      if (r < rn && q < kb) {
+      if (SPLIT) {
+        if (r < rn) {
+          const bool piv = i >= k0 && i < k0 + kb;
+          const T x = q < kb ? (piv ? ((i - k0 == q) ? T(-1) : T(0)) : xv[u]) : T(0);
+          const T h = tc::tf32_round(x);
+          X[(int64_t)i * NB + q] = h;
+          Xlo[d.offX + (int64_t)i * NB + q] = tc::tf32_round(x - h);
+          if (q < kb) A[(int64_t)i * d.ld + k0 + q] = T(0);
+        }
+      } else if (r < rn && q < kb) {
         const bool piv = i >= k0 && i < k0 + kb;
         X[(int64_t)i * NB + q] = piv ? ((i - k0 == q) ? T(-1) : T(0)) : xv[u];
         A[(int64_t)i * d.ld + k0 + q] = T(0);
@@ -596,19 +653,30 @@ sweep_panel_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ ma
   if (cn == 0) return;
   __syncthreads();
   // Y[r, j] = sum_q P[r][q] A[k0+q, j]  (j outside kk),  Y[:, kk] = P
-  const int ty = tid / CH, c = tid % CH;   // rows 4 ty .. 4 ty + 3 of column c
-  T acc[4] = {T(0), T(0), T(0), T(0)};
+  const int ty = tid / CH, c = tid % CH;   // rows RY ty .. RY ty + RY - 1 of column c
+  T acc[RY];
+#pragma unroll
+  for (int i = 0; i < RY; ++i) acc[i] = T(0);
   for (int q = 0; q < kb; ++q) {
     const T cq = col[q][c];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i] = fma(Ps[4 * ty + i][q], cq, acc[i]);
+    for (int i = 0; i < RY; ++i) acc[i] = fma(Ps[RY * ty + i][q], cq, acc[i]);
   }
   if (c >= cn) return;
   const int jg = c0 + c;
   const bool pivc = jg >= k0 && jg < k0 + kb;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = 4 * ty + i;
+  for (int i = 0; i < RY; ++i) {
+    const int r = RY * ty + i;
+    if (SPLIT) {
+      // Y^T row jg, K index r (zero beyond kb)
+      const T y = r < kb ? (pivc ? Ps[r][jg - k0] : acc[i]) : T(0);
+      const T h = tc::tf32_round(y);
+      Y[(int64_t)jg * NB + r] = h;
+      Ylo[d.offY + (int64_t)jg * NB + r] = tc::tf32_round(y - h);
+      if (r < kb) A[(int64_t)(k0 + r) * d.ld + jg] = T(0);
+      continue;
+    }
     if (r >= kb) continue;
     Y[(int64_t)r * d.ld + jg] = pivc ? Ps[r][jg - k0] : acc[i];
     A[(int64_t)(k0 + r) * d.ld + jg] = T(0);

@@ -17,5 +17,5 @@ Conventions (they are part of the library's public input format):
   paper; a Dirichlet node has all three components clamped.
 """
 from .slab import slab_problem, slab_config, SLAB_CONFIGS, box_groups  # noqa: F401
-from .lv import lv_problem, lv_config, LV_CONFIGS  # noqa: F401
+from .lv import lv_problem, lv_config, lv_part_problem, clamped_parts, LV_CONFIGS  # noqa: F401
 from .material import default_material  # noqa: F401

@@ -374,3 +374,51 @@ def lv_config(name, **overrides):
     kw = dict(LV_CONFIGS[name])
     kw.update(overrides)
     return lv_problem(**kw)
+
+
+def lv_part_problem(prob, parts):
+    """The part of a ventricle workload that lies in the given level-1
+    subdomains, as a workload of its own: their elements, the nodes of those
+    renumbered in increasing order, the clamped base nodes and endocardial
+    pressure faces among them, the nodal fibres, material and loads
+    unchanged, and the subdomains renumbered 0, 1, ... in increasing order.
+    Nodes on the cut are left free (traction-free), so it is a sample of the
+    workload's element, subdomain and load structure, not a piece of its
+    solution."""
+    epart = np.asarray(prob["elem_part"])
+    keep_part = np.zeros(int(prob["n_parts"]), dtype=bool)
+    keep_part[np.asarray(parts)] = True
+    sel = np.nonzero(keep_part[epart])[0]
+    elems = np.asarray(prob["elems"])[sel]
+    nodes = np.unique(elems)
+    new_id = -np.ones(len(prob["coords"]), dtype=np.int64)
+    new_id[nodes] = np.arange(nodes.size)
+    used, local_part = np.unique(epart[sel], return_inverse=True)
+    pf = np.asarray(prob["pressure_faces"])
+    emap = -np.ones(len(prob["elems"]), dtype=np.int64)
+    emap[sel] = np.arange(sel.size)
+    keep = emap[pf[:, 0]] >= 0
+    dn = np.asarray(prob["dirichlet_nodes"])
+    dn = dn[new_id[dn] >= 0]
+    fib = prob["fibers"]
+    out = dict(prob)
+    out.pop("part2", None)
+    out.pop("n_parts2", None)
+    out.update({
+        "coords": np.asarray(prob["coords"])[nodes],
+        "elems": new_id[elems].astype(np.int32),
+        "elem_part": local_part.astype(np.int32),
+        "n_parts": int(used.size),
+        "dirichlet_nodes": np.sort(new_id[dn]).astype(np.int32),
+        "pressure_faces": np.stack([emap[pf[keep, 0]], pf[keep, 1]], axis=1).astype(np.int32),
+        "fibers": {"kind": "nodal", "f": np.asarray(fib["f"])[nodes], "n": np.asarray(fib["n"])[nodes]},
+    })
+    return out
+
+
+def clamped_parts(prob):
+    """Level-1 subdomains that contain clamped (base) nodes, increasing."""
+    isdir = np.zeros(len(prob["coords"]), dtype=bool)
+    isdir[np.asarray(prob["dirichlet_nodes"])] = True
+    touch = isdir[np.asarray(prob["elems"])].any(axis=1)
+    return np.unique(np.asarray(prob["elem_part"])[touch])
