@@ -432,13 +432,15 @@ enum {
                                      and the coarse inverse)                  */
 };
 
-/* Selects the kernel of the FP32 setup GEMMs for every BDDC setup run
-   afterwards in this process: 1 (the default) = tcgen05 tensor cores with
-   the three-term TF32 split (FP32-level accuracy), 0 = FP32 CUDA-core
-   kernels.  Returns the previous setting.  Host-side state, not thread
-   safe; a diagnostic and comparison switch, the results agree to FP32
-   rounding. */
-CBDDC_API int cbddc_set_tensor_cores(int enable);
+/* Selects the kernels of the FP32 setup GEMMs.  mode bit 0: tcgen05 tensor
+   cores with operands split into TF32 parts (else the FP32 CUDA cores);
+   bit 1: three parts (six products, FP32-level accuracy) for the
+   Gauss-Jordan sweep updates, else two (three products); bit 2: the same
+   for the other setup products.  Default 3 (tensor cores, three-part sweep
+   updates).  The enable bit is read at every setup, the part counts when a
+   context is created.  Returns the previous mode.  Host-side state, not
+   thread safe; a diagnostic and comparison switch. */
+CBDDC_API int cbddc_set_tensor_cores(int mode);
 
 /* Starts recording CUDA events around every launch of the given class (and
    stops recording every other class), on the stream the launch uses (at

@@ -215,10 +215,16 @@ def load_library():
     return lib
 
 
-def set_tensor_cores(enable):
-    """FP32 setup GEMMs on the tcgen05 tensor cores (True, the default) or
-    on the FP32 CUDA cores (False); returns the previous setting."""
-    return bool(load_library().cbddc_set_tensor_cores(1 if enable else 0))
+def set_tensor_cores(mode):
+    """FP32 setup GEMMs: mode bit 0 = tcgen05 tensor cores (else the FP32
+    CUDA cores), bit 1 = three TF32 parts for the sweep updates, bit 2 =
+    three parts for the other products (True means the default, 3; False
+    means 0).  Returns the previous mode."""
+    if mode is True:
+        mode = 3
+    elif mode is False:
+        mode = 0
+    return int(load_library().cbddc_set_tensor_cores(int(mode)))
 
 
 def kernel_launches():

@@ -1354,67 +1354,83 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     // sweep updates: operands written split by the panel kernel into
     // Xp/Xlo ([rows][nb]) and Yp/Ylo ([columns][nb])
     const int nb = C->nb;
+    const int ps = tc_parts(true), po = tc_parts(false);
+    C->tc_parts_sweep = ps;
+    C->tc_parts_other = po;
     C->Xlo.alloc(std::max<size_t>(C->Xp.bytes() / 4, 1));
     C->Ylo.alloc(std::max<size_t>(C->Yp.bytes() / 4, 1));
-    float* xh = reinterpret_cast<float*>(C->Xp.p);
-    float* yh = reinterpret_cast<float*>(C->Yp.p);
+    if (ps == 3) {
+      C->Xlo2.alloc(std::max<size_t>(C->Xp.bytes() / 4, 1));
+      C->Ylo2.alloc(std::max<size_t>(C->Yp.bytes() / 4, 1));
+    }
+    float* xs[3] = {reinterpret_cast<float*>(C->Xp.p), C->Xlo.p, C->Xlo2.p};
+    float* ys[3] = {reinterpret_cast<float*>(C->Yp.p), C->Ylo.p, C->Ylo2.p};
     const int64_t rx = (int64_t)(C->Xp.bytes() / 4) / nb, ry = (int64_t)(C->Yp.bytes() / 4) / nb;
     for (auto* v : {&C->gl_sw1, &C->gl_sw2, &C->gl_swg})
       for (auto& g : *v)
-        if (rx > 0 && ry > 0) g.bind_presplit(nb, xh, C->Xlo.p, rx, yh, C->Ylo.p, ry, P->status.p);
+        if (rx > 0 && ry > 0) g.bind_presplit(nb, ps, xs, rx, ys, ry, P->status.p);
     if (C->DX.bytes() > 0) {
       C->DXlo.alloc(C->DX.bytes() / 4);
       C->DYlo.alloc(C->DY.bytes() / 4);
+      if (ps == 3) {
+        C->DXlo2.alloc(C->DX.bytes() / 4);
+        C->DYlo2.alloc(C->DY.bytes() / 4);
+      }
+      float* dxs[3] = {reinterpret_cast<float*>(C->DX.p), C->DXlo.p, C->DXlo2.p};
+      float* dys[3] = {reinterpret_cast<float*>(C->DY.p), C->DYlo.p, C->DYlo2.p};
       const int64_t dx = (int64_t)(C->DX.bytes() / 4) / nb, dy = (int64_t)(C->DY.bytes() / 4) / nb;
       for (auto& g : C->gl_swd)
-        if (dx > 0 && dy > 0)
-          g.bind_presplit(nb, reinterpret_cast<float*>(C->DX.p), C->DXlo.p, dx, reinterpret_cast<float*>(C->DY.p),
-                          C->DYlo.p, dy, P->status.p);
+        if (dx > 0 && dy > 0) g.bind_presplit(nb, ps, dxs, dx, dys, dy, P->status.p);
     }
     std::vector<GemmList*> lists{&C->gl_E, &C->gl_S, &C->gl_W, &C->gl_T, &C->gl_PhiA, &C->gl_SPhi, &C->gl_Kc,
                                  &C->gl_PsiV, &C->gl_dlx};
     for (auto* v : {&C->gl_sw1, &C->gl_sw2, &C->gl_swg, &C->gl_swd})
       for (auto& g : *v) lists.push_back(&g);
     int64_t need = 0;
-    for (auto* g : lists) need = std::max(need, g->tc_floats());
+    for (auto* g : lists) need = std::max(need, g->tc_floats(po));
     if (need > 0) {
       C->tc_scratch.alloc((size_t)need);
-      for (auto* g : lists) g->bind_tc(C->tc_scratch.p, P->status.p);
+      for (auto* g : lists) g->bind_tc(C->tc_scratch.p, po, P->status.p);
     }
   }
 }
 
 // ------------------------------------------------------------------- setup
-template <typename T, int NB, bool SPLIT>
+template <typename T, int NB, int NP>
 static void panel_launch(dim3 grid, cudaStream_t s, const SweepDesc* desc, int k, T* mat, const T* Pbuf, T* X,
-                         T* Y, T* Xlo, T* Ylo) {
+                         T* Y, T* const* lo) {
   constexpr size_t smem = panel_smem_bytes<T, NB>();
   static bool attr = false;
   if (!attr) {
-    CB_CUDA(cudaFuncSetAttribute(sweep_panel_kernel<T, NB, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CB_CUDA(cudaFuncSetAttribute(sweep_panel_kernel<T, NB, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     attr = true;
   }
-  sweep_panel_kernel<T, NB, SPLIT><<<grid, 256, smem, s>>>(desc, k, mat, Pbuf, X, Y, Xlo, Ylo);
+  sweep_panel_kernel<T, NB, NP><<<grid, 256, smem, s>>>(desc, k, mat, Pbuf, X, Y, lo[0], lo[1], lo[2], lo[3]);
   CB_LAUNCH();
 }
 
 // One sweep: per pivot block the diagonal inverse, the panels and the
 // rank-NB update.  FP32 lists bound to the tensor cores get their panels as
 // split TF32 operands (X, Xlo, Y^T, Ylo) and skip the split pass.
+// lo: the further TF32 parts of the panels {Xlo, Ylo, Xlo2, Ylo2} (FP32
+// tensor-core lists; the list's part count selects how many are written).
 template <typename T, int NB>
 static void run_sweep_nb(const DVec<SweepDesc>& desc, int nmat, const std::vector<GemmList>& lists,
                          int maxRows, int maxCols, T* mat, T* X, T* Y, T* Pbuf, int* status, double tol,
-                         cudaStream_t s, T* Xlo, T* Ylo) {
+                         cudaStream_t s, T* const* lo) {
+  T* const none[4] = {nullptr, nullptr, nullptr, nullptr};
   for (int k = 0; k < (int)lists.size(); ++k) {
     sweep_diag_kernel<T, NB><<<nmat, DiagThreads<NB>::value, 0, s>>>(desc.p, k, mat, Pbuf, status, tol);
     CB_LAUNCH();
     dim3 grid(cdiv(std::max(maxRows, maxCols), PANEL_CH), nmat);
-    const bool split = sizeof(T) == 4 && lists[k].presplit && tensor_cores_enabled();
-    if (split)
-      panel_launch<T, NB, true>(grid, s, desc.p, k, mat, Pbuf, X, Y, Xlo, Ylo);
+    const bool split = sizeof(T) == 4 && lists[k].presplit && lists[k].tc_bound && tensor_cores_for(true);
+    if (split && lists[k].np == 3)
+      panel_launch<T, NB, 3>(grid, s, desc.p, k, mat, Pbuf, X, Y, lo);
+    else if (split)
+      panel_launch<T, NB, 2>(grid, s, desc.p, k, mat, Pbuf, X, Y, lo);
     else
-      panel_launch<T, NB, false>(grid, s, desc.p, k, mat, Pbuf, X, Y, nullptr, nullptr);
+      panel_launch<T, NB, 0>(grid, s, desc.p, k, mat, Pbuf, X, Y, none);
     launch_list<T, false, false>(lists[k], X, Y, mat, T(-1), T(1), s);
   }
 }
@@ -1423,15 +1439,16 @@ static void run_sweep_nb(const DVec<SweepDesc>& desc, int nmat, const std::vecto
 template <typename T>
 static void run_sweep(const DVec<SweepDesc>& desc, int nmat, const std::vector<GemmList>& lists,
                       int maxRows, int maxCols, T* mat, T* X, T* Y, T* Pbuf, int* status, double tol,
-                      cudaStream_t s, int nb = SWEEP_NB, T* Xlo = nullptr, T* Ylo = nullptr) {
+                      cudaStream_t s, int nb = SWEEP_NB, T* const* lo = nullptr) {
+  T* const none[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (!lo) lo = none;
   if constexpr (sizeof(T) == 4) {
     if (nb == SWEEP_NB_MAX) {
-      run_sweep_nb<T, SWEEP_NB_MAX>(desc, nmat, lists, maxRows, maxCols, mat, X, Y, Pbuf, status, tol, s, Xlo,
-                                    Ylo);
+      run_sweep_nb<T, SWEEP_NB_MAX>(desc, nmat, lists, maxRows, maxCols, mat, X, Y, Pbuf, status, tol, s, lo);
       return;
     }
   }
-  run_sweep_nb<T, SWEEP_NB>(desc, nmat, lists, maxRows, maxCols, mat, X, Y, Pbuf, status, tol, s, Xlo, Ylo);
+  run_sweep_nb<T, SWEEP_NB>(desc, nmat, lists, maxRows, maxCols, mat, X, Y, Pbuf, status, tol, s, lo);
 }
 
 template <typename T>
@@ -1461,9 +1478,9 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
   CB_LAUNCH();
   // 2. interior elimination: A_II^-1 by a sweep of the II block, then
   //    E = A_II^-1 A_IG and S = A_GG - A_GI E, and E stored over A_IG
-  T* Xlo = reinterpret_cast<T*>(C->Xlo.p);
-  T* Ylo = reinterpret_cast<T*>(C->Ylo.p);
-  run_sweep<T>(C->sw1, nsub, C->gl_sw1, C->maxI, C->maxI, Aloc, Xp, Yp, Pd, status, tol, s, C->nb, Xlo, Ylo);
+  T* const lo[4] = {reinterpret_cast<T*>(C->Xlo.p), reinterpret_cast<T*>(C->Ylo.p),
+                    reinterpret_cast<T*>(C->Xlo2.p), reinterpret_cast<T*>(C->Ylo2.p)};
+  run_sweep<T>(C->sw1, nsub, C->gl_sw1, C->maxI, C->maxI, Aloc, Xp, Yp, Pd, status, tol, s, C->nb, lo);
   if (C->maxG == 0) return;  // one subdomain: no interface
   launch_list<T, false, false>(C->gl_E, Aloc, Aloc, Et, T(1), T(0), s);
   launch_list<T, false, false>(C->gl_S, Aloc, Et, Aloc, T(-1), T(1), s);
@@ -1487,9 +1504,10 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
     deluxe_sum_kernel<T><<<gk, 256, 0, s>>>(C->dcls_ptr.p, C->dcls_blk.p, C->dlx_n.p, C->dlx_ld.p,
                                                    C->dlx_off.p, C->dcls_off.p, Dsb, Dsh);
     CB_LAUNCH();
+    T* const dlo[4] = {reinterpret_cast<T*>(C->DXlo.p), reinterpret_cast<T*>(C->DYlo.p),
+                       reinterpret_cast<T*>(C->DXlo2.p), reinterpret_cast<T*>(C->DYlo2.p)};
     run_sweep<T>(C->swd, C->n_dcls, C->gl_swd, C->maxDn, C->maxDn, Dsh, reinterpret_cast<T*>(C->DX.p),
-                 reinterpret_cast<T*>(C->DY.p), reinterpret_cast<T*>(C->DP.p), status, tol, s, C->nb,
-                 reinterpret_cast<T*>(C->DXlo.p), reinterpret_cast<T*>(C->DYlo.p));
+                 reinterpret_cast<T*>(C->DY.p), reinterpret_cast<T*>(C->DP.p), status, tol, s, C->nb, dlo);
     launch_list<T, false, false>(C->gl_dlx, Dsh, Dsb, Ddb, T(1), T(0), s);
     deluxe_transpose_kernel<T><<<gb, 256, 0, s>>>(C->dlx_n.p, C->dlx_ld.p, C->dlx_off.p, Ddb,
                                                         reinterpret_cast<T*>(C->Deb.p));
@@ -1504,7 +1522,7 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
                                           C->cons_idx.p, C->cons_w.p, C->d_offS.p, C->d_ldS.p, Sw);
     CB_LAUNCH();
   }
-  run_sweep<T>(C->sw2, nsub, C->gl_sw2, C->maxG, C->maxG, Sw, Xp, Yp, Pd, status, tol, s, C->nb, Xlo, Ylo);
+  run_sweep<T>(C->sw2, nsub, C->gl_sw2, C->maxG, C->maxG, Sw, Xp, Yp, Pd, status, tol, s, C->nb, lo);
   // 4. average constraints
   if (C->maxA > 0) {
     cons_y_kernel<T><<<dim3(cdiv(C->maxR, 8), nsub), 256, 0, s>>>(
@@ -1519,7 +1537,7 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
         C->d_na.p, C->d_offCon.p, C->cons_ptr.p, C->cons_idx.p, C->cons_w.p, C->d_offY.p, C->d_ldY.p,
         C->d_offG.p, C->d_ldG.p, Y, G);
     CB_LAUNCH();
-    run_sweep<T>(C->swg, nsub, C->gl_swg, C->maxA, C->maxA, G, Xp, Yp, Pd, status, tol, s, C->nb, Xlo, Ylo);
+    run_sweep<T>(C->swg, nsub, C->gl_swg, C->maxA, C->maxA, G, Xp, Yp, Pd, status, tol, s, C->nb, lo);
     launch_list<T, false, false>(C->gl_W, G, Zf, Wf, T(1), T(0), s);
     launch_list<T, false, false>(C->gl_T, Y, Wf, Sw, T(-1), T(1), s);
     launch_list<T, false, false>(C->gl_PhiA, Y, G, Phi, T(1), T(0), s);

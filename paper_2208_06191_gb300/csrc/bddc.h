@@ -29,7 +29,9 @@ struct bddc_ctx {
   // local operators (element type float or double, raw storage)
   cbddc::DVec<unsigned char> Aloc, Sw, Phi, Y, Zf, Wf, G, SPhi, Kc, Xp, Yp, Pd, Et;
   cbddc::DVec<float> tc_scratch;            // split operands of the tensor-core GEMMs (FP32)
-  cbddc::DVec<float> Xlo, Ylo, DXlo, DYlo;  // low TF32 parts of the sweep panels (FP32)
+  cbddc::DVec<float> Xlo, Ylo, DXlo, DYlo;  // second TF32 parts of the sweep panels (FP32)
+  cbddc::DVec<float> Xlo2, Ylo2, DXlo2, DYlo2;  // third parts (three-part split)
+  int tc_parts_sweep = 0, tc_parts_other = 0;  // TF32 parts per operand chosen at creation
   // apply maps
   cbddc::DVec<int> gdofI, gdofG, gam_if, if_dof, if_ptr, if_src;
   cbddc::DVec<double> Dg;

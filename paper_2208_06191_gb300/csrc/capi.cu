@@ -19,8 +19,16 @@ void set_last_error(const std::string& msg) { g_last_error = msg; }
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-static std::atomic<bool> g_tensor_cores{true};
-bool tensor_cores_enabled() { return g_tensor_cores.load(std::memory_order_relaxed); }
+// bit 0: tensor cores on; bit 1: three-part split for the sweep updates;
+// bit 2: three-part split for the other FP32 setup products
+static std::atomic<int> g_tensor_cores{1};
+bool tensor_cores_enabled() { return (g_tensor_cores.load(std::memory_order_relaxed) & 1) != 0; }
+bool tensor_cores_for(bool sweep) {
+  const int m = g_tensor_cores.load(std::memory_order_relaxed);
+  return (m & 1) && !(m & (sweep ? 16 : 8));
+}
+bool tc_sweep_ks1() { return (g_tensor_cores.load(std::memory_order_relaxed) & 32) == 0; }
+int tc_parts(bool sweep) { return (g_tensor_cores.load(std::memory_order_relaxed) & (sweep ? 2 : 4)) ? 3 : 2; }
 
 // Launch timer: event pairs recorded on the launching stream, one pool per
 // kernel class; several classes can be recorded at the same time.
@@ -528,10 +536,7 @@ const char* cbddc_last_error(void) { return g_last_error.c_str(); }
 
 uint64_t cbddc_kernel_launches(void) { return g_launches.load(); }
 
-int cbddc_set_tensor_cores(int enable) {
-  const bool prev = g_tensor_cores.exchange(enable != 0);
-  return prev ? 1 : 0;
-}
+int cbddc_set_tensor_cores(int mode) { return g_tensor_cores.exchange(mode & 63); }
 
 int cbddc_timer_start(int kernel_class) {
   return guard([&] {

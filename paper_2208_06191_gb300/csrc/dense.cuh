@@ -29,9 +29,15 @@ struct GemmProb {
   int64_t a, b, c;  // element offsets from the kernel's base pointers
 };
 
-// FP32 setup GEMMs run on the tensor cores (tcgen05, 3xTF32) unless this is
-// cleared (cbddc_set_tensor_cores); the FP64 path always uses the SIMT kernels.
+// FP32 setup GEMMs run on the tensor cores (tcgen05, split TF32) unless
+// this is cleared (cbddc_set_tensor_cores); the FP64 path always uses the
+// SIMT kernels.  tc_parts(sweep) is the number of TF32 parts per operand
+// (2 or 3) for sweep updates and for the other products, read when a
+// context is created.
 bool tensor_cores_enabled();
+bool tensor_cores_for(bool sweep);  // per kind of list (sweep updates / other products)
+bool tc_sweep_ks1();                 // sweep updates accumulate one K-step per TMEM slice
+int tc_parts(bool sweep);
 
 template <typename T> struct GemmCfg;
 template <> struct GemmCfg<float> { static constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8; };
@@ -307,7 +313,8 @@ struct GemmList {
   DVec<tc::SplitProb> spa, spb;
   float* tc_base = nullptr;
   int* tc_status = nullptr;
-  CUtensorMap maps[4];
+  int np = 2;  // TF32 parts per operand
+  tc::TcMaps maps;
   std::vector<GemmProb> h;  // host copy of the problems
   void set(const std::vector<GemmProb>& v, size_t esize, bool ta = false) {
     h = v;
@@ -358,12 +365,12 @@ struct GemmList {
     tc_planned = true;
   }
   // floats of split operands this list needs
-  int64_t tc_floats() const { return tc_planned ? 2 * (rowsA + rowsB) * (int64_t)Kp : 0; }
+  int64_t tc_floats(int parts) const { return tc_planned ? parts * (rowsA + rowsB) * (int64_t)Kp : 0; }
   // Sweep updates whose operands the panel kernel writes already split:
   // op(A) = X at rows a / nb of the [rowsA][nb] hi/lo arrays, op(B)^T =
   // Y^T at rows b / nb of the [rowsB][nb] ones (panel offsets are multiples
   // of nb).
-  void bind_presplit(int nb, float* Ahi, float* Alo, int64_t rA, float* Bhi, float* Blo, int64_t rB,
+  void bind_presplit(int nb, int parts, float* const* Ap, int64_t rA, float* const* Bp, int64_t rB,
                      int* status) {
     if (ntiles == 0 || n > 65535) return;
     const std::vector<GemmProb>& v = h;
@@ -378,21 +385,25 @@ struct GemmList {
     rowsA = rA;
     rowsB = rB;
     tc_status = status;
-    maps[0] = tc::encode_kmajor(Ahi, rA, nb);
-    maps[1] = tc::encode_kmajor(Alo, rA, nb);
-    maps[2] = tc::encode_kmajor(Bhi, rB, nb);
-    maps[3] = tc::encode_kmajor(Blo, rB, nb);
+    np = parts;
+    for (int q = 0; q < np; ++q) {
+      maps.a[q] = tc::encode_kmajor(Ap[q], rA, nb);
+      maps.b[q] = tc::encode_kmajor(Bp[q], rB, nb);
+    }
     tc_planned = false;  // no split arrays in the shared scratch
     tc_bound = presplit = true;
   }
-  void bind_tc(float* base, int* status) {
+  // split arrays in the scratch: the parts of op(A) ([rowsA][Kp] each),
+  // then those of op(B)^T ([rowsB][Kp] each)
+  void bind_tc(float* base, int parts, int* status) {
     if (!tc_planned) return;
     tc_base = base;
     tc_status = status;
-    maps[0] = tc::encode_kmajor(base, rowsA, Kp);
-    maps[1] = tc::encode_kmajor(base + rowsA * Kp, rowsA, Kp);
-    maps[2] = tc::encode_kmajor(base + 2 * rowsA * Kp, rowsB, Kp);
-    maps[3] = tc::encode_kmajor(base + 2 * rowsA * Kp + rowsB * Kp, rowsB, Kp);
+    np = parts;
+    for (int q = 0; q < np; ++q) {
+      maps.a[q] = tc::encode_kmajor(base + q * rowsA * Kp, rowsA, Kp);
+      maps.b[q] = tc::encode_kmajor(base + np * rowsA * Kp + q * rowsB * Kp, rowsB, Kp);
+    }
     tc_bound = true;
   }
 };
@@ -404,27 +415,40 @@ template <bool TA, bool TB>
 void launch_tc(const GemmList& g, const float* A, const float* B, float* C, float alpha, float beta,
                cudaStream_t s) {
   if (!g.presplit) {
-    float* Ah = g.tc_base;
-    float* Al = Ah + g.rowsA * g.Kp;
-    float* Bh = Al + g.rowsA * g.Kp;
-    float* Bl = Bh + g.rowsB * g.Kp;
+    float* Ap = g.tc_base;
+    float* Bp = Ap + g.np * g.rowsA * g.Kp;
     const dim3 ga(cdiv(g.maxM, 32) * (unsigned)(g.Kp / 32), g.n), gb(cdiv(g.maxN, 32) * (unsigned)(g.Kp / 32), g.n);
     // op(A) rows are A's rows unless TA; op(B)^T rows are B's rows when TB
-    tc::tc_split_kernel<!TA><<<ga, 256, 0, s>>>(g.spa.p, g.Kp, A, Ah, Al);
-    CB_LAUNCH();
-    tc::tc_split_kernel<TB><<<gb, 256, 0, s>>>(g.spb.p, g.Kp, B, Bh, Bl);
+    if (g.np == 3) {
+      tc::tc_split_kernel<!TA, 3><<<ga, 256, 0, s>>>(g.spa.p, g.Kp, A, Ap, g.rowsA * g.Kp);
+      CB_LAUNCH();
+      tc::tc_split_kernel<TB, 3><<<gb, 256, 0, s>>>(g.spb.p, g.Kp, B, Bp, g.rowsB * g.Kp);
+    } else {
+      tc::tc_split_kernel<!TA, 2><<<ga, 256, 0, s>>>(g.spa.p, g.Kp, A, Ap, g.rowsA * g.Kp);
+      CB_LAUNCH();
+      tc::tc_split_kernel<TB, 2><<<gb, 256, 0, s>>>(g.spb.p, g.Kp, B, Bp, g.rowsB * g.Kp);
+    }
     CB_LAUNCH();
   }
   tc::set_smem_attr();
   // rank-64 sweep updates (two K chunks) are bound by C's traffic: one
-  // operand stage and two C buffers; longer K: two stages, one C buffer
+  // operand stage and two C buffers; longer K: two stages and one C buffer
+  // (three-part operands: one stage and two C buffers always)
   const int grid = tc::tc_grid(g.ntiles);
-  if (g.Kp <= 2 * tc::BKC)
-    tc::tc_gemm_kernel<1, 2><<<grid, tc::TC_THREADS, tc::TcSmem<1, 2>::bytes, s>>>(
-        g.tiles.p, g.ntiles, g.tcp.p, g.maps[0], g.maps[1], g.maps[2], g.maps[3], C, alpha, beta, g.tc_status);
-  else
-    tc::tc_gemm_kernel<2, 1><<<grid, tc::TC_THREADS, tc::TcSmem<2, 1>::bytes, s>>>(
-        g.tiles.p, g.ntiles, g.tcp.p, g.maps[0], g.maps[1], g.maps[2], g.maps[3], C, alpha, beta, g.tc_status);
+  const bool ks1 = g.presplit && tc_sweep_ks1();  // sweep updates: one K-step per TMEM slice
+#define CB_TC_LAUNCH(NST, NCB, NP, KS)                                                              \
+  tc::tc_gemm_kernel<NST, NCB, NP, KS><<<grid, tc::TC_THREADS, tc::TcSmem<NST, NCB, NP>::bytes, s>>>( \
+      g.tiles.p, g.ntiles, g.tcp.p, g.maps, C, alpha, beta, g.tc_status)
+  if (g.np == 3) {
+    if (ks1) CB_TC_LAUNCH(1, 2, 3, 1);
+    else CB_TC_LAUNCH(1, 2, 3, 4);
+  } else if (g.Kp <= 2 * tc::BKC) {
+    if (ks1) CB_TC_LAUNCH(1, 2, 2, 1);
+    else CB_TC_LAUNCH(1, 2, 2, 4);
+  } else {
+    CB_TC_LAUNCH(2, 1, 2, 4);
+  }
+#undef CB_TC_LAUNCH
   CB_LAUNCH();
 }
 
@@ -451,7 +475,7 @@ void launch_list(const GemmList& g, const T* A, const T* B, T* C, T alpha, T bet
   const int cls = sizeof(T) == 4 ? CBDDC_TIMER_SWEEP_GEMM : CBDDC_TIMER_SETUP_GEMM_F64;
   timer_begin(cls, s);
   if constexpr (sizeof(T) == 4) {
-    if (g.tc_bound && tensor_cores_enabled()) {
+    if (g.tc_bound && tensor_cores_for(g.presplit)) {
       launch_tc<TA, TB>(g, A, B, C, alpha, beta, s);
       timer_end(cls, s, g.flops, g.bytes);
       return;
@@ -584,16 +608,17 @@ constexpr size_t panel_smem_bytes() {
 }
 
 //
-// SPLIT (FP32 operators on the tensor cores): the panels are written as the
-// K-major TF32 hi/lo operands of the update GEMM instead, X_hi/X_lo (rows x
-// NB) at Xbuf/Xlo and Y^T_hi/Y^T_lo (columns x NB) at Ybuf/Ylo, with zeros
-// beyond the kb pivots of a partial last block, so the update needs no
-// separate split pass.
-template <typename T, int NB, bool SPLIT>
+// NP > 0 (FP32 operators on the tensor cores): the panels are written as the
+// K-major TF32 parts of the update GEMM's operands instead, X parts (rows x
+// NB) at Xbuf, Xlo (, Xlo2) and Y^T parts (columns x NB) at Ybuf, Ylo (,
+// Ylo2), with zeros beyond the kb pivots of a partial last block, so the
+// update needs no separate split pass.
+template <typename T, int NB, int NP>
 __global__ void __launch_bounds__(256)
 sweep_panel_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ mat,
                    const T* __restrict__ Pbuf, T* __restrict__ Xbuf, T* __restrict__ Ybuf,
-                   T* __restrict__ Xlo, T* __restrict__ Ylo) {
+                   T* __restrict__ Xlo, T* __restrict__ Ylo, T* __restrict__ Xlo2, T* __restrict__ Ylo2) {
+  constexpr bool SPLIT = NP > 0;
   constexpr int CH = PANEL_CH, PER = NB * CH / 256, RY = NB / 16;
   static_assert(CH == 16 && NB % 16 == 0, "NB / 16 rows of one column per thread");
   extern __shared__ __align__(16) unsigned char panel_smem[];
@@ -638,9 +663,11 @@ sweep_panel_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ ma
         if (r < rn) {
           const bool piv = i >= k0 && i < k0 + kb;
           const T x = q < kb ? (piv ? ((i - k0 == q) ? T(-1) : T(0)) : xv[u]) : T(0);
-          const T h = tc::tf32_round(x);
-          X[(int64_t)i * NB + q] = h;
-          Xlo[d.offX + (int64_t)i * NB + q] = tc::tf32_round(x - h);
+          float parts[3];
+          tc::split_tf32<NP == 3 ? 3 : 2>((float)x, parts);
+          X[(int64_t)i * NB + q] = parts[0];
+          Xlo[d.offX + (int64_t)i * NB + q] = parts[1];
+          if (NP == 3) Xlo2[d.offX + (int64_t)i * NB + q] = parts[2];
           if (q < kb) A[(int64_t)i * d.ld + k0 + q] = T(0);
         }
       } else if (r < rn && q < kb) {
@@ -671,9 +698,11 @@ sweep_panel_kernel(const SweepDesc* __restrict__ desc, int k, T* __restrict__ ma
     if (SPLIT) {
       // Y^T row jg, K index r (zero beyond kb)
       const T y = r < kb ? (pivc ? Ps[r][jg - k0] : acc[i]) : T(0);
-      const T h = tc::tf32_round(y);
-      Y[(int64_t)jg * NB + r] = h;
-      Ylo[d.offY + (int64_t)jg * NB + r] = tc::tf32_round(y - h);
+      float parts[3];
+      tc::split_tf32<NP == 3 ? 3 : 2>((float)y, parts);
+      Y[(int64_t)jg * NB + r] = parts[0];
+      Ylo[d.offY + (int64_t)jg * NB + r] = parts[1];
+      if (NP == 3) Ylo2[d.offY + (int64_t)jg * NB + r] = parts[2];
       if (r < kb) A[(int64_t)(k0 + r) * d.ld + jg] = T(0);
       continue;
     }

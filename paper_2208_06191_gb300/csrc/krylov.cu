@@ -179,7 +179,7 @@ __device__ void givens_update(int j, int m, double* __restrict__ H, double* __re
                               const double* h2, double wn2, double* __restrict__ scal, double rtol,
                               int* __restrict__ done, int* __restrict__ iters) {
   double* col = H + (int64_t)j * (m + 1);
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  for (int i = 0; i <= j; ++i) col[i] = h2 ? h1[i] + h2[i] : h1[i];
   const double hn = sqrt(fmax(wn2, 0.0));
   col[j + 1] = hn;
   scal[1] = hn > 0.0 ? 1.0 / hn : 0.0;
@@ -328,6 +328,95 @@ __global__ void __launch_bounds__(DOT_THREADS) cgs2_coop_kernel(CgsArgs a) {
   }
 }
 
+// The Arnoldi step for long vectors or long bases in one cooperative
+// launch, by modified Gram-Schmidt (backward stable for GMRES without a
+// second pass, and the oracle's orthogonalisation): each thread keeps
+// RPT rows of w in registers (32-row slices of its warp's segment); for
+// i = 0..j: h_i = v_i . w (block sums, one grid-wide barrier, every CTA
+// adds the CTA partials in CTA order), w -= h_i v_i; then ||w||, the
+// Givens update (CTA 0) and v_{j+1} = w / ||w||.  V is read once per step
+// (the update re-reads the rows of v_i that the thread has just read), and
+// every FP64 FMA of the step is one of the 2 (j + 1) n of MGS.
+constexpr int MGS_THREADS = 640;
+struct MgsArgs {
+  const double* V;   // j + 1 columns of length n (stride n)
+  int64_t n;
+  double* w;
+  double* vnext;
+  double* part;      // [2][gridDim.x]
+  double* hcol;      // [m + 1]: this step's Hessenberg column
+  int j, m;
+  double *H, *cs, *sn, *g, *scal;
+  double rtol;
+  int *done, *iters;
+};
+
+template <int RPT>
+__global__ void __launch_bounds__(MGS_THREADS, 1) mgs_coop_kernel(MgsArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  if (*a.done) return;  // read by every CTA before any barrier: uniform
+  __shared__ double red[MGS_THREADS / 32];
+  __shared__ double hsh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+  // warp-contiguous rows: the warp's segment of 32 RPT rows, lane + 32 k
+  // (coalesced, and the offsets of the k loop are constants)
+  const int64_t base = ((int64_t)blockIdx.x * (MGS_THREADS / 32) + warp) * (32 * RPT) + lane;
+  const int64_t lim = a.n - base;  // row k exists iff 32 k < lim
+  double x[RPT];
+  {
+    const double* wp = a.w + base;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) x[k] = 32 * k < lim ? wp[32 * k] : 0.0;
+  }
+  // grid-wide sum of one value per thread (deterministic), into hsh
+  auto grid_sum = [&](double v, int buf) -> double {
+    v = wsum(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < MGS_THREADS / 32; ++q) t += red[q];
+      a.part[(int64_t)buf * G + blockIdx.x] = t;
+    }
+    grid.sync();
+    if (warp == 0) {
+      double t = 0.0;
+      for (int b = lane; b < G; b += 32) t += __ldcg(a.part + (int64_t)buf * G + b);
+      t = wsum(t);
+      if (lane == 0) hsh = t;
+    }
+    __syncthreads();
+    const double out = hsh;
+    __syncthreads();
+    return out;
+  };
+  for (int i = 0; i <= a.j; ++i) {
+    const double* vp = a.V + (int64_t)i * a.n + base;
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+      if (32 * k < lim) acc = fma(vp[32 * k], x[k], acc);
+    const double h = grid_sum(acc, i & 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.hcol[i] = h;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+      if (32 * k < lim) x[k] = fma(-h, vp[32 * k], x[k]);
+  }
+  double nacc = 0.0;
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) nacc = fma(x[k], x[k], nacc);
+  const double wn2 = grid_sum(nacc, (a.j + 1) & 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    givens_update(a.j, a.m, a.H, a.cs, a.sn, a.g, a.hcol, nullptr, wn2, a.scal, a.rtol, a.done, a.iters);
+  const double hn = sqrt(fmax(wn2, 0.0));
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  double* op = a.vnext + base;
+#pragma unroll
+  for (int k = 0; k < RPT; ++k)
+    if (32 * k < lim) op[32 * k] = x[k] * inv;
+}
+
 __global__ void scale_kernel(const double* __restrict__ w, double* __restrict__ v, int64_t n,
                              const double* __restrict__ scal, int idx, const int* __restrict__ done) {
   if (done && *done) return;
@@ -446,6 +535,26 @@ void Gmres::ensure(int64_t n_, int m_) {
                                                                    std::max<int64_t>(1, tiles / 4))
                                           : 0;
     if (coop_grid > 0) cpart.alloc((size_t)3 * coop_grid * MAXV);
+    // MGS cooperative launch: one CTA of MGS_THREADS per SM, rows per
+    // thread rounded up to 8, 16, 24 or 32 (n up to 3.1M on 152 SMs; 0:
+    // the multi-launch path)
+    mgs_grid = 0;
+    mgs_rpt = 0;
+    if (coop) {
+      const int64_t T = (int64_t)sms * MGS_THREADS;
+      const int64_t need = (n_ + T - 1) / T;
+      const int rpt = need <= 8 ? 8 : need <= 16 ? 16 : need <= 24 ? 24 : need <= 32 ? 32 : 0;
+      int per = 0;
+      if (rpt == 8) CB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mgs_coop_kernel<8>, MGS_THREADS, 0));
+      if (rpt == 16) CB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mgs_coop_kernel<16>, MGS_THREADS, 0));
+      if (rpt == 24) CB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mgs_coop_kernel<24>, MGS_THREADS, 0));
+      if (rpt == 32) CB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mgs_coop_kernel<32>, MGS_THREADS, 0));
+      if (rpt > 0 && per >= 1) {
+        mgs_grid = sms;
+        mgs_rpt = rpt;
+        mpart.alloc((size_t)2 * sms);
+      }
+    }
   }
   CB_CHECK(m_ >= 1 && m_ < MAXR, CBDDC_EINVAL, "restart must be in [1, 1023]");
   n = n_;
@@ -546,11 +655,22 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
       double* wn2 = G.h.p + 2 * G.hstride;
       timer_begin(CBDDC_TIMER_ORTH, s);
       if (G.coop_grid > 0 && j + 1 <= MAXV) {
+        // short vectors and bases: CGS2 in one cooperative launch
         CgsArgs ca{G.V.p, n, j + 1, G.w.p, G.V.p + (int64_t)(j + 1) * n, G.cpart.p, j, m,
                    G.H.p, G.cs.p, G.sn.p, G.g.p, G.scal.p, rtol, done, kcount};
         void* args[] = {&ca};
         CB_CUDA(cudaLaunchCooperativeKernel((const void*)cgs2_coop_kernel, dim3(G.coop_grid),
                                             dim3(DOT_THREADS), args, 0, s));
+        CB_LAUNCH();
+      } else if (G.mgs_grid > 0) {
+        MgsArgs ma{G.V.p, n, G.w.p, G.V.p + (int64_t)(j + 1) * n, G.mpart.p, G.h.p, j, m,
+                   G.H.p, G.cs.p, G.sn.p, G.g.p, G.scal.p, rtol, done, kcount};
+        void* args[] = {&ma};
+        const void* fn = G.mgs_rpt == 8    ? (const void*)mgs_coop_kernel<8>
+                         : G.mgs_rpt == 16 ? (const void*)mgs_coop_kernel<16>
+                         : G.mgs_rpt == 24 ? (const void*)mgs_coop_kernel<24>
+                                           : (const void*)mgs_coop_kernel<32>;
+        CB_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G.mgs_grid), dim3(MGS_THREADS), args, 0, s));
         CB_LAUNCH();
       } else {
         // classical Gram-Schmidt with a second pass only where the first

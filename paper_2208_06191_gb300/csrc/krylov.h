@@ -18,6 +18,8 @@ struct Gmres {
   DVec<unsigned> ticket;
   DVec<double> cpart;        // per-CTA partials of the cooperative orthogonalisation
   int coop_grid = 0;         // its grid size (0: use the multi-launch path)
+  DVec<double> mpart;        // per-CTA partials of the cooperative MGS step
+  int mgs_grid = 0, mgs_rpt = 0;  // its grid and rows per thread (0: not available)
   double* host_scal = nullptr;
   int* host_flags = nullptr;
   void ensure_small(int64_t n_);

@@ -5,11 +5,16 @@
 //
 // Precision: a TF32 operand keeps 10 mantissa bits, too few for explicit
 // inverses of local matrices whose condition numbers reach 1e4.  Every
-// operand x is therefore split into x_hi = tf32(x) and x_lo = tf32(x - x_hi)
-// and the product is accumulated in FP32 as
-//     A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
-// which drops only A_lo B_lo (relative size 2^-22), i.e. FP32-level accuracy
-// with three tensor-core passes.
+// operand x is therefore split into TF32 parts and the product accumulated
+// in FP32 over the significant part products:
+//   NP = 2: x = x1 + x2 + O(2^-22 x), x1 = tf32(x), x2 = tf32(x - x1);
+//           A B ~ A1 B1 + A1 B2 + A2 B1 (three passes, about 2^-21 relative);
+//   NP = 3: x = x1 + x2 + x3 exactly (x3 = x - x1 - x2 has at most a few
+//           significant bits); A B ~ A1 B1 + A1 B2 + A2 B1 + A1 B3 + A3 B1
+//           + A2 B2 (six passes; the dropped products are 2^-33 relative,
+//           FP32-level results).
+// The Gauss-Jordan sweeps need NP = 3 to keep the FP32 path's GMRES
+// iterations within two of the FP64 path's.
 //
 // Data flow of C = alpha op(A) op(B) + beta C for a list of problems:
 //   1. split kernels write op(A) (M x K) and op(B)^T (N x K) as K-major
@@ -47,11 +52,14 @@ namespace tc {
 constexpr int BM = 128, BN = 128;             // output tile
 constexpr int BKC = 32;                       // K per chunk: 32 x 4 B = one 128-byte swizzle row
 constexpr int OPND_BYTES = BM * BKC * 4;      // one operand tile of a chunk (16 KB)
-constexpr int STAGE_BYTES = 4 * OPND_BYTES;   // A_hi, A_lo, B_hi, B_lo
-constexpr int TC_THREADS = 192;               // GEMM: producer, MMA and four epilogue warps
-constexpr int TMEM_COLS = 128;                // one accumulator; the kernel holds two
-constexpr int CLD = BN + 4;                   // row pitch (floats) of the C tile in shared memory
-constexpr int C_BYTES = BM * CLD * 4;         // 67,584 B
+// operand tiles per stage: NP parts of A and NP parts of B (NP = 2: hi, lo;
+// NP = 3: three-way split)
+template <int NP>
+struct TcStage { static constexpr int bytes = 2 * NP * OPND_BYTES; };
+constexpr int TC_THREADS = 320;               // GEMM: producer, MMA and eight epilogue warps
+constexpr int TMEM_COLS = 128;                // one accumulator slice; the kernel holds two
+constexpr int CLD = BN;                       // row pitch (floats) of the C tile in shared memory
+constexpr int C_BYTES = BM * CLD * 4;         // 64 KB; 16-byte chunk q of row r sits at q ^ (r % 8)
 constexpr uint32_t kWaitLimit = 1u << 25;     // polls of one mbarrier before giving up
 
 // Instruction descriptor of kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
@@ -153,6 +161,18 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(h);
 }
 
+// x as NP TF32 parts, largest first: NP = 2 rounds twice (x - x1 - x2 is
+// about 2^-22 x); NP = 3 leaves no remainder.
+template <int NP>
+__device__ __forceinline__ void split_tf32(float x, float* p) {
+  const float x1 = tf32_round(x);
+  const float r = x - x1;  // exact
+  const float x2 = tf32_round(r);
+  p[0] = x1;
+  p[1] = x2;
+  if (NP == 3) p[2] = r - x2;  // exact, a few significant bits
+}
+
 // Problem of a tensor-core list: sizes, C placement and the first rows of
 // its operands in the split arrays.
 struct TcProb {
@@ -163,30 +183,49 @@ struct TcProb {
 
 // Shared-memory footprint of the persistent kernel with NST operand stages
 // and NCB C-tile buffers.
-template <int NST, int NCB>
+template <int NST, int NCB, int NP>
 struct TcSmem {
-  static constexpr int bytes = NST * STAGE_BYTES + NCB * C_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+  static constexpr int bytes = NST * TcStage<NP>::bytes + NCB * C_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+  static_assert(bytes <= 232448, "shared memory per CTA");
+};
+
+// TMA maps of the split operands: parts of op(A) and of op(B)^T.
+struct TcMaps {
+  CUtensorMap a[3];
+  CUtensorMap b[3];
 };
 
 // Persistent grouped GEMM: CTA b takes the tiles b, b + gridDim.x, ... of the
 // list ({problem, tile row, tile column}), each C = alpha A B + beta C.
-// Warp roles (192 threads):
+//
+// Accumulation: the tensor cores add into TMEM with truncation (measured:
+// errors all of one sign on positive data, 5-20x those of FP32 FMAs), and
+// the Gauss-Jordan sweeps compound such a bias over their passes.  So every
+// KS K-steps of 8 are accumulated on their own in one of two 128-column
+// TMEM slices, and the slice sums are added on the CUDA cores in FP32 with
+// round-to-nearest (registers of the epilogue threads); the truncated sums
+// then span 8 KS products instead of the whole K (KS = 4, one K chunk, for
+// long products; KS = 1 for the rank-NB sweep updates).
+//
+// Warp roles (320 threads):
 //   warp 0, one lane: TMA producer of the operand chunks (NST-stage ring);
-//   warp 1, one lane: MMA issuer into one of two 128-column TMEM
-//     accumulators (tile i uses accumulator i % 2, so the MMAs of tile i + 1
-//     run while tile i is written back);
-//   warps 2-5: epilogue; warp w owns TMEM lanes (tile rows) 32 (w % 4) ..
-//     + 31.  It stages the C rows of tile i + 1 in shared memory with
-//     16-byte asynchronous copies (NCB = 2 buffers) while it combines and
-//     stores tile i, so C's DRAM traffic overlaps the rest.
-// Barriers: full/empty per operand stage, tmem_full/tmem_empty per
-// accumulator (tmem_empty counts the four epilogue warps).
-template <int NST, int NCB>
+//   warp 1, one lane: MMA issuer; chunk g of the CTA goes to TMEM slice g % 2;
+//   warps 2-9: epilogue; warp w reads TMEM lanes (tile rows) 32 (w % 4) ..
+//     + 31 and column half (w - 2) / 4 (64 columns), adds every chunk's
+//     slice into 64 FP32 running sums per thread and frees the slice; at the
+//     end of a tile it combines them with C, staged in shared memory by
+//     16-byte asynchronous copies (the next tile's C rows are copied while
+//     this tile's chunks are summed when NCB = 2), and writes its rows back
+//     with coalesced 256-byte half-row stores.
+// Barriers: full/empty per operand stage, sfull/sempty per TMEM slice
+// (sempty counts the eight epilogue warps).
+template <int NST, int NCB, int NP, int KS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const int4* __restrict__ tiles, int ntiles, const TcProb* __restrict__ probs,
-               const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
-               float* __restrict__ C, float alpha, float beta, int* __restrict__ status) {
+               const __grid_constant__ TcMaps maps, float* __restrict__ C, float alpha, float beta,
+               int* __restrict__ status) {
+  constexpr int STAGE_BYTES = TcStage<NP>::bytes;
+  constexpr int SPC = (BKC / 8) / KS;  // TMEM slices per K chunk (KS K-steps of 8 each)
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned operand stages (the swizzle pattern repeats every 1 KB)
   const uint32_t base = smem_u32(smem_raw);
@@ -194,9 +233,9 @@ tc_gemm_kernel(const int4* __restrict__ tiles, int ntiles, const TcProb* __restr
   float* Cbuf = reinterpret_cast<float*>(smem + NST * STAGE_BYTES);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * STAGE_BYTES + NCB * C_BYTES);
   uint64_t* empty = full + NST;
-  uint64_t* tfull = empty + NST;
-  uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* sfull = empty + NST;
+  uint64_t* sempty = sfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntl = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -207,8 +246,8 @@ tc_gemm_kernel(const int4* __restrict__ tiles, int ntiles, const TcProb* __restr
       mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
-      mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 4);
+      mbar_init(&sfull[a], 1);
+      mbar_init(&sempty[a], 8);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -242,149 +281,157 @@ tc_gemm_kernel(const int4* __restrict__ tiles, int ntiles, const TcProb* __restr
           }
           uint8_t* st = smem + s * STAGE_BYTES;
           mbar_expect_tx(&full[s], STAGE_BYTES);
-          tma_load_2d(st, &mAh, c * BKC, ya, &full[s]);
-          tma_load_2d(st + OPND_BYTES, &mAl, c * BKC, ya, &full[s]);
-          tma_load_2d(st + 2 * OPND_BYTES, &mBh, c * BKC, yb, &full[s]);
-          tma_load_2d(st + 3 * OPND_BYTES, &mBl, c * BKC, yb, &full[s]);
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            tma_load_2d(st + q * OPND_BYTES, &maps.a[q], c * BKC, ya, &full[s]);
+            tma_load_2d(st + (NP + q) * OPND_BYTES, &maps.b[q], c * BKC, yb, &full[s]);
+          }
           issued = g + 1;
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      int g = 0;
-      for (int i = 0; i < ntl && !*(volatile int*)abort_flag; ++i) {
+      int g = 0;  // TMEM slices of this CTA so far (SPC per operand chunk)
+      bool ok = true;
+      for (int i = 0; i < ntl && ok && !*(volatile int*)abort_flag; ++i) {
         const int4 tl = tiles[blockIdx.x + i * gridDim.x];
         const int nk = (probs[tl.x].K + BKC - 1) / BKC;
-        const int a = i & 1;
-        if (i >= 2 && !mbar_wait(&tempty[a], ((i >> 1) - 1) & 1)) {
-          atomicExch(abort_flag, 1);
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t acc = tmem + (uint32_t)(a * TMEM_COLS);
-        bool ok = true;
-        for (int c = 0; c < nk; ++c, ++g) {
-          const int s = g % NST;
-          if (!mbar_wait(&full[s], (g / NST) & 1)) {
-            atomicExch(abort_flag, 1);
+        for (int c = 0; c < nk; ++c) {
+          const int s = (g / SPC) % NST;  // operand stage of chunk c (g counts slices)
+          if (!mbar_wait(&full[s], ((g / SPC) / NST) & 1)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+          for (int sl = 0; sl < SPC && ok; ++sl, ++g) {
+            const int a = g & 1;
+            if (g >= 2 && !mbar_wait(&sempty[a], ((g >> 1) - 1) & 1)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + (uint32_t)(a * TMEM_COLS);
 #pragma unroll
-          for (int k = 0; k < BKC / 8; ++k) {
-            const uint64_t ah = sw128_desc(st + 32 * k);
-            const uint64_t al = sw128_desc(st + OPND_BYTES + 32 * k);
-            const uint64_t bh = sw128_desc(st + 2 * OPND_BYTES + 32 * k);
-            const uint64_t bl = sw128_desc(st + 3 * OPND_BYTES + 32 * k);
-            mma_tf32(acc, al, bh, (c > 0 || k > 0) ? 1u : 0u);
-            mma_tf32(acc, ah, bl, 1u);
-            mma_tf32(acc, ah, bh, 1u);
+            for (int kk = 0; kk < KS; ++kk) {
+              const int k = sl * KS + kk;
+              // parts: a_q at tile q, b_q at tile NP + q; small products first
+              auto da = [&](int q) { return sw128_desc(st + q * OPND_BYTES + 32 * k); };
+              auto db = [&](int q) { return sw128_desc(st + (NP + q) * OPND_BYTES + 32 * k); };
+              const uint32_t first = kk > 0 ? 1u : 0u;  // each slice starts afresh
+              if (NP == 3) {
+                mma_tf32(acc, da(1), db(1), first);
+                mma_tf32(acc, da(2), db(0), 1u);
+                mma_tf32(acc, da(0), db(2), 1u);
+                mma_tf32(acc, da(1), db(0), 1u);
+              } else {
+                mma_tf32(acc, da(1), db(0), first);
+              }
+              mma_tf32(acc, da(0), db(1), 1u);
+              mma_tf32(acc, da(0), db(0), 1u);
+            }
+            mma_commit(&sfull[a]);
           }
+          if (!ok) break;
           mma_commit(&empty[s]);
         }
-        mma_commit(&tfull[a]);  // also after an abort: the epilogue must not wait forever
         if (!ok) break;
       }
+      if (!ok) atomicExch(abort_flag, 1);
     }
   } else {
     // epilogue warps
-    const int wq = warp & 3;
-    const int wrow0 = 32 * wq;
+    const int wq = warp & 3, half = (warp - 2) >> 2;
+    const int wrow0 = 32 * wq, col0 = 64 * half;
+    // C rows of a tile into buffer (i % NCB): 32 rows x 64 columns, two rows
+    // per warp instruction (16 lanes x 16 bytes each)
     auto prefetch = [&](int i) {
       const int4 tl = tiles[blockIdx.x + i * gridDim.x];
       const TcProb p = probs[tl.x];
       if (beta == 0.f || (p.c & 3) || (p.ldc & 3)) return;
       float* Cs = Cbuf + (i % NCB) * (BM * CLD);
       const int m0 = tl.y * BM, n0 = tl.z * BN;
-      for (int r = 0; r < 32; ++r) {
-        const int lr = wrow0 + r, gr = m0 + lr, gc = n0 + 4 * lane;
+      const int sub = lane >> 4, q = (col0 >> 2) + (lane & 15);  // 16-byte chunk of the row
+      for (int r = 0; r < 32; r += 2) {
+        const int lr = wrow0 + r + sub, gr = m0 + lr, gc = n0 + 4 * q;
         const int valid = (gr < p.M) ? max(0, min(4, p.N - gc)) : 0;
         const float* src = valid > 0 ? C + p.c + (int64_t)gr * p.ldc + gc : C;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(Cs + lr * CLD + 4 * lane)),
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                         smem_u32(Cs + lr * CLD + 4 * (q ^ (lr & 7)))),
                      "l"(src), "r"(valid * 4)
                      : "memory");
       }
     };
     if (ntl > 0) prefetch(0);
     asm volatile("cp.async.commit_group;" ::: "memory");
-    for (int i = 0; i < ntl; ++i) {
-      const bool ahead = NCB == 2 && i + 1 < ntl;
+    int g = 0;
+    bool ok = true;
+    for (int i = 0; i < ntl && ok; ++i) {
       const int4 tl = tiles[blockIdx.x + i * gridDim.x];
       const TcProb p = probs[tl.x];
       const int m0 = tl.y * BM, n0 = tl.z * BN;
-      const int a = i & 1;
-      const bool cvec = ((p.c & 3) == 0) && ((p.ldc & 3) == 0);
-      // the next tile's C rows go to the other buffer (NCB = 2) while this
-      // one is finished; with one buffer they are fetched after the stores
+      const int nk = (p.K + BKC - 1) / BKC;
+      const bool ahead = NCB == 2 && i + 1 < ntl;
       if (ahead) {
         prefetch(i + 1);
         asm volatile("cp.async.commit_group;" ::: "memory");
       }
-      const bool ok = mbar_wait(&tfull[a], (i >> 1) & 1);
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // this tile's C rows have landed (only the next tile's copies may
-      // still be pending)
-      if (ahead) asm volatile("cp.async.wait_group 1;" ::: "memory");
-      else asm volatile("cp.async.wait_group 0;" ::: "memory");
-      __syncwarp();
-      if (!ok || *(volatile int*)abort_flag) {
+      float rs[64];
+#pragma unroll
+      for (int q = 0; q < 64; ++q) rs[q] = 0.f;
+      for (int c = 0; c < nk * SPC; ++c, ++g) {
+        const int a = g & 1;
+        if (!mbar_wait(&sfull[a], (g >> 1) & 1) || *(volatile int*)abort_flag) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(a * TMEM_COLS) + ((uint32_t)wrow0 << 16) + (uint32_t)col0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v[32];
+          tmem_ld32(acc + (uint32_t)(32 * h), v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) rs[32 * h + q] += v[q];
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sempty[a])) : "memory");
+      }
+      if (!ok) {
         atomicExch(abort_flag, 1);
         break;
       }
-      const uint32_t acc = tmem + (uint32_t)(a * TMEM_COLS) + ((uint32_t)wrow0 << 16);
-      float* Cs = Cbuf + (i % NCB) * (BM * CLD);
-      const int lr = wrow0 + lane;
-      if (cvec) {
-        float* crow_s = Cs + lr * CLD;
-#pragma unroll 1
-        for (int cc = 0; cc < BN / 32; ++cc) {
-          float v[32];
-          tmem_ld32(acc + (uint32_t)(cc * 32), v);
-          float4* c4 = reinterpret_cast<float4*>(crow_s + cc * 32);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            float4 o;
-            if (beta != 0.f) {
-              const float4 old = c4[q];
-              o = make_float4(alpha * v[4 * q] + beta * old.x, alpha * v[4 * q + 1] + beta * old.y,
-                              alpha * v[4 * q + 2] + beta * old.z, alpha * v[4 * q + 3] + beta * old.w);
-            } else {
-              o = make_float4(alpha * v[4 * q], alpha * v[4 * q + 1], alpha * v[4 * q + 2],
-                              alpha * v[4 * q + 3]);
-            }
-            c4[q] = o;
-          }
-        }
-      } else {
-        // unaligned C: each thread updates its own row in global memory
-        const int row = m0 + lr;
-        float* crow = C + p.c + (int64_t)row * p.ldc;
-#pragma unroll 1
-        for (int cc = 0; cc < BN / 32; ++cc) {
-          float v[32];
-          tmem_ld32(acc + (uint32_t)(cc * 32), v);
-          const int nb = n0 + cc * 32;
-          if (row < p.M && nb < p.N) {
-            for (int q = 0; q < 32 && nb + q < p.N; ++q) {
-              float* cp = crow + nb + q;
-              *cp = (beta != 0.f) ? alpha * v[q] + beta * *cp : alpha * v[q];
-            }
-          }
-        }
-      }
-      // accumulator a is free once this warp's TMEM reads are done
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      if (ahead) asm volatile("cp.async.wait_group 1;" ::: "memory");
+      else asm volatile("cp.async.wait_group 0;" ::: "memory");
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[a])) : "memory");
+      const int lr = wrow0 + lane;
+      const bool cvec = ((p.c & 3) == 0) && ((p.ldc & 3) == 0);
+      float* Cs = Cbuf + (i % NCB) * (BM * CLD);
       if (cvec) {
-        for (int r = 0; r < 32; ++r) {
-          const int lr2 = wrow0 + r, gr = m0 + lr2, gc = n0 + 4 * lane;
+        float4* c4 = reinterpret_cast<float4*>(Cs + lr * CLD);
+#pragma unroll
+        for (int qq = 0; qq < 16; ++qq) {
+          const int q = ((col0 >> 2) + qq) ^ (lr & 7);  // swizzled 16-byte chunk of this row
+          float4 o;
+          if (beta != 0.f) {
+            const float4 old = c4[q];
+            o = make_float4(alpha * rs[4 * qq] + beta * old.x, alpha * rs[4 * qq + 1] + beta * old.y,
+                            alpha * rs[4 * qq + 2] + beta * old.z, alpha * rs[4 * qq + 3] + beta * old.w);
+          } else {
+            o = make_float4(alpha * rs[4 * qq], alpha * rs[4 * qq + 1], alpha * rs[4 * qq + 2],
+                            alpha * rs[4 * qq + 3]);
+          }
+          c4[q] = o;
+        }
+        __syncwarp();
+        const int sub = lane >> 4, q = (col0 >> 2) + (lane & 15);
+        for (int r = 0; r < 32; r += 2) {
+          const int lr2 = wrow0 + r + sub, gr = m0 + lr2, gc = n0 + 4 * q;
           if (gr >= p.M || gc >= p.N) continue;
           float* dst = C + p.c + (int64_t)gr * p.ldc + gc;
-          const float4 o = *reinterpret_cast<const float4*>(Cs + lr2 * CLD + 4 * lane);
+          const float4 o = *reinterpret_cast<const float4*>(Cs + lr2 * CLD + 4 * (q ^ (lr2 & 7)));
           if (gc + 4 <= p.N) {
             *reinterpret_cast<float4*>(dst) = o;
           } else {
@@ -392,6 +439,14 @@ tc_gemm_kernel(const int4* __restrict__ tiles, int ntiles, const TcProb* __restr
             if (gc + 1 < p.N) dst[1] = o.y;
             if (gc + 2 < p.N) dst[2] = o.z;
           }
+        }
+      } else {
+        // unaligned C: each thread updates its own row half in global memory
+        const int row = m0 + lr;
+        if (row < p.M) {
+          float* crow = C + p.c + (int64_t)row * p.ldc + n0 + col0;
+          for (int q = 0; q < 64 && n0 + col0 + q < p.N; ++q)
+            crow[q] = (beta != 0.f) ? alpha * rs[q] + beta * crow[q] : alpha * rs[q];
         }
       }
       __syncwarp();
@@ -431,10 +486,10 @@ struct SplitProb {
   int r0;  // first output row
 };
 
-template <bool KMAJ>
+template <bool KMAJ, int NP>
 __global__ void __launch_bounds__(256)
 tc_split_kernel(const SplitProb* __restrict__ probs, int Kp, const float* __restrict__ X,
-                float* __restrict__ hi, float* __restrict__ lo) {
+                float* __restrict__ p0, int64_t part_stride) {
   __shared__ float t[32][33];
   const SplitProb q = probs[blockIdx.y];
   const int nkt = Kp / 32;
@@ -462,10 +517,11 @@ tc_split_kernel(const SplitProb* __restrict__ probs, int Kp, const float* __rest
     const int r = rb + ty + 8 * i, k = kb + tx;
     if (r < q.rows) {
       const float x = t[ty + 8 * i][tx];
-      const float h = tf32_round(x);
       const int64_t o = (int64_t)(q.r0 + r) * Kp + k;
-      hi[o] = h;
-      lo[o] = tf32_round(x - h);
+      float parts[NP];
+      split_tf32<NP>(x, parts);
+#pragma unroll
+      for (int pp = 0; pp < NP; ++pp) p0[o + pp * part_stride] = parts[pp];
     }
   }
 }
@@ -513,13 +569,20 @@ inline CUtensorMap encode_kmajor(const float* base, int64_t rows, int Kp) {
   return m;
 }
 
+template <int NST, int NCB, int NP, int KS>
+inline void set_smem_attr_one() {
+  CB_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<NST, NCB, NP, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcSmem<NST, NCB, NP>::bytes));
+}
+
 inline void set_smem_attr() {
   static bool done = false;
   if (!done) {
-    CB_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 TcSmem<1, 2>::bytes));
-    CB_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 TcSmem<2, 1>::bytes));
+    set_smem_attr_one<1, 2, 2, 1>();
+    set_smem_attr_one<1, 2, 2, 4>();
+    set_smem_attr_one<2, 1, 2, 4>();
+    set_smem_attr_one<1, 2, 3, 1>();
+    set_smem_attr_one<1, 2, 3, 4>();
     done = true;
   }
 }
