@@ -124,9 +124,10 @@ def _parse():
     ap.add_argument("--oracle-budget-s", type=float, default=150.0)
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--max-gmres", type=int, default=3000)
-    ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
-                    help="kernels: one BDDC setup and a few applies and SpMVs of the workload "
-                         "(a short program for profiler captures)")
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "step"],
+                    help="kernels: one BDDC setup and a few applies and SpMVs of the workload; "
+                         "step: one FP32 Newton step from d = 0 at the first load level (short "
+                         "programs for profiler captures)")
     return ap.parse_args()
 
 
@@ -262,6 +263,10 @@ else:
     parts = [cp[(first + i) %% len(cp)] for i in range(%(nparts)d)]
     prob = workloads.lv_part_problem(full, parts)
     maxit = 3
+if %(sync)d:
+    # all-cores run: wait until every process has built its mesh
+    print("ready", flush=True)
+    sys.stdin.readline()
 t0 = time.perf_counter()
 fe = FEProblem(prob)
 cl = Classification(fe, prob["elem_part"], prob["n_parts"])
@@ -281,13 +286,14 @@ print(json.dumps({"prep": t1 - t0, "assemble": t2 - t1, "setup": t3 - t2, "gmres
 """
 
 
-def _oracle_proc(name, first, threads):
-    code = _ORACLE_STEP % {"root": ROOT, "name": name, "first": first, "nparts": SAMPLE_PARTS}
+def _oracle_proc(name, first, threads, sync=False):
+    code = _ORACLE_STEP % {"root": ROOT, "name": name, "first": first, "nparts": SAMPLE_PARTS,
+                           "sync": int(sync)}
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(threads)
     return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
-                            text=True, env=env)
+                            stdin=subprocess.PIPE if sync else None, text=True, env=env)
 
 
 def _collect(proc, timeout):
@@ -330,7 +336,15 @@ def oracle_baseline(name, its, all_cores=True, timeout=900):
         # all host cores: independent samples (different subdomains) in
         # parallel, one process per core; the per-subdomain loops of the
         # oracle's setup and apply parallelise the same way
-        procs = [_oracle_proc(name, SAMPLE_PARTS * i, 1) for i in range(ncpu)]
+        # one process per core; the clock starts once every process has
+        # built its sample (mesh generation is not part of a Newton step)
+        procs = [_oracle_proc(name, SAMPLE_PARTS * i, 1, sync=True) for i in range(ncpu)]
+        for p in procs:
+            if p.stdout.readline().strip() != "ready":
+                raise RuntimeError(p.communicate(timeout=timeout)[1][-2000:])
+        for p in procs:
+            p.stdin.write("go\n")
+            p.stdin.flush()
         t0 = time.perf_counter()
         res = [_collect(p, timeout) for p in procs]
         wall = time.perf_counter() - t0
@@ -386,12 +400,14 @@ def _opts(pkg, prob, spec, precision, max_gmres):
     ml = {}
     if spec["levels"] == 3:
         ml = dict(levels=3, part2=prob["part2"], n_parts2=prob["n_parts2"], primal2="VEF")
+    # FP32: the setup is autotuned when the first Newton step creates the
+    # context (sweep block x tile order, timed on that tangent)
     return pkg.SolveOptions(precision=precision, primal=prob["primal"], max_gmres=max_gmres,
                             restart=spec["restart"], precision2=precision,
-                            scaling=prob.get("scaling", "counting"), **ml)
+                            scaling=prob.get("scaling", "counting"), autotune=precision == pkg.FP32, **ml)
 
 
-def newton_states(P, prob, opts, n_load, torch):
+def newton_states(P, prob, opts, n_load, torch, records=None):
     """Untimed FP32 solve over the first n_load load steps (all if None):
     every Newton state (d before the step, load factor) in order."""
     n = P.n_free
@@ -412,6 +428,8 @@ def newton_states(P, prob, opts, n_load, torch):
             rec, ctx = P.newton_step(d, lam, opts, ctx)
             if rec["status"] != 0:
                 raise RuntimeError("Newton step failed during the untimed solve: %r" % rec)
+            if records is not None:
+                records.append(rec)
     return states, ctx
 
 
@@ -438,8 +456,15 @@ def run_ours(args, world, rank, local):
     opts32 = _opts(pkg, prob, spec, pkg.FP32, args.max_gmres)
     opts64 = _opts(pkg, prob, spec, pkg.FP64, args.max_gmres)
 
-    states, ctx32 = newton_states(P, prob, opts32, spec["n_load"], torch)
+    solve_recs = []
+    states, ctx32 = newton_states(P, prob, opts32, spec["n_load"], torch, solve_recs)
     ns = len(states)
+    inf32 = ctx32.info()
+    autotune = {"sweep_block": inf32["sweep_block"], "tile_order": inf32["tile_order"],
+                "ms_setup_tuned": inf32["ms_setup_tuned"], "ms_setup_default": inf32["ms_setup_default"],
+                "ms_tuning": solve_recs[0]["ms_autotune"],
+                "candidates": "sweep block 64/128 x GEMM tile order by subdomain/largest first, one timed "
+                              "setup each on the first Newton state's tangent"}
     dw = torch.empty_like(states[0][0])
 
     def run_steps(seq, opts, ctx, records=None):
@@ -520,7 +545,11 @@ def run_ours(args, world, rank, local):
     per_level["assembly_element_kernel_ms"] = per_step("ELEMENT")
     per_level["steps_averaged"] = nk
 
-    # ---- FP64 local operators on a subset of the same states, paired
+    # ---- FP64 local operators on a subset of the same states, paired (the
+    # FP32 context is released first: both do not fit at 3M DoFs)
+    ctx32.close()
+    ctx32 = None
+    torch.cuda.synchronize()
     n64 = args.fp64_states if args.fp64_states is not None else spec["fp64_states"]
     sel64 = _spread(ns, ns if n64 is None else n64)
     ctx64 = run_steps(sel64[:1], opts64, None)  # context creation, untimed
@@ -546,11 +575,16 @@ def run_ours(args, world, rank, local):
     speedup = (statistics.mean(p["ms64"] for p in paired) / statistics.mean(p["ms32"] for p in paired)
                if paired else None)
 
-    # ---- end to end through the C ABI with host buffers (pinned)
+    ctx64.close()
+    ctx64 = None
+    # ---- end to end through the C ABI with host buffers (pinned); one
+    # untimed host step first recreates the FP32 context
     host = torch.empty(n, dtype=torch.float64, pin_memory=True)
     host_np = host.numpy()
     states_h = [(s.cpu().numpy(), lam) for s, lam in states]
     e2e_seq = list(range(ns)) if ns <= K else _spread(ns, K)
+    host_np[:] = states_h[0][0]
+    rec, ctx32 = P.newton_step(host_np, states_h[0][1], opts32, None, host=True)
     torch.cuda.synchronize()
     _barrier(world)
     t0 = time.perf_counter()
@@ -622,6 +656,7 @@ def run_ours(args, world, rank, local):
                            "ms_step_median": statistics.median(r["ms_total"] for r in recs32),
                            "ms_step_max": max(r["ms_total"] for r in recs32)},
         "per_level": per_level,
+        "autotune": autotune,
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                 "steps": len(e2e_seq)},
         "gpu_launches": int(launches),
@@ -672,11 +707,35 @@ def run_kernels(args):
     print(json.dumps({"mode": "kernels", "n_free": P.n_free, "apply_norm": float(z.norm())}))
 
 
+def run_step(args):
+    """One FP32 Newton step of the workload from d = 0 at the first load
+    level, in the benchmark's launch configuration without autotuning."""
+    import torch
+
+    import paper_2208_06191_gb300 as pkg
+
+    pkg.build()
+    pkg.load_library()
+    spec = WORKLOADS[args.workload]
+    prob = spec["build"]()
+    P = pkg.Problem(prob)
+    opts = _opts(pkg, prob, spec, pkg.FP32, args.max_gmres)
+    opts.autotune = 0
+    d = torch.zeros(P.n_free, dtype=torch.float64, device="cuda")
+    rec, ctx = P.newton_step(d, 1.0 / prob["load_steps"], opts)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "step", "n_free": P.n_free, "gmres_its": rec["gmres_its"],
+                      "ms_total": rec["ms_total"], "status": rec["status"]}))
+
+
 def main():
     args = _parse()
     world, rank, local = _dist_init()
     if args.mode == "kernels":
         run_kernels(args)
+        return
+    if args.mode == "step":
+        run_step(args)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

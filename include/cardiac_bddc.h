@@ -263,6 +263,9 @@ typedef struct {
   int sweep_block;   /* pivot block width of the local Gauss-Jordan sweeps:
                         0 or 64 (default), or 128 (FP32 operators only:
                         half the passes over each local matrix) */
+  int tile_order;    /* order of the output tiles of the setup GEMMs: 0 =
+                        by subdomain (default), 1 = largest problems first
+                        (uneven subdomains: the long ones start first) */
 } bddc_options;
 
 typedef struct bddc_ctx bddc_ctx;
@@ -274,6 +277,12 @@ typedef struct {
   int64_t local_bytes;         /* bytes of local operators read per apply   */
   int64_t device_bytes;        /* device memory held by the context         */
   double setup_flops;          /* algorithmic flops of the last setup       */
+  int sweep_block;             /* pivot block width of the local sweeps     */
+  int tile_order;              /* tile order of the setup GEMMs             */
+  float ms_setup_tuned;        /* autotuned contexts: the chosen candidate's
+                                  setup time, and that of the default
+                                  (64, subdomain order); 0 otherwise        */
+  float ms_setup_default;
 } bddc_info;
 
 /* BDDC setup for the tangent last assembled on P (Section 3.2): subdomain
@@ -358,6 +367,15 @@ typedef struct {
   int scaling;         /* as in bddc_options                                 */
   int coarse;          /* as in bddc_options                                 */
   int sweep_block;     /* as in bddc_options                                 */
+  int tile_order;      /* as in bddc_options                                 */
+  int autotune;        /* 1: when a Newton step creates the BDDC context, it
+                          first times one setup for every candidate (sweep
+                          block 64/128 for FP32 operators, tile order 0/1)
+                          on the assembled tangent and keeps the fastest;
+                          the choice is cached in the problem per precision
+                          and reported by bddc_get_info, the tuning time in
+                          newton_record.ms_autotune.  sweep_block and
+                          tile_order are then ignored. */
 } solve_options;
 
 #define CBDDC_MAX_RECORDS 512
@@ -370,6 +388,7 @@ typedef struct {
   float ms_assemble, ms_setup, ms_gmres, ms_total; /* CUDA-event times       */
   double gmres_relres; /* ||b - K delta|| / ||b|| of the tangent solve at exit */
   int gmres_reorth;    /* Arnoldi steps that took a second Gram-Schmidt pass */
+  float ms_autotune;   /* time spent tuning the setup in this step (0: none) */
 } newton_record;
 
 typedef struct {
@@ -432,14 +451,18 @@ enum {
                                      and the coarse inverse)                  */
 };
 
-/* Selects the kernels of the FP32 setup GEMMs.  mode bit 0: tcgen05 tensor
-   cores with operands split into TF32 parts (else the FP32 CUDA cores);
-   bit 1: three parts (six products, FP32-level accuracy) for the
-   Gauss-Jordan sweep updates, else two (three products); bit 2: the same
-   for the other setup products.  Default 3 (tensor cores, three-part sweep
-   updates).  The enable bit is read at every setup, the part counts when a
-   context is created.  Returns the previous mode.  Host-side state, not
-   thread safe; a diagnostic and comparison switch. */
+/* Selects the kernels of the FP32 setup GEMMs.  mode bit 0 (1): tcgen05
+   tensor cores with operands split into TF32 parts (else every FP32 setup
+   GEMM on the CUDA cores); bit 1 (2): three parts (six products) for the
+   Gauss-Jordan sweep updates, else two (three products); bit 2 (4): the
+   same for the other setup products; bit 3 (8): the other products on the
+   CUDA cores; bit 4 (16): the sweep updates on the CUDA cores; bit 5 (32):
+   the tensor-core sweep updates sum four K-slices in FP32 instead of one
+   per 32-wide K block.  Bits above 5 are ignored.  Default 1 (tensor
+   cores, two parts, one slice per K block).  The enable bits are read at
+   every setup, the part counts when a context is created.  Returns the
+   previous mode.  Host-side state, not thread safe; a diagnostic and
+   comparison switch. */
 CBDDC_API int cbddc_set_tensor_cores(int mode);
 
 /* Starts recording CUDA events around every launch of the given class (and

@@ -111,13 +111,15 @@ class _BddcOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("primal", ctypes.c_int), ("pivot_tol", ctypes.c_double),
                 ("levels", ctypes.c_int), ("n_parts2", ctypes.c_int), ("part2", _i32p),
                 ("primal2", ctypes.c_int), ("precision2", ctypes.c_int), ("scaling", ctypes.c_int),
-                ("coarse", ctypes.c_int), ("sweep_block", ctypes.c_int)]
+                ("coarse", ctypes.c_int), ("sweep_block", ctypes.c_int), ("tile_order", ctypes.c_int)]
 
 
 class _BddcInfo(ctypes.Structure):
     _fields_ = [("n_primal", ctypes.c_int), ("n_primal2", ctypes.c_int), ("precision", ctypes.c_int),
                 ("local_bytes", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("setup_flops", ctypes.c_double)]
+                ("device_bytes", ctypes.c_int64), ("setup_flops", ctypes.c_double),
+                ("sweep_block", ctypes.c_int), ("tile_order", ctypes.c_int),
+                ("ms_setup_tuned", ctypes.c_float), ("ms_setup_default", ctypes.c_float)]
 
 
 class _GmresOptions(ctypes.Structure):
@@ -136,6 +138,7 @@ class _SolveOptions(ctypes.Structure):
         ("pivot_tol", ctypes.c_double), ("levels", ctypes.c_int), ("n_parts2", ctypes.c_int),
         ("part2", _i32p), ("primal2", ctypes.c_int), ("precision2", ctypes.c_int),
         ("scaling", ctypes.c_int), ("coarse", ctypes.c_int), ("sweep_block", ctypes.c_int),
+        ("tile_order", ctypes.c_int), ("autotune", ctypes.c_int),
     ]
 
 
@@ -144,7 +147,7 @@ class _Record(ctypes.Structure):
         ("load", ctypes.c_double), ("newton", ctypes.c_int), ("gmres_its", ctypes.c_int),
         ("res", ctypes.c_double), ("res0", ctypes.c_double), ("ms_assemble", ctypes.c_float),
         ("ms_setup", ctypes.c_float), ("ms_gmres", ctypes.c_float), ("ms_total", ctypes.c_float),
-        ("gmres_relres", ctypes.c_double), ("gmres_reorth", ctypes.c_int),
+        ("gmres_relres", ctypes.c_double), ("gmres_reorth", ctypes.c_int), ("ms_autotune", ctypes.c_float),
     ]
 
 
@@ -218,10 +221,12 @@ def load_library():
 def set_tensor_cores(mode):
     """FP32 setup GEMMs: mode bit 0 = tcgen05 tensor cores (else the FP32
     CUDA cores), bit 1 = three TF32 parts for the sweep updates, bit 2 =
-    three parts for the other products (True means the default, 3; False
-    means 0).  Returns the previous mode."""
+    three parts for the other products, bits 3/4 = the other products / the
+    sweep updates on the CUDA cores, bit 5 = four K-slices per sweep tile
+    (True means the default, 1; False means 0).  Returns the previous
+    mode."""
     if mode is True:
-        mode = 3
+        mode = 1
     elif mode is False:
         mode = 0
     return int(load_library().cbddc_set_tensor_cores(int(mode)))
@@ -295,12 +300,15 @@ class SolveOptions:
     scaling: "counting" or "deluxe" (first level); coarse: "galerkin" or
     "petrov" (left coarse basis from the transposed local problems);
     sweep_block: pivot block width of the local sweeps (0/64, or 128 for
-    FP32 operators)."""
+    FP32 operators); tile_order: 1 orders the setup GEMM tiles largest
+    problem first; autotune: time the candidates at context creation and
+    keep the fastest."""
 
     def __init__(self, precision=FP64, primal="V", load_steps=4, max_newton=25, max_halvings=6,
                  restart=100, max_gmres=1000, newton_rtol=1e-8, gmres_rtol=1e-8, pivot_tol=1e-13,
                  levels=2, part2=None, n_parts2=0, primal2="VEF", precision2=FP64, scaling="counting",
-                 coarse="galerkin", sweep_block=0):
+                 coarse="galerkin", sweep_block=0, tile_order=0,
+                 autotune=False):
         self.precision = precision
         self.primal = primal if isinstance(primal, int) else primal_mask(primal)
         self.load_steps = load_steps
@@ -319,13 +327,15 @@ class SolveOptions:
         self.scaling = scaling_code(scaling)
         self.coarse = coarse_code(coarse)
         self.sweep_block = int(sweep_block)
+        self.tile_order = int(tile_order)
+        self.autotune = int(bool(autotune))
 
     def c(self):
         return _SolveOptions(self.precision, self.primal, self.load_steps, self.max_newton,
                              self.max_halvings, self.restart, self.max_gmres, self.newton_rtol,
                              self.gmres_rtol, self.pivot_tol, self.levels, self.n_parts2,
                              self._part2_ptr, self.primal2, self.precision2, self.scaling, self.coarse,
-                             self.sweep_block)
+                             self.sweep_block, self.tile_order, self.autotune)
 
 
 def _record_dict(r):
@@ -528,14 +538,15 @@ class BDDC:
 
     def __init__(self, problem, precision=FP64, primal="V", pivot_tol=1e-13, levels=2, part2=None,
                  n_parts2=0, primal2="VEF", precision2=FP64, scaling="counting", coarse="galerkin",
-                 sweep_block=0):
+                 sweep_block=0, tile_order=0):
         self.problem = problem
         self._h = ctypes.c_void_p()
         self._part2, p2 = _part2_arg(part2)
         self._opt = _BddcOptions(precision, primal if isinstance(primal, int) else primal_mask(primal),
                                  pivot_tol, levels, int(n_parts2), p2,
                                  primal2 if isinstance(primal2, int) else primal_mask(primal2),
-                                 precision2, scaling_code(scaling), coarse_code(coarse), int(sweep_block))
+                                 precision2, scaling_code(scaling), coarse_code(coarse), int(sweep_block),
+                                 int(tile_order))
 
     @classmethod
     def _wrap(cls, h, problem):

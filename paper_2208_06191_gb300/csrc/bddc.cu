@@ -423,13 +423,15 @@ __global__ void gather_kernel(const int* __restrict__ idx, int64_t n, const doub
   if (i < n) out[i] = x[idx[i]];
 }
 
-// u0 = A_II^-1 r_I (rows of the A_II^-1 block), 64 rows per CTA.
-template <typename T>
+// A_II^-1 x_I (rows of the A_II^-1 block), 64 rows per CTA: into the packed
+// interior vector u0, or (SCATTER) into the interior entries of the global
+// vector z.
+template <typename T, bool SCATTER>
 __global__ void __launch_bounds__(256)
 apply_interior_kernel(const int2* __restrict__ items, const int* __restrict__ nI,
                       const int64_t* __restrict__ offA, const int* __restrict__ ldA,
-                      const int64_t* __restrict__ offI, const T* __restrict__ Aloc,
-                      const double* __restrict__ xI, double* __restrict__ u0) {
+                      const int64_t* __restrict__ offI, const int* __restrict__ gdofI,
+                      const T* __restrict__ Aloc, const double* __restrict__ xI, double* __restrict__ u0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* xs = reinterpret_cast<T*>(smraw);
   const int2 it = items[blockIdx.x];
@@ -437,10 +439,53 @@ apply_interior_kernel(const int2* __restrict__ items, const int* __restrict__ nI
   const int ni = nI[s];
   const int rb = it.y * GROWS * GGROUPS;
   if (rb >= ni) return;
-  load_x<T>(xs, xI + offI[s], ni);
-  double* out = u0 + offI[s];
-  gemv_rows<T>(Aloc + offA[s], ldA[s], rb, min(ni, rb + GROWS * GGROUPS), xs, ni,
-               [&](int row, T v) { out[row] = (double)v; });
+  const int64_t oi = offI[s];
+  load_x<T>(xs, xI + oi, ni);
+  gemv_rows<T>(Aloc + offA[s], ldA[s], rb, min(ni, rb + GROWS * GGROUPS), xs, ni, [&](int row, T v) {
+    if (SCATTER) u0[gdofI[oi + row]] = (double)v;
+    else u0[oi + row] = (double)v;
+  });
+}
+
+// Sparse interior-interface coupling of the assembled matrix: out[t] =
+// r[rdof[t]] - (row t % 3 of block row t / 3) x, where the block row's 3x3
+// blocks (val, 9 per block, row-major) multiply x at 3 col[b] .. 3 col[b] +
+// 2.  Used twice per apply: g_Gamma = r_Gamma - K_Gamma,I u0 (rows: the
+// assembled interface nodes, x: the packed interior solution) and t_I =
+// r_I - K_I,Gamma z (rows: the packed interior nodes, x: the global z with
+// its interface entries set).  Three threads per block row, as the BSR
+// product, accumulating in the operator precision.
+template <typename T>
+__global__ void __launch_bounds__(256)
+coupling_kernel(const int* __restrict__ ptr, const int* __restrict__ col, const T* __restrict__ val,
+                const int* __restrict__ rdof, const double* __restrict__ r, const double* __restrict__ x,
+                double* __restrict__ out, int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int64_t row = t / 3;
+  const int rr = (int)(t - 3 * row);
+  const int b0 = __ldg(ptr + row), b1 = __ldg(ptr + row + 1);
+  const T* v = val + (int64_t)b0 * 9 + 3 * rr;
+  T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll 4
+  for (int b = b0; b < b1; ++b, v += 9) {
+    const double* xc = x + (int64_t)__ldg(col + b) * 3;
+    a0 = fma(__ldg(v), (T)__ldg(xc), a0);
+    a1 = fma(__ldg(v + 1), (T)__ldg(xc + 1), a1);
+    a2 = fma(__ldg(v + 2), (T)__ldg(xc + 2), a2);
+  }
+  out[t] = r[rdof[t]] - (double)(a0 + a1 + a2);
+}
+
+// val[9 k + e] = (T) bsr_vals[9 src[k] + e]: the coupling blocks of the
+// assembled tangent in the operator precision (once per setup).
+template <typename T>
+__global__ void coupling_values_kernel(const int* __restrict__ src, int64_t nblk,
+                                       const double* __restrict__ bsr_vals, T* __restrict__ val) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 9 * nblk) return;
+  const int64_t k = t / 9;
+  val[t] = (T)bsr_vals[(int64_t)src[k] * 9 + (t - 9 * k)];
 }
 
 // hG = -A_GI u0 (the interface part of the interior correction).
@@ -810,6 +855,8 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
                (opt->sweep_block == 128 && opt->precision == CBDDC_FP32),
            CBDDC_EINVAL, "sweep_block must be 0, 64, or 128 with FP32 operators");
   C->nb = opt->sweep_block == 128 ? 128 : SWEEP_NB;
+  CB_CHECK(opt->tile_order == 0 || opt->tile_order == 1, CBDDC_EINVAL, "tile_order must be 0 or 1");
+  C->tile_order = opt->tile_order;
   const int nsub = P->n_parts;
   C->nsub = nsub;
   const bool useV = opt->primal & CBDDC_PRIMAL_V;
@@ -1090,7 +1137,9 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   C->sw1.upload(sw1);
   C->sw2.upload(sw2);
   C->swg.upload(swg);
-  auto sweep_gemms = [NB, es](const std::vector<SweepDesc>& sw, int steps, std::vector<GemmList>& out) {
+  const int to_sw = C->tile_order;
+  auto sweep_gemms = [NB, es, to_sw](const std::vector<SweepDesc>& sw, int steps, std::vector<GemmList>& out) {
+    const int to = to_sw;
     const int nmat = (int)sw.size();
     out.clear();
     out.resize(steps);
@@ -1101,7 +1150,7 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
         const int kb = std::max(0, std::min(NB, d.p - k * NB));
         g.push_back(GemmProb{d.rows, d.cols, kb, NB, d.ld, d.ld, d.offX, d.offY, d.off});
       }
-      out[k].set(g, es);
+      out[k].set(g, es, false, to);
     }
   };
   sweep_gemms(sw1, C->steps1, C->gl_sw1);
@@ -1164,7 +1213,7 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     for (int k = 0; k < nk; ++k)
       for (int q = cptr[k]; q < cptr[k + 1]; ++q)
         gd[q] = GemmProb{bn[q], bn[q], bn[q], bld[q], bld[q], bld[q], coff[k], boff[q], boff[q]};
-    C->gl_dlx.set(gd, es);
+    C->gl_dlx.set(gd, es, false, C->tile_order);
     auto sz = [&](int64_t n) { return (size_t)(std::max<int64_t>(n, 1) + kAlign) * es; };
     C->Dsb.alloc(sz(boff[nb]));
     C->Ddb.alloc(sz(boff[nb]));
@@ -1195,13 +1244,14 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     gKc.push_back(GemmProb{C->nc[s], C->nc[s], C->nG[s], C->ldPhi[s], C->ldPhi[s], C->ldPhi[s],
                            C->offPhi[s], C->offPhi[s], C->offKc[s]});
   }
-  C->gl_E.set(gE, es);
-  C->gl_S.set(gS, es);
-  C->gl_W.set(gW, es);
-  C->gl_T.set(gT, es);
-  C->gl_PhiA.set(gPA, es);
-  C->gl_SPhi.set(gSP, es);
-  C->gl_Kc.set(gKc, es, true);
+  const int to = C->tile_order;
+  C->gl_E.set(gE, es, false, to);
+  C->gl_S.set(gS, es, false, to);
+  C->gl_W.set(gW, es, false, to);
+  C->gl_T.set(gT, es, false, to);
+  C->gl_PhiA.set(gPA, es, false, to);
+  C->gl_SPhi.set(gSP, es, false, to);
+  C->gl_Kc.set(gKc, es, true, to);
   if (C->coarse == CBDDC_COARSE_PETROV) {
     // Psi[0:nr, 0:nv] = -T^T S_vr^T (T: constrained inverse in Sw's rr
     // block; S_vr: vertex rows, r columns of the Schur complement in Aloc)
@@ -1212,7 +1262,7 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
       gPV.push_back(GemmProb{C->nr[s], C->nv[s], C->nr[s], C->ldS[s], C->ldA[s], C->ldPhi[s], C->offS[s],
                              aGG + (int64_t)C->nr[s] * C->ldA[s], C->offPhi[s]});
     }
-    C->gl_PsiV.set(gPV, es, true);
+    C->gl_PsiV.set(gPV, es, true, C->tile_order);
     C->Psi.alloc(sized(C->offPhi[nsub]));
   }
 
@@ -1311,6 +1361,44 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
   C->rc.alloc(std::max(C->n_pi, 1));
   C->uc.alloc(std::max(C->n_pi, 1));
   C->gl.alloc(std::max<int64_t>(C->totG, 1));
+  // Sparse interior-interface coupling.  Every element holding an interior
+  // DoF of a subdomain belongs to that subdomain, so sum_i R_i^T A_Gamma,I^(i)
+  // u0_i is the assembled block K_Gamma,I times the interior solution, and
+  // A_I,Gamma^(i) z_Gamma,i is K_I,Gamma z.  Problems that carry the global
+  // BSR matrix (every problem built from a mesh) read these blocks there:
+  // about 9 values per coupled node pair instead of the dense n_I x n_Gamma
+  // blocks, and the harmonic extension becomes A_II^-1 (r_I - K_I,Gamma z)
+  // instead of u0 - E z_Gamma (n_I^2 values instead of n_I n_Gamma).
+  C->sparse_cpl = P->nnzb > 0 && P->bsr_vals.p != nullptr && C->totI > 0 && C->n_if > 0;
+  if (C->sparse_cpl) {
+    const int64_t nfn = P->n_free_nodes;
+    std::vector<int> rp(nfn + 1), bc(P->nnzb);
+    CB_CUDA(cudaMemcpy(rp.data(), P->bsr_row_ptr.p, rp.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    CB_CUDA(cudaMemcpy(bc.data(), P->bsr_col.p, bc.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<int> int_of(nfn, -1);  // free node -> packed interior node
+    std::vector<char> on_if(nfn, 0);
+    for (int64_t q = 0; q < C->totI; q += 3) int_of[gdofI[q] / 3] = (int)(q / 3);
+    for (int m = 0; m < C->n_if; m += 3) on_if[if_dof[m] / 3] = 1;
+    std::vector<int> gptr{0}, gcol, gsrc, iptr{0}, icol, isrc;
+    for (int m = 0; m < C->n_if; m += 3) {
+      const int f = if_dof[m] / 3;
+      for (int b = rp[f]; b < rp[f + 1]; ++b)
+        if (int_of[bc[b]] >= 0) { gcol.push_back(int_of[bc[b]]); gsrc.push_back(b); }
+      gptr.push_back((int)gcol.size());
+    }
+    for (int64_t q = 0; q < C->totI; q += 3) {
+      const int f = gdofI[q] / 3;
+      for (int b = rp[f]; b < rp[f + 1]; ++b)
+        if (on_if[bc[b]]) { icol.push_back(bc[b]); isrc.push_back(b); }
+      iptr.push_back((int)icol.size());
+    }
+    C->n_cgi = (int64_t)gcol.size();
+    C->n_cig = (int64_t)icol.size();
+    C->cgi_ptr.upload(gptr); C->cgi_col.upload(gcol); C->cgi_src.upload(gsrc);
+    C->cig_ptr.upload(iptr); C->cig_col.upload(icol); C->cig_src.upload(isrc);
+    C->cgi_val.alloc((size_t)std::max<int64_t>(C->n_cgi, 1) * 9 * C->esize);
+    C->cig_val.alloc((size_t)std::max<int64_t>(C->n_cig, 1) * 9 * C->esize);
+  }
   // flops of one setup and bytes of local operators read per apply
   double fl = 0.0;
   int64_t lb = 0;
@@ -1320,8 +1408,11 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     fl += 2.0 * ni * ni * ni + 2.0 * ni * ni * ng + 2.0 * ng * ng * ni + 2.0 * ng * ng * nr +
           2.0 * na * na * ng + 2.0 * nr * na * ng + 2.0 * nr * na * na + 2.0 * ng * ng * nc +
           2.0 * nc * nc * ng;
-    lb += (int64_t)((ni * ni + 2.0 * ni * ng + nr * nr + 2.0 * ng * nc) * C->esize);
+    if (C->sparse_cpl) lb += (int64_t)((2.0 * ni * ni + nr * nr + 2.0 * ng * nc) * C->esize);
+    else lb += (int64_t)((ni * ni + 2.0 * ni * ng + nr * nr + 2.0 * ng * nc) * C->esize);
   }
+  // coupling blocks: 9 values and one column index each
+  if (C->sparse_cpl) lb += (C->n_cgi + C->n_cig) * (int64_t)(9 * C->esize + 4);
   fl += dlx_flops;
   lb += dlx_bytes;
   // multilevel: coarse problem and its BDDC context
@@ -1484,7 +1575,18 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
   if (C->maxG == 0) return;  // one subdomain: no interface
   launch_list<T, false, false>(C->gl_E, Aloc, Aloc, Et, T(1), T(0), s);
   launch_list<T, false, false>(C->gl_S, Aloc, Et, Aloc, T(-1), T(1), s);
-  if (C->maxI > 0) {
+  if (C->sparse_cpl) {  // the apply reads the coupling blocks, not E
+    if (C->n_cgi > 0) {
+      coupling_values_kernel<T><<<cdiv(9 * C->n_cgi, 256), 256, 0, s>>>(
+          C->cgi_src.p, C->n_cgi, P->bsr_vals.p, reinterpret_cast<T*>(C->cgi_val.p));
+      CB_LAUNCH();
+    }
+    if (C->n_cig > 0) {
+      coupling_values_kernel<T><<<cdiv(9 * C->n_cig, 256), 256, 0, s>>>(
+          C->cig_src.p, C->n_cig, P->bsr_vals.p, reinterpret_cast<T*>(C->cig_val.p));
+      CB_LAUNCH();
+    }
+  } else if (C->maxI > 0) {
     copy_e_kernel<T><<<dim3(cdiv(C->maxI, 8), nsub), 256, 0, s>>>(
         C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offE.p, C->d_ldS.p, Et, Aloc);
     CB_LAUNCH();
@@ -1623,11 +1725,11 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
   gather_kernel<<<cdiv(std::max<int64_t>(C->totI, 1), 256), 256, 0, s>>>(C->gdofI.p, C->totI, r, w.xI);
   CB_LAUNCH();
   if (C->n_itI > 0) {
-    apply_interior_kernel<T><<<C->n_itI, 256, smI, s>>>(
-        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, Aloc, w.xI, w.u0);
+    apply_interior_kernel<T, false><<<C->n_itI, 256, smI, s>>>(
+        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->gdofI.p, Aloc, w.xI, w.u0);
     CB_LAUNCH();
   }
-  if (C->maxG > 0) {
+  if (C->maxG > 0 && !C->sparse_cpl) {
     if (C->n_itG > 0) {
       apply_gi_kernel<T><<<C->n_itG, 256, smI, s>>>(
           C->itG.p, C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, Aloc, w.u0, w.hG);
@@ -1635,8 +1737,14 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
     }
   }
   if (C->n_if > 0) {
-    assemble_g_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
-                                                        r, w.hG, w.gI);
+    if (C->sparse_cpl) {  // g = r_Gamma - K_Gamma,I u0
+      coupling_kernel<T><<<cdiv(C->n_if, 256), 256, 0, s>>>(C->cgi_ptr.p, C->cgi_col.p,
+                                                          reinterpret_cast<const T*>(C->cgi_val.p),
+                                                          C->if_dof.p, r, w.u0, w.gI, C->n_if);
+    } else {
+      assemble_g_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
+                                                          r, w.hG, w.gI);
+    }
     CB_LAUNCH();
     restrict_kernel<<<cdiv(C->totG, 256), 256, 0, s>>>(C->gam_if.p, C->Dg.p, C->totG, w.gI, w.gl);
     CB_LAUNCH();
@@ -1698,7 +1806,17 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
                                                      yavg, z, w.zl);
     CB_LAUNCH();
   }
-  if (C->n_itI > 0) {
+  if (C->sparse_cpl) {
+    // z_I = A_II^-1 (r_I - K_I,Gamma z): the coupling overwrites the
+    // gathered r_I (no longer needed) with its right-hand side
+    coupling_kernel<T><<<cdiv(C->totI, 256), 256, 0, s>>>(C->cig_ptr.p, C->cig_col.p,
+                                                        reinterpret_cast<const T*>(C->cig_val.p),
+                                                        C->gdofI.p, r, z, w.xI, C->totI);
+    CB_LAUNCH();
+    apply_interior_kernel<T, true><<<C->n_itI, 256, smI, s>>>(
+        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->gdofI.p, Aloc, w.xI, z);
+    CB_LAUNCH();
+  } else if (C->n_itI > 0) {
     apply_extend_kernel<T><<<C->n_itI, 256,
                              (size_t)round_up(std::max(C->maxG, 4), 4) * sizeof(T), s>>>(
         C->itI.p, C->d_nI.p, C->d_nG.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->d_offGam.p, C->gdofI.p,
@@ -1802,6 +1920,7 @@ int64_t bddc_ctx::device_bytes() const {
                    Sc.bytes() + ScX.bytes() + ScY.bytes() + ScP.bytes() + u0.bytes() + hG.bytes() +
                    gI.bytes() + wG.bytes() + cl.bytes() + rc.bytes() + uc.bytes() + yG.bytes() + gl.bytes() + xI.bytes() + zl.bytes() +
                    Dsb.bytes() + Ddb.bytes() + Deb.bytes() + Dsh.bytes() + DX.bytes() + DY.bytes() + DP.bytes() +
-                   yD.bytes() + Psi.bytes()) +
+                   yD.bytes() + Psi.bytes() + cgi_ptr.bytes() + cgi_col.bytes() + cgi_src.bytes() +
+                   cgi_val.bytes() + cig_ptr.bytes() + cig_col.bytes() + cig_src.bytes() + cig_val.bytes()) +
          (next ? next->device_bytes() + coarse_prob->device_bytes() : 0);
 }

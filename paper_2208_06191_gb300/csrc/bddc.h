@@ -10,6 +10,8 @@ struct bddc_ctx {
   fem_problem* P = nullptr;
   int precision = CBDDC_FP64, primal = CBDDC_PRIMAL_V;
   int nb = 64;                              // pivot block width of the local sweeps
+  int tile_order = 0;                       // setup GEMM tiles: 0 by subdomain, 1 largest first
+  float ms_setup_tuned = 0.f, ms_setup_default = 0.f;  // autotuning record (FP32 contexts)
   double pivot_tol = 1e-13;
   int nsub = 0;
   size_t esize = 8;  // bytes per element of the local operators
@@ -45,6 +47,14 @@ struct bddc_ctx {
   cbddc::DVec<int2> itI, itG, itP, itR;
   int n_itI = 0, n_itG = 0, n_itP = 0, n_itR = 0;
   cbddc::DVec<int> cnch;                   // coarse-restriction chunks per local primal entry
+  // sparse interior-interface coupling blocks of the assembled matrix
+  // (problems with a global BSR): rows = assembled interface nodes, columns
+  // = packed interior nodes (cgi); rows = packed interior nodes, columns =
+  // free nodes on the interface (cig); src = block index in the BSR
+  bool sparse_cpl = false;
+  int64_t n_cgi = 0, n_cig = 0;
+  cbddc::DVec<int> cgi_ptr, cgi_col, cgi_src, cig_ptr, cig_col, cig_src;
+  cbddc::DVec<unsigned char> cgi_val, cig_val;
   // apply work vectors
   cbddc::DVec<double> u0, hG, gI, wG, cl, rc, uc, yG, xI, zl;
   // sweep descriptors and GEMM problem lists

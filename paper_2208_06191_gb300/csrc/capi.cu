@@ -3,6 +3,8 @@
 // of Section 2 (load steps, Newton on Eq. tangent problem).
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <memory>
 #include <cmath>
 #include <new>
 #include <string>
@@ -145,8 +147,7 @@ static void fill_tangent(fem_problem* P, fem_tangent* K) {
 
 static int sweep_block_of(const bddc_options* opt) { return opt->sweep_block == 128 ? 128 : 64; }
 
-static void ensure_ctx(fem_problem* P, const solve_options* opt, bddc_ctx** C) {
-  if (*C) return;
+static bddc_options options_of(const solve_options* opt) {
   bddc_options bo{};
   bo.precision = opt->precision;
   bo.primal = opt->primal;
@@ -159,6 +160,18 @@ static void ensure_ctx(fem_problem* P, const solve_options* opt, bddc_ctx** C) {
   bo.scaling = opt->scaling;
   bo.coarse = opt->coarse;
   bo.sweep_block = opt->sweep_block;
+  bo.tile_order = opt->tile_order;
+  return bo;
+}
+
+static void ensure_ctx(fem_problem* P, const solve_options* opt, bddc_ctx** C) {
+  if (*C) return;
+  bddc_options bo = options_of(opt);
+  const int pi = opt->precision == CBDDC_FP32 ? 1 : 0;
+  if (opt->autotune && P->tuned_to[pi] >= 0) {
+    bo.sweep_block = P->tuned_nb[pi];
+    bo.tile_order = P->tuned_to[pi];
+  }
   bddc_ctx* c = new bddc_ctx;
   try {
     bddc_create(P, &bo, c);
@@ -166,8 +179,13 @@ static void ensure_ctx(fem_problem* P, const solve_options* opt, bddc_ctx** C) {
     delete c;
     throw;
   }
+  if (opt->autotune) {
+    c->ms_setup_tuned = P->tuned_ms[pi];
+    c->ms_setup_default = P->default_ms[pi];
+  }
   *C = c;
 }
+
 
 static void ensure_work(bddc_ctx* C, int64_t n) {
   if (C->nw_r.n != (size_t)n) {
@@ -193,10 +211,63 @@ struct Events {
   }
 };
 
+// Autotuning of the setup (solve_options.autotune): on the tangent at d,
+// one timed setup (after an untimed one) per candidate {sweep block 64 /
+// 128 (FP32 only)} x {tile order 0 / 1}; the fastest is cached in P per
+// precision.  Returns the time spent (ms).
+static float autotune_setup(fem_problem* P, const solve_options* opt, double lam, const double* d,
+                            cudaStream_t s) {
+  const int pi = opt->precision == CBDDC_FP32 ? 1 : 0;
+  if (P->tuned_to[pi] >= 0) return 0.f;
+  const auto t0 = std::chrono::steady_clock::now();
+  {
+    DVec<double> rtmp;
+    rtmp.alloc(P->n_free);
+    assemble(P, d, lam, rtmp.p, true, s);
+    CB_CUDA(cudaStreamSynchronize(s));
+  }
+  CB_CHECK(!(take_status(P, s) & DEV_INVERTED), CBDDC_EINVERTED, "J <= 0 at a quadrature point");
+  std::vector<int> nbs{64};
+  if (opt->precision == CBDDC_FP32) nbs.push_back(128);
+  float best = 1e30f, dflt = 0.f;
+  int best_nb = 64, best_to = 0;
+  for (int nb : nbs) {
+    for (int to = 0; to < 2; ++to) {
+      bddc_options bo = options_of(opt);
+      bo.sweep_block = nb;
+      bo.tile_order = to;
+      std::unique_ptr<bddc_ctx> c(new bddc_ctx);
+      bddc_create(P, &bo, c.get());
+      bddc_run_setup(c.get(), s);
+      Events ev;
+      CB_CUDA(cudaEventRecord(ev.e[0], s));
+      bddc_run_setup(c.get(), s);
+      CB_CUDA(cudaEventRecord(ev.e[1], s));
+      CB_CUDA(cudaEventSynchronize(ev.e[1]));
+      const int st = take_status(P, s);
+      if (st & (DEV_PIVOT | DEV_TIMEOUT)) continue;  // not a usable candidate
+      const float ms = ev.ms(0, 1);
+      if (nb == 64 && to == 0) dflt = ms;
+      if (ms < best) {
+        best = ms;
+        best_nb = nb;
+        best_to = to;
+      }
+    }
+  }
+  P->tuned_nb[pi] = best_nb;
+  P->tuned_to[pi] = best_to;
+  P->tuned_ms[pi] = best < 1e30f ? best : 0.f;
+  P->default_ms[pi] = dflt;
+  return std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 // One Newton step at load lam: assemble residual + tangent, BDDC setup,
 // GMRES on DF(d) delta = -F(d), d += delta.  Returns the GMRES status.
 static int newton_step_impl(fem_problem* P, bddc_ctx** Cp, const solve_options* opt, double lam,
                             double* d, newton_record* rec, cudaStream_t s) {
+  float tune_ms = 0.f;
+  if (opt->autotune && *Cp == nullptr) tune_ms = autotune_setup(P, opt, lam, d, s);
   ensure_ctx(P, opt, Cp);
   bddc_ctx* C = *Cp;
   const int64_t n = P->n_free;
@@ -233,6 +304,7 @@ static int newton_step_impl(fem_problem* P, bddc_ctx** Cp, const solve_options* 
     rec->ms_total = ev.ms(0, 4);
     rec->gmres_relres = rel;
     rec->gmres_reorth = C->gm.reorth;
+    rec->ms_autotune = tune_ms;
   }
   return gst;
 }
@@ -405,6 +477,10 @@ int bddc_get_info(const bddc_ctx* C, bddc_info* info) {
     info->local_bytes = C->local_bytes;
     info->device_bytes = C->device_bytes();
     info->setup_flops = C->setup_flops;
+    info->sweep_block = C->nb;
+    info->tile_order = C->tile_order;
+    info->ms_setup_tuned = C->ms_setup_tuned;
+    info->ms_setup_default = C->ms_setup_default;
   });
 }
 

@@ -153,5 +153,9 @@ struct fem_problem {
   cbddc::DVec<int> status;                  // device error bits
   cbddc::DVec<double> scratch;              // norms etc.
   bool has_tangent = false;
+  // autotuned setup per precision (index 0 FP64, 1 FP32): sweep block,
+  // tile order (-1: not tuned yet) and the measured setup times
+  int tuned_nb[2] = {64, 64}, tuned_to[2] = {-1, -1};
+  float tuned_ms[2] = {0.f, 0.f}, default_ms[2] = {0.f, 0.f};
   int64_t device_bytes() const;
 };

@@ -316,7 +316,9 @@ struct GemmList {
   int np = 2;  // TF32 parts per operand
   tc::TcMaps maps;
   std::vector<GemmProb> h;  // host copy of the problems
-  void set(const std::vector<GemmProb>& v, size_t esize, bool ta = false) {
+  // order 1: tiles of the largest problems (M N K) first, so that with
+  // uneven subdomains the long tile runs of a persistent kernel start early
+  void set(const std::vector<GemmProb>& v, size_t esize, bool ta = false, int order = 0) {
     h = v;
     n = (int)v.size();
     flops = bytes = 0.0;
@@ -332,6 +334,10 @@ struct GemmList {
       if (q.a % w || q.b % w || q.lda % w || q.ldb % w) fast = false;
       for (int tm = 0; tm < (int)cdiv(q.M, tile); ++tm)
         for (int tn = 0; tn < (int)cdiv(q.N, tile); ++tn) t.push_back(make_int4(i, tm, tn, 0));
+    }
+    if (order == 1) {
+      auto work = [&](const int4& a) { return (double)v[a.x].M * v[a.x].N * v[a.x].K; };
+      std::stable_sort(t.begin(), t.end(), [&](const int4& a, const int4& b) { return work(a) > work(b); });
     }
     ntiles = (int)t.size();
     d.upload(v);

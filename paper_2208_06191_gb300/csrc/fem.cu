@@ -1044,52 +1044,38 @@ void assemble(fem_problem* P, const double* d, double lam, double* residual, boo
   }
 }
 
-// y = K x, one warp per block row.  FP64 issue is the roof here (GB300 runs
-// about two FP64 FMAs per SM and clock), so every lane keeps one fixed
-// entry e = lane % 9 (row r = e / 3, column c = e % 3) of the 3 x 3 blocks
-// and takes block 3 t + lane / 9 at step t: 27 lanes read 27 consecutive
-// values of the row's contiguous block run (coalesced) and issue one FMA
-// each.  The row's column indices are read once (coalesced, 32 at a time)
-// and passed by shuffle, so the x gathers do not wait on a dependent load.
-// Partial sums: lanes with equal e, then the three e of each r.
+// y = K x, three threads per block row: thread 3 i + r forms row r of the
+// block row i, walking the row's blocks in order with one FMA per block
+// entry of that row (three independent chains) and no reduction between
+// threads.  FP64 FMA issue is the roof here (GB300 runs about two FP64 FMAs
+// per SM and clock), so all 32 lanes of a warp carry useful FMAs except for
+// the length differences of the about eleven block rows a warp holds; the
+// 72-byte blocks of those rows are read 24 bytes per thread, and the
+// sectors a thread leaves are the ones its row reads next (kept in L1).
 __global__ void __launch_bounds__(256)
 bsr_spmv_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col, const double* __restrict__ vals,
                 const double* __restrict__ x, double* __restrict__ y, int nrows) {
-  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= nrows) return;
-  const int b0 = __ldg(row_ptr + row), nb = __ldg(row_ptr + row + 1) - b0;
-  const int e = lane % 9, q = lane / 9, c = e % 3;
-  const bool active = lane < 27;
-  const double* v = vals + (int64_t)b0 * 9;
-  double acc = 0.0;
-  for (int base = 0; base < nb; base += 32) {
-    // column indices of blocks base .. base + 31 of this row
-    const int cl = (base + lane < nb) ? __ldg(col + b0 + base + lane) : 0;
-    const int nbc = min(32, nb - base);
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 3 * (int64_t)nrows) return;
+  const int row = (int)(t / 3), r = (int)(t - 3 * (int64_t)row);
+  const int b0 = __ldg(row_ptr + row), b1 = __ldg(row_ptr + row + 1);
+  const double* v = vals + (int64_t)b0 * 9 + 3 * r;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
 #pragma unroll 4
-    for (int t = 0; t < 11; ++t) {      // 11 steps of 3 blocks cover 32 blocks
-      const int bl = 3 * t + q;           // block within this chunk of 32
-      const int cb = __shfl_sync(0xffffffffu, cl, bl & 31);
-      if (3 * t >= nbc) break;
-      if (active && bl < nbc)
-        acc = fma(__ldcs(v + (int64_t)(base + bl) * 9 + e), __ldg(x + (int64_t)cb * 3 + c), acc);
-    }
+  for (int b = b0; b < b1; ++b, v += 9) {
+    const double* xc = x + (int64_t)__ldg(col + b) * 3;
+    a0 = fma(__ldg(v), __ldg(xc), a0);
+    a1 = fma(__ldg(v + 1), __ldg(xc + 1), a1);
+    a2 = fma(__ldg(v + 2), __ldg(xc + 2), a2);
   }
-  // lanes 0..8: entry e summed over the lanes e, e + 9, e + 18; then lanes
-  // 0, 3, 6: the three entries of row r = lane / 3
-  const double s = acc + __shfl_sync(0xffffffffu, acc, (lane + 9) & 31) +
-                   __shfl_sync(0xffffffffu, acc, (lane + 18) & 31);
-  const double s1 = __shfl_sync(0xffffffffu, s, (lane + 1) & 31);
-  const double s2 = __shfl_sync(0xffffffffu, s, (lane + 2) & 31);
-  if (lane < 9 && lane % 3 == 0) y[(int64_t)row * 3 + lane / 3] = s + s1 + s2;
+  y[t] = a0 + a1 + a2;
 }
 
 void bsr_spmv(const fem_problem* P, const double* x, double* y, cudaStream_t s) {
   const int64_t rows = P->n_free_nodes;
   timer_begin(CBDDC_TIMER_SPMV, s);
-  bsr_spmv_kernel<<<cdiv(rows * 32, 256), 256, 0, s>>>(P->bsr_row_ptr.p, P->bsr_col.p,
-                                                       P->bsr_vals.p, x, y, (int)rows);
+  bsr_spmv_kernel<<<cdiv(rows * 3, 256), 256, 0, s>>>(P->bsr_row_ptr.p, P->bsr_col.p,
+                                                      P->bsr_vals.p, x, y, (int)rows);
   CB_LAUNCH();
   // bytes: 9 values + 1 column index per block, x read and y written once
   timer_end(CBDDC_TIMER_SPMV, s, 18.0 * P->nnzb, 76.0 * P->nnzb + 16.0 * 3 * rows);

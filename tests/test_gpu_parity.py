@@ -123,6 +123,7 @@ def test_bddc_apply_parity(primal, precision, tol):
         pc.apply(_dev(r), z)
         z_ref = ref.apply(r)
         assert np.linalg.norm(_host(z) - z_ref) <= tol * np.linalg.norm(z_ref)
+        assert np.abs(_host(z) - z_ref).max() <= 2 * tol * np.abs(z_ref).max()
 
 
 @pytest.mark.parametrize("order,parts", [(2, (2, 2, 1)), (1, (3, 1, 2))])
@@ -134,6 +135,7 @@ def test_bddc_apply_parity_q2_and_uneven(order, parts):
     pc.apply(_dev(r), z)
     z_ref = ref.apply(r)
     assert np.linalg.norm(_host(z) - z_ref) <= 1e-9 * np.linalg.norm(z_ref)
+    assert np.abs(_host(z) - z_ref).max() <= 2 * 1e-9 * np.abs(z_ref).max()
 
 
 def test_single_subdomain_is_exact_solve():
@@ -251,6 +253,7 @@ def test_full_size_slab_residual_and_apply_sampled():
         pc.apply(_dev(-r_ref), z)
         z_ref = ref.apply(-r_ref)
         assert np.linalg.norm(_host(z) - z_ref) <= tol * np.linalg.norm(z_ref)
+        assert np.abs(_host(z) - z_ref).max() <= 2 * tol * np.abs(z_ref).max()
 
 
 # ------------------------------------------------------------- multilevel
@@ -280,6 +283,7 @@ def test_multilevel_apply_parity(precision, tol):
     pc.apply(_dev(r), z)
     z_ref = ref.apply(r)
     assert np.linalg.norm(_host(z) - z_ref) <= tol * np.linalg.norm(z_ref)
+    assert np.abs(_host(z) - z_ref).max() <= 2 * tol * np.abs(z_ref).max()
 
 
 def test_rotations_refused_for_multilevel():
@@ -326,3 +330,39 @@ def test_multilevel_newton_solve_fp32():
     assert repm["final_rel_residual"] <= 1e-8
     assert repm["total_gmres_its"] >= rep2["total_gmres_its"]
     assert float(torch.linalg.vector_norm(dm - d2)) <= 1e-6 * float(torch.linalg.vector_norm(d2))
+
+
+@pytest.mark.parametrize("config", ["ragged", "slab48_q1"])
+def test_tensor_core_setup_accuracy(config):
+    """FP32 local operators from the tcgen05 setup GEMMs (split TF32
+    operands, slices of K summed in FP32 on the CUDA cores) are as close to
+    the FP64 operators as those from FP32 CUDA-core GEMMs: the BDDC apply's
+    distance to the FP64 apply, element by element and in norm."""
+    prob = slab_problem(order=1, **RAGGED) if config == "ragged" else slab_config(config)
+    P = pkg.Problem(prob)
+    fe = FEProblem(prob)
+    d = smooth_displacement(fe, seed=31) if config == "ragged" else np.zeros(fe.n_free)
+    P.assemble_tangent(_dev(d), 0.75)
+    r = _dev(np.random.default_rng(12).standard_normal(fe.n_free))
+    primal = "VEF" if config == "ragged" else prob["primal"]
+
+    def apply(precision, mode):
+        prev = pkg.set_tensor_cores(mode)
+        try:
+            pc = pkg.BDDC(P, precision=precision, primal=primal).setup()
+            z = torch.empty_like(r)
+            pc.apply(r, z)
+            return _host(z)
+        finally:
+            pkg.set_tensor_cores(prev)
+
+    z64 = apply(pkg.FP64, 1)
+    z_tc = apply(pkg.FP32, 1)
+    z_cc = apply(pkg.FP32, 0)
+    e_tc = np.linalg.norm(z_tc - z64) / np.linalg.norm(z64)
+    e_cc = np.linalg.norm(z_cc - z64) / np.linalg.norm(z64)
+    assert e_tc <= 1e-3 and e_cc <= 1e-3
+    assert e_tc <= 1.5 * e_cc, (e_tc, e_cc)
+    m_tc = np.abs(z_tc - z64).max() / np.abs(z64).max()
+    m_cc = np.abs(z_cc - z64).max() / np.abs(z64).max()
+    assert m_tc <= 1.5 * m_cc, (m_tc, m_cc)

@@ -98,6 +98,7 @@ def test_tet_bddc_apply_parity(order, primal, precision, tol):
     pc.apply(_dev(r), z)
     z_ref = ref.apply(r)
     assert np.linalg.norm(_host(z) - z_ref) <= tol * np.linalg.norm(z_ref)
+    assert np.abs(_host(z) - z_ref).max() <= 2 * tol * np.abs(z_ref).max()
 
 
 def test_tet_multilevel_apply_parity():
@@ -117,6 +118,7 @@ def test_tet_multilevel_apply_parity():
     pc.apply(_dev(r), z)
     z_ref = ref.apply(r)
     assert np.linalg.norm(_host(z) - z_ref) <= 1e-9 * np.linalg.norm(z_ref)
+    assert np.abs(_host(z) - z_ref).max() <= 2 * 1e-9 * np.abs(z_ref).max()
 
 
 @pytest.mark.parametrize("order", [1, 2])
