@@ -339,11 +339,13 @@ typedef struct {
   double rel_residual; /* true relative residual at exit                    */
 } gmres_report;
 
-/* Flexible GMRES (right preconditioned by BDDC, Arnoldi by classical
-   Gram-Schmidt applied twice, FP64) for K x = b with the last assembled
-   tangent of P.  b, x: dev [n_free]; x is overwritten (zero initial
-   guess).  Synchronises once per iteration to test convergence.  Returns
-   CBDDC_ENOCONV if max_iters is reached. */
+/* Flexible GMRES (right preconditioned by BDDC) for K x = b with the last
+   assembled tangent of P.  Arnoldi step in FP64: for n_free <= 10^6 and
+   at most 128 basis vectors classical Gram-Schmidt applied twice, else
+   modified Gram-Schmidt.  b, x:
+   dev [n_free]; x is overwritten (zero initial guess).  Synchronises once
+   per iteration to test convergence.  Returns CBDDC_ENOCONV if max_iters
+   is reached. */
 CBDDC_API int gmres_solve(fem_problem* P, bddc_ctx* C, const double* b, double* x,
                 const gmres_options* opt, gmres_report* rep,
                 cbddc_stream_t stream);
@@ -439,8 +441,8 @@ enum {
   CBDDC_TIMER_ELEMENT = 2,    /* element residual/tangent kernel              */
   CBDDC_TIMER_APPLY = 3,      /* one whole BDDC apply (all its launches)      */
   CBDDC_TIMER_SPMV = 4,       /* BSR SpMV                                     */
-  CBDDC_TIMER_ORTH = 5,       /* one GMRES orthogonalisation (CGS2, Givens,
-                                 normalisation)                               */
+  CBDDC_TIMER_ORTH = 5,       /* one GMRES Arnoldi step (Gram-Schmidt,
+                                 Givens, normalisation)                       */
   CBDDC_TIMER_SETUP = 6,      /* one whole BDDC setup (all levels)            */
   CBDDC_TIMER_LEVEL2_SETUP = 7, /* setup of the level-2 BDDC (multilevel)     */
   CBDDC_TIMER_LEVEL2_APPLY = 8, /* apply of the level-2 BDDC (multilevel)     */
