@@ -691,7 +691,7 @@ def run_kernels(args):
     P = pkg.Problem(prob)
     d = torch.zeros(P.n_free, dtype=torch.float64, device="cuda")
     r = torch.empty_like(d)
-    P.assemble_tangent(d, 1.0 / prob["load_steps"], r)
+    tangent = P.assemble_tangent(d, 1.0 / prob["load_steps"], r)
     ml = {}
     if spec["levels"] == 3:
         ml = dict(levels=3, part2=prob["part2"], n_parts2=prob["n_parts2"], primal2="VEF",
@@ -704,7 +704,9 @@ def run_kernels(args):
         pc.apply(r, z)
         P.spmv(z, y)
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "kernels", "n_free": P.n_free, "apply_norm": float(z.norm())}))
+    inf = pc.info()
+    print(json.dumps({"mode": "kernels", "n_free": P.n_free, "apply_norm": float(z.norm()),
+                      "local_bytes": inf["local_bytes"], "nnzb": tangent["nnzb"]}))
 
 
 def run_step(args):
