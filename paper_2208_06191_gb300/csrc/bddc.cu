@@ -431,7 +431,8 @@ __global__ void __launch_bounds__(256)
 apply_interior_kernel(const int2* __restrict__ items, const int* __restrict__ nI,
                       const int64_t* __restrict__ offA, const int* __restrict__ ldA,
                       const int64_t* __restrict__ offI, const int* __restrict__ gdofI,
-                      const T* __restrict__ Aloc, const double* __restrict__ xI, double* __restrict__ u0) {
+                      const T* __restrict__ Aloc, const double* __restrict__ xI, double* __restrict__ u0,
+                      T* __restrict__ uq) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* xs = reinterpret_cast<T*>(smraw);
   const int2 it = items[blockIdx.x];
@@ -442,50 +443,72 @@ apply_interior_kernel(const int2* __restrict__ items, const int* __restrict__ nI
   const int64_t oi = offI[s];
   load_x<T>(xs, xI + oi, ni);
   gemv_rows<T>(Aloc + offA[s], ldA[s], rb, min(ni, rb + GROWS * GGROUPS), xs, ni, [&](int row, T v) {
-    if (SCATTER) u0[gdofI[oi + row]] = (double)v;
-    else u0[oi + row] = (double)v;
+    if (SCATTER) {
+      u0[gdofI[oi + row]] = (double)v;
+    } else {
+      u0[oi + row] = (double)v;
+      // node-packed copy for the coupling product (packed interior DoFs
+      // are node-major, 3 per node)
+      if (uq) uq[(oi + row) / 3 * 4 + (oi + row) % 3] = v;
+    }
   });
 }
 
-// Sparse interior-interface coupling of the assembled matrix: out[t] =
-// r[rdof[t]] - (row t % 3 of block row t / 3) x, where the block row's 3x3
-// blocks (val, 9 per block, row-major) multiply x at 3 col[b] .. 3 col[b] +
-// 2.  Used twice per apply: g_Gamma = r_Gamma - K_Gamma,I u0 (rows: the
-// assembled interface nodes, x: the packed interior solution) and t_I =
-// r_I - K_I,Gamma z (rows: the packed interior nodes, x: the global z with
-// its interface entries set).  Three threads per block row, as the BSR
-// product, accumulating in the operator precision.
+// Sparse interior-interface coupling of the assembled matrix, in sliced
+// ELL form: slice q holds 32 block rows (node rows, sorted by length inside
+// windows of 8 slices), step k of lane l is block k of row rowmap[32 q + l]
+// (column 0 and zero values past the row's end).  Values are stored
+// [step][entry][lane] and column indices [step][lane], so each load of a
+// warp reads 128 consecutive bytes; x comes node-packed as (x, y, z, pad).
+// out[3 i + r] = r_in[rdof[3 i + r]] - (row r of block row i) x.  Used
+// twice per apply: g_Gamma = r_Gamma - K_Gamma,I u0 (rows: assembled
+// interface nodes, x: the packed interior solution) and t_I = r_I -
+// K_I,Gamma z (rows: packed interior nodes, x: z on the interface nodes).
+// One lane per block row, all nine products in the operator precision.
+template <typename T> struct Q4;
+template <> struct Q4<float> { using type = float4; };
+template <> struct Q4<double> { using type = double4; };
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-coupling_kernel(const int* __restrict__ ptr, const int* __restrict__ col, const T* __restrict__ val,
-                const int* __restrict__ rdof, const double* __restrict__ r, const double* __restrict__ x,
-                double* __restrict__ out, int64_t n) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const int64_t row = t / 3;
-  const int rr = (int)(t - 3 * row);
-  const int b0 = __ldg(ptr + row), b1 = __ldg(ptr + row + 1);
-  const T* v = val + (int64_t)b0 * 9 + 3 * rr;
+coupling_kernel(const int* __restrict__ off, const int* __restrict__ len, const int* __restrict__ rowmap,
+                const int* __restrict__ col, const T* __restrict__ val,
+                const typename Q4<T>::type* __restrict__ xq, const int* __restrict__ rdof,
+                const double* __restrict__ r, double* __restrict__ out, int nslices) {
+  const int q = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q >= nslices) return;
+  const int row = rowmap[32 * q + lane];
+  const int L = len[q];
+  const int64_t base = off[q];
   T a0 = T(0), a1 = T(0), a2 = T(0);
-#pragma unroll 4
-  for (int b = b0; b < b1; ++b, v += 9) {
-    const double* xc = x + (int64_t)__ldg(col + b) * 3;
-    a0 = fma(__ldg(v), (T)__ldg(xc), a0);
-    a1 = fma(__ldg(v + 1), (T)__ldg(xc + 1), a1);
-    a2 = fma(__ldg(v + 2), (T)__ldg(xc + 2), a2);
+#pragma unroll 2
+  for (int k = 0; k < L; ++k) {
+    const typename Q4<T>::type x = xq[__ldg(col + (base + k) * 32 + lane)];
+    const T* v = val + (base + k) * 288 + lane;
+    a0 = fma(__ldcs(v + 0), x.x, fma(__ldcs(v + 32), x.y, fma(__ldcs(v + 64), x.z, a0)));
+    a1 = fma(__ldcs(v + 96), x.x, fma(__ldcs(v + 128), x.y, fma(__ldcs(v + 160), x.z, a1)));
+    a2 = fma(__ldcs(v + 192), x.x, fma(__ldcs(v + 224), x.y, fma(__ldcs(v + 256), x.z, a2)));
   }
-  out[t] = r[rdof[t]] - (double)(a0 + a1 + a2);
+  if (row >= 0) {
+    out[3 * (int64_t)row + 0] = r[rdof[3 * row + 0]] - (double)a0;
+    out[3 * (int64_t)row + 1] = r[rdof[3 * row + 1]] - (double)a1;
+    out[3 * (int64_t)row + 2] = r[rdof[3 * row + 2]] - (double)a2;
+  }
 }
 
-// val[9 k + e] = (T) bsr_vals[9 src[k] + e]: the coupling blocks of the
-// assembled tangent in the operator precision (once per setup).
+// Values of the sliced coupling blocks from the assembled tangent, in the
+// operator precision (once per setup): val[(step 9 + e) 32 + lane] = entry
+// e of BSR block src[step 32 + lane] (zero where src < 0).
 template <typename T>
-__global__ void coupling_values_kernel(const int* __restrict__ src, int64_t nblk,
+__global__ void coupling_values_kernel(const int* __restrict__ src, int64_t steps,
                                        const double* __restrict__ bsr_vals, T* __restrict__ val) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= 9 * nblk) return;
-  const int64_t k = t / 9;
-  val[t] = (T)bsr_vals[(int64_t)src[k] * 9 + (t - 9 * k)];
+  if (t >= steps * 288) return;
+  const int64_t step = t / 288;
+  const int rem = (int)(t - step * 288), e = rem >> 5, lane = rem & 31;
+  const int b = src[step * 32 + lane];
+  val[t] = b >= 0 ? (T)bsr_vals[(int64_t)b * 9 + e] : T(0);
 }
 
 // hG = -A_GI u0 (the interface part of the interior correction).
@@ -688,7 +711,9 @@ apply_prolong_kernel(const int2* __restrict__ items, const int* __restrict__ nG,
                      const int* __restrict__ gprim, const T* __restrict__ Phi,
                      const double* __restrict__ uc, const double* __restrict__ wG,
                      const double* __restrict__ Dg, double* __restrict__ yG) {
-  __shared__ T ucl[NC_MAX];
+  using V = typename Vec2<T>::type;
+  constexpr int W = Vec2<T>::W;
+  __shared__ __align__(16) T ucl[NC_MAX];
   const int2 it = items[blockIdx.x];
   const int s = it.x;
   const int ng = nG[s], ncs = nc[s];
@@ -700,9 +725,15 @@ apply_prolong_kernel(const int2* __restrict__ items, const int* __restrict__ nG,
   const int row = r0 + grp;
   T acc = T(0);  // operator precision, as in the other local products
   if (row < ng) {
+    // rows start 16-byte aligned (offsets and leading dimensions are
+    // multiples of 8 elements): 8 lanes read 8 consecutive 16-byte chunks
     const T* pr = Phi + offPhi[s] + (int64_t)row * ldPhi[s];
-#pragma unroll 4
-    for (int c = sub; c < ncs; c += 8) acc += pr[c] * ucl[c];
+    const V* pv = reinterpret_cast<const V*>(pr);
+    const V* uv = reinterpret_cast<const V*>(ucl);
+    const int nv = ncs / W;
+#pragma unroll 2
+    for (int c = sub; c < nv; c += 8) acc += vdot2(__ldcs(pv + c), uv[c]);
+    for (int c = nv * W + sub; c < ncs; c += 8) acc += pr[c] * ucl[c];
   }
   acc += __shfl_xor_sync(0xffffffffu, acc, 4);
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
@@ -714,16 +745,20 @@ apply_prolong_kernel(const int2* __restrict__ items, const int* __restrict__ nG,
 }
 
 // z_G = sum over sharing subdomains of yG; also written to every packed
-// local interface position (zl), the input of the harmonic extension.
+// local interface position (zl), the input of the harmonic extension, and,
+// if zq is given, node-packed in the operator precision (the coupling
+// product's input; interface DoFs are node-major, 3 per node).
+template <typename T>
 __global__ void average_kernel(const int* __restrict__ if_dof, const int* __restrict__ if_ptr,
                                const int* __restrict__ if_src, int n_if, const double* __restrict__ yG,
-                               double* __restrict__ z, double* __restrict__ zl) {
+                               double* __restrict__ z, double* __restrict__ zl, T* __restrict__ zq) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_if) return;
   double v = 0.0;
   for (int j = if_ptr[m]; j < if_ptr[m + 1]; ++j) v += yG[if_src[j]];
   z[if_dof[m]] = v;
   for (int j = if_ptr[m]; j < if_ptr[m + 1]; ++j) zl[if_src[j]] = v;
+  if (zq) zq[m / 3 * 4 + m % 3] = (T)v;
 }
 
 template <typename T>
@@ -829,6 +864,60 @@ static void build_coarse_problem(bddc_ctx* C, fem_problem* CP) {
   CB_CUDA(cudaMemset(CP->status.p, 0, CP->status.bytes()));
   CP->has_tangent = true;
   C->d_cbase.upload(cbase);
+}
+
+// Sliced ELL layout (32 rows per slice) of a block matrix given as CSR over
+// node rows: rows sorted by decreasing length inside windows of 8 slices,
+// so that a slice's rows have similar lengths and neighbouring rows stay
+// together.
+struct SellHost {
+  std::vector<int> off, len, row, col, src;
+  int64_t steps = 0;
+};
+
+static SellHost build_sell(const std::vector<int>& ptr, const std::vector<int>& col,
+                           const std::vector<int>& src) {
+  const int nrows = (int)ptr.size() - 1;
+  std::vector<int> order(nrows);
+  for (int i = 0; i < nrows; ++i) order[i] = i;
+  for (int w0 = 0; w0 < nrows; w0 += 256) {
+    const int w1 = std::min(nrows, w0 + 256);
+    std::stable_sort(order.begin() + w0, order.begin() + w1,
+                     [&](int a, int b) { return ptr[a + 1] - ptr[a] > ptr[b + 1] - ptr[b]; });
+  }
+  const int nsl = (nrows + 31) / 32;
+  SellHost S;
+  S.off.assign(nsl + 1, 0);
+  S.len.assign(nsl, 0);
+  S.row.assign((size_t)nsl * 32, -1);
+  int64_t steps = 0;
+  for (int q = 0; q < nsl; ++q) {
+    int L = 0;
+    for (int l = 0; l < 32 && 32 * q + l < nrows; ++l) {
+      const int r = order[32 * q + l];
+      S.row[32 * q + l] = r;
+      L = std::max(L, ptr[r + 1] - ptr[r]);
+    }
+    CB_CHECK(steps < INT32_MAX, CBDDC_EINVAL, "coupling matrix too large");
+    S.off[q] = (int)steps;
+    S.len[q] = L;
+    steps += L;
+  }
+  S.off[nsl] = (int)steps;
+  S.steps = steps;
+  S.col.assign((size_t)steps * 32, 0);
+  S.src.assign((size_t)steps * 32, -1);
+  for (int q = 0; q < nsl; ++q)
+    for (int l = 0; l < 32; ++l) {
+      const int r = S.row[32 * q + l];
+      if (r < 0) continue;
+      for (int k = 0; k < ptr[r + 1] - ptr[r]; ++k) {
+        const size_t p = ((size_t)S.off[q] + k) * 32 + l;
+        S.col[p] = col[ptr[r] + k];
+        S.src[p] = src[ptr[r] + k];
+      }
+    }
+  return S;
 }
 
 void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
@@ -1376,9 +1465,9 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     CB_CUDA(cudaMemcpy(rp.data(), P->bsr_row_ptr.p, rp.size() * sizeof(int), cudaMemcpyDeviceToHost));
     CB_CUDA(cudaMemcpy(bc.data(), P->bsr_col.p, bc.size() * sizeof(int), cudaMemcpyDeviceToHost));
     std::vector<int> int_of(nfn, -1);  // free node -> packed interior node
-    std::vector<char> on_if(nfn, 0);
+    std::vector<int> if_of(nfn, -1);   // free node -> interface node
     for (int64_t q = 0; q < C->totI; q += 3) int_of[gdofI[q] / 3] = (int)(q / 3);
-    for (int m = 0; m < C->n_if; m += 3) on_if[if_dof[m] / 3] = 1;
+    for (int m = 0; m < C->n_if; m += 3) if_of[if_dof[m] / 3] = m / 3;
     std::vector<int> gptr{0}, gcol, gsrc, iptr{0}, icol, isrc;
     for (int m = 0; m < C->n_if; m += 3) {
       const int f = if_dof[m] / 3;
@@ -1389,15 +1478,25 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     for (int64_t q = 0; q < C->totI; q += 3) {
       const int f = gdofI[q] / 3;
       for (int b = rp[f]; b < rp[f + 1]; ++b)
-        if (on_if[bc[b]]) { icol.push_back(bc[b]); isrc.push_back(b); }
+        if (if_of[bc[b]] >= 0) { icol.push_back(if_of[bc[b]]); isrc.push_back(b); }
       iptr.push_back((int)icol.size());
     }
-    C->n_cgi = (int64_t)gcol.size();
-    C->n_cig = (int64_t)icol.size();
-    C->cgi_ptr.upload(gptr); C->cgi_col.upload(gcol); C->cgi_src.upload(gsrc);
-    C->cig_ptr.upload(iptr); C->cig_col.upload(icol); C->cig_src.upload(isrc);
-    C->cgi_val.alloc((size_t)std::max<int64_t>(C->n_cgi, 1) * 9 * C->esize);
-    C->cig_val.alloc((size_t)std::max<int64_t>(C->n_cig, 1) * 9 * C->esize);
+    C->n_cpl_blocks = (int64_t)gcol.size() + (int64_t)icol.size();
+    const SellHost gi = build_sell(gptr, gcol, gsrc), ig = build_sell(iptr, icol, isrc);
+    C->n_sgi = (int)gi.len.size();
+    C->n_sig = (int)ig.len.size();
+    C->steps_gi = gi.steps;
+    C->steps_ig = ig.steps;
+    C->sgi_off.upload(gi.off); C->sgi_len.upload(gi.len); C->sgi_row.upload(gi.row);
+    C->sgi_col.upload(gi.col); C->sgi_src.upload(gi.src);
+    C->sig_off.upload(ig.off); C->sig_len.upload(ig.len); C->sig_row.upload(ig.row);
+    C->sig_col.upload(ig.col); C->sig_src.upload(ig.src);
+    C->sgi_val.alloc((size_t)std::max<int64_t>(gi.steps, 1) * 288 * C->esize);
+    C->sig_val.alloc((size_t)std::max<int64_t>(ig.steps, 1) * 288 * C->esize);
+    C->uq.alloc((size_t)(C->totI / 3) * 4 * C->esize);
+    C->zq.alloc((size_t)(C->n_if / 3) * 4 * C->esize);
+    CB_CUDA(cudaMemset(C->uq.p, 0, C->uq.bytes()));
+    CB_CUDA(cudaMemset(C->zq.p, 0, C->zq.bytes()));
   }
   // flops of one setup and bytes of local operators read per apply
   double fl = 0.0;
@@ -1411,8 +1510,9 @@ void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
     if (C->sparse_cpl) lb += (int64_t)((2.0 * ni * ni + nr * nr + 2.0 * ng * nc) * C->esize);
     else lb += (int64_t)((ni * ni + 2.0 * ni * ng + nr * nr + 2.0 * ng * nc) * C->esize);
   }
-  // coupling blocks: 9 values and one column index each
-  if (C->sparse_cpl) lb += (C->n_cgi + C->n_cig) * (int64_t)(9 * C->esize + 4);
+  // coupling blocks: 9 values and one column index each (padding of the
+  // sliced layout not counted)
+  if (C->sparse_cpl) lb += C->n_cpl_blocks * (int64_t)(9 * C->esize + 4);
   fl += dlx_flops;
   lb += dlx_bytes;
   // multilevel: coarse problem and its BDDC context
@@ -1576,14 +1676,14 @@ static void setup_impl(bddc_ctx* C, cudaStream_t s) {
   launch_list<T, false, false>(C->gl_E, Aloc, Aloc, Et, T(1), T(0), s);
   launch_list<T, false, false>(C->gl_S, Aloc, Et, Aloc, T(-1), T(1), s);
   if (C->sparse_cpl) {  // the apply reads the coupling blocks, not E
-    if (C->n_cgi > 0) {
-      coupling_values_kernel<T><<<cdiv(9 * C->n_cgi, 256), 256, 0, s>>>(
-          C->cgi_src.p, C->n_cgi, P->bsr_vals.p, reinterpret_cast<T*>(C->cgi_val.p));
+    if (C->steps_gi > 0) {
+      coupling_values_kernel<T><<<cdiv(288 * C->steps_gi, 256), 256, 0, s>>>(
+          C->sgi_src.p, C->steps_gi, P->bsr_vals.p, reinterpret_cast<T*>(C->sgi_val.p));
       CB_LAUNCH();
     }
-    if (C->n_cig > 0) {
-      coupling_values_kernel<T><<<cdiv(9 * C->n_cig, 256), 256, 0, s>>>(
-          C->cig_src.p, C->n_cig, P->bsr_vals.p, reinterpret_cast<T*>(C->cig_val.p));
+    if (C->steps_ig > 0) {
+      coupling_values_kernel<T><<<cdiv(288 * C->steps_ig, 256), 256, 0, s>>>(
+          C->sig_src.p, C->steps_ig, P->bsr_vals.p, reinterpret_cast<T*>(C->sig_val.p));
       CB_LAUNCH();
     }
   } else if (C->maxI > 0) {
@@ -1708,6 +1808,7 @@ namespace {
 
 struct ApplyWork {
   double *u0, *hG, *gI, *gl, *wG, *cl, *rc, *uc, *yG, *xI, *zl, *yD;
+  void *uq, *zq;  // node-packed coupling inputs (operator precision)
 };
 
 void apply_untimed(bddc_ctx* C, const double* r, double* z, cudaStream_t s);
@@ -1726,7 +1827,8 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
   CB_LAUNCH();
   if (C->n_itI > 0) {
     apply_interior_kernel<T, false><<<C->n_itI, 256, smI, s>>>(
-        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->gdofI.p, Aloc, w.xI, w.u0);
+        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->gdofI.p, Aloc, w.xI, w.u0,
+        C->sparse_cpl ? static_cast<T*>(w.uq) : nullptr);
     CB_LAUNCH();
   }
   if (C->maxG > 0 && !C->sparse_cpl) {
@@ -1738,9 +1840,9 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
   }
   if (C->n_if > 0) {
     if (C->sparse_cpl) {  // g = r_Gamma - K_Gamma,I u0
-      coupling_kernel<T><<<cdiv(C->n_if, 256), 256, 0, s>>>(C->cgi_ptr.p, C->cgi_col.p,
-                                                          reinterpret_cast<const T*>(C->cgi_val.p),
-                                                          C->if_dof.p, r, w.u0, w.gI, C->n_if);
+      coupling_kernel<T><<<cdiv((int64_t)C->n_sgi * 32, 256), 256, 0, s>>>(
+          C->sgi_off.p, C->sgi_len.p, C->sgi_row.p, C->sgi_col.p, reinterpret_cast<const T*>(C->sgi_val.p),
+          static_cast<const typename Q4<T>::type*>(w.uq), C->if_dof.p, r, w.gI, C->n_sgi);
     } else {
       assemble_g_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
                                                           r, w.hG, w.gI);
@@ -1802,19 +1904,20 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
       CB_LAUNCH();
       yavg = w.yD;
     }
-    average_kernel<<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
-                                                     yavg, z, w.zl);
+    average_kernel<T><<<cdiv(C->n_if, 256), 256, 0, s>>>(C->if_dof.p, C->if_ptr.p, C->if_src.p, C->n_if,
+                                                        yavg, z, w.zl,
+                                                        C->sparse_cpl ? static_cast<T*>(w.zq) : nullptr);
     CB_LAUNCH();
   }
   if (C->sparse_cpl) {
     // z_I = A_II^-1 (r_I - K_I,Gamma z): the coupling overwrites the
     // gathered r_I (no longer needed) with its right-hand side
-    coupling_kernel<T><<<cdiv(C->totI, 256), 256, 0, s>>>(C->cig_ptr.p, C->cig_col.p,
-                                                        reinterpret_cast<const T*>(C->cig_val.p),
-                                                        C->gdofI.p, r, z, w.xI, C->totI);
+    coupling_kernel<T><<<cdiv((int64_t)C->n_sig * 32, 256), 256, 0, s>>>(
+        C->sig_off.p, C->sig_len.p, C->sig_row.p, C->sig_col.p, reinterpret_cast<const T*>(C->sig_val.p),
+        static_cast<const typename Q4<T>::type*>(w.zq), C->gdofI.p, r, w.xI, C->n_sig);
     CB_LAUNCH();
     apply_interior_kernel<T, true><<<C->n_itI, 256, smI, s>>>(
-        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->gdofI.p, Aloc, w.xI, z);
+        C->itI.p, C->d_nI.p, C->d_offA.p, C->d_ldA.p, C->d_offI.p, C->gdofI.p, Aloc, w.xI, z, nullptr);
     CB_LAUNCH();
   } else if (C->n_itI > 0) {
     apply_extend_kernel<T><<<C->n_itI, 256,
@@ -1828,7 +1931,7 @@ void apply_with_work(bddc_ctx* C, const double* r, double* z, const ApplyWork& w
 template <typename T>
 void apply_impl(bddc_ctx* C, const double* r, double* z, cudaStream_t s) {
   ApplyWork w{C->u0.p, C->hG.p, C->gI.p, C->gl.p, C->wG.p, C->cl.p, C->rc.p,
-              C->uc.p, C->yG.p, C->xI.p, C->zl.p, C->yD.p};
+              C->uc.p, C->yG.p, C->xI.p, C->zl.p, C->yD.p, C->uq.p, C->zq.p};
   apply_with_work<T>(C, r, z, w, s);
 }
 
@@ -1880,8 +1983,12 @@ double* noalloc_scratch_address() {
 int64_t bddc_noalloc_scratch_needed(const bddc_ctx* C) {
   auto pad = [](int64_t n) { return round_up(std::max<int64_t>(n, 1), 32); };
   const int64_t nch = cdiv(std::max(C->maxG, 1), PHIT_ROWS);
+  // node-packed coupling inputs: 4 values of esize bytes per node
+  const int64_t q = C->sparse_cpl ? pad((C->totI / 3) * 4 * (int64_t)C->esize / 8) +
+                                        pad((C->n_if / 3) * 4 * (int64_t)C->esize / 8)
+                                  : 0;
   return 2 * pad(C->totI) + (C->n_dlx > 0 ? 6 : 5) * pad(C->totG) + pad(C->n_if) + pad(C->totC * nch) +
-         2 * pad(C->n_pi);
+         2 * pad(C->n_pi) + q;
 }
 
 int64_t bddc_noalloc_scratch_capacity() { return kNoAllocScratchDoubles; }
@@ -1907,7 +2014,13 @@ void bddc_run_apply_noalloc(bddc_ctx* C, const double* r, double* z, cudaStream_
   w.cl = p; p += pad(C->totC * (int64_t)cdiv(std::max(C->maxG, 1), PHIT_ROWS));
   w.rc = p; p += pad(C->n_pi);
   w.uc = p; p += pad(C->n_pi);
-  w.yD = C->n_dlx > 0 ? p : nullptr;
+  w.yD = nullptr;
+  if (C->n_dlx > 0) { w.yD = p; p += pad(C->totG); }
+  w.uq = w.zq = nullptr;
+  if (C->sparse_cpl) {
+    w.uq = p; p += pad((C->totI / 3) * 4 * (int64_t)C->esize / 8);
+    w.zq = p; p += pad((C->n_if / 3) * 4 * (int64_t)C->esize / 8);
+  }
   if (C->precision == CBDDC_FP32) apply_with_work<float>(C, r, z, w, s);
   else apply_with_work<double>(C, r, z, w, s);
 }
@@ -1920,7 +2033,9 @@ int64_t bddc_ctx::device_bytes() const {
                    Sc.bytes() + ScX.bytes() + ScY.bytes() + ScP.bytes() + u0.bytes() + hG.bytes() +
                    gI.bytes() + wG.bytes() + cl.bytes() + rc.bytes() + uc.bytes() + yG.bytes() + gl.bytes() + xI.bytes() + zl.bytes() +
                    Dsb.bytes() + Ddb.bytes() + Deb.bytes() + Dsh.bytes() + DX.bytes() + DY.bytes() + DP.bytes() +
-                   yD.bytes() + Psi.bytes() + cgi_ptr.bytes() + cgi_col.bytes() + cgi_src.bytes() +
-                   cgi_val.bytes() + cig_ptr.bytes() + cig_col.bytes() + cig_src.bytes() + cig_val.bytes()) +
+                   yD.bytes() + Psi.bytes() + sgi_off.bytes() + sgi_len.bytes() + sgi_row.bytes() +
+                   sgi_col.bytes() + sgi_src.bytes() + sgi_val.bytes() + sig_off.bytes() + sig_len.bytes() +
+                   sig_row.bytes() + sig_col.bytes() + sig_src.bytes() + sig_val.bytes() + uq.bytes() +
+                   zq.bytes()) +
          (next ? next->device_bytes() + coarse_prob->device_bytes() : 0);
 }

@@ -48,13 +48,18 @@ struct bddc_ctx {
   int n_itI = 0, n_itG = 0, n_itP = 0, n_itR = 0;
   cbddc::DVec<int> cnch;                   // coarse-restriction chunks per local primal entry
   // sparse interior-interface coupling blocks of the assembled matrix
-  // (problems with a global BSR): rows = assembled interface nodes, columns
-  // = packed interior nodes (cgi); rows = packed interior nodes, columns =
-  // free nodes on the interface (cig); src = block index in the BSR
+  // (problems with a global BSR), sliced ELL: gi = rows of the assembled
+  // interface nodes, columns = packed interior nodes; ig = rows of the
+  // packed interior nodes, columns = interface nodes; per slice its first
+  // step (off) and step count (len), per lane slot its row, per step and
+  // lane the column and the BSR block (src, -1 = padding); uq / zq: the
+  // node-packed inputs (x, y, z, pad) in the operator precision
   bool sparse_cpl = false;
-  int64_t n_cgi = 0, n_cig = 0;
-  cbddc::DVec<int> cgi_ptr, cgi_col, cgi_src, cig_ptr, cig_col, cig_src;
-  cbddc::DVec<unsigned char> cgi_val, cig_val;
+  int n_sgi = 0, n_sig = 0;
+  int64_t steps_gi = 0, steps_ig = 0, n_cpl_blocks = 0;
+  cbddc::DVec<int> sgi_off, sgi_len, sgi_row, sgi_col, sgi_src;
+  cbddc::DVec<int> sig_off, sig_len, sig_row, sig_col, sig_src;
+  cbddc::DVec<unsigned char> sgi_val, sig_val, uq, zq;
   // apply work vectors
   cbddc::DVec<double> u0, hG, gI, wG, cl, rc, uc, yG, xI, zl;
   // sweep descriptors and GEMM problem lists

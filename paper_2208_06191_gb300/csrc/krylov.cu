@@ -335,12 +335,8 @@ __global__ void __launch_bounds__(DOT_THREADS) cgs2_coop_kernel(CgsArgs a) {
 // i = 0..j: h_i = v_i . w (block sums, one grid-wide barrier, every CTA
 // adds the CTA partials in CTA order), w -= h_i v_i; then ||w||, the
 // Givens update (CTA 0) and v_{j+1} = w / ||w||.  V is read once per step
-// and every FP64 FMA of the step is one of the 2 (j + 1) n of MGS.  The
-// FP64 FMAs are the roof (about 10 us per basis vector at n = 3M), so the
-// waits around them are cut: the dot loop copies the thread's rows of v_i
-// into shared memory for the update (no second read after the barrier),
-// and each warp asks L2 for its segment of v_{i+1} before the barrier
-// (one bulk prefetch), so the next dot loop reads L2 instead of HBM.
+// (the update re-reads the rows of v_i that the thread has just read), and
+// every FP64 FMA of the step is one of the 2 (j + 1) n of MGS.
 constexpr int MGS_THREADS = 640;
 struct MgsArgs {
   const double* V;   // j + 1 columns of length n (stride n)
@@ -361,7 +357,6 @@ __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_coop_kernel(MgsArgs a) {
   if (*a.done) return;  // read by every CTA before any barrier: uniform
   __shared__ double red[MGS_THREADS / 32];
   __shared__ double hsh;
-  extern __shared__ double stash[];  // [RPT][MGS_THREADS]: this thread's rows of v_i
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x;
   // warp-contiguous rows: the warp's segment of 32 RPT rows, lane + 32 k
@@ -396,35 +391,17 @@ __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_coop_kernel(MgsArgs a) {
     __syncthreads();
     return out;
   };
-  // the warp's segment: rows [seg, seg + 32 RPT) of every column
-  const int64_t seg = ((int64_t)blockIdx.x * (MGS_THREADS / 32) + warp) * (32 * RPT);
   for (int i = 0; i <= a.j; ++i) {
     const double* vp = a.V + (int64_t)i * a.n + base;
-    // two independent FMA chains (the FP64 pipe's result latency is long)
-    double acc2[2] = {0.0, 0.0};
+    double acc = 0.0;
 #pragma unroll
     for (int k = 0; k < RPT; ++k)
-      if (32 * k < lim) {
-        const double v = vp[32 * k];
-        stash[k * MGS_THREADS + threadIdx.x] = v;
-        acc2[k & 1] = fma(v, x[k], acc2[k & 1]);
-      }
-    const double acc = acc2[0] + acc2[1];
-    if (i < a.j && lane == 0 && seg < a.n) {
-      // L2 prefetch of the segment in column i + 1, widened to 16-byte
-      // bounds: at most 8 bytes into column i and into column i + 2,
-      // which exists (i + 2 <= j + 1 <= m, V holds m + 1 columns)
-      const double* c = a.V + (int64_t)(i + 1) * a.n;
-      const size_t p0 = __cvta_generic_to_global(c + seg) & ~(size_t)15;
-      const size_t p1 = (__cvta_generic_to_global(c + min(a.n, seg + 32 * RPT)) + 15) & ~(size_t)15;
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p0), "r"((unsigned)(p1 - p0))
-                   : "memory");
-    }
+      if (32 * k < lim) acc = fma(vp[32 * k], x[k], acc);
     const double h = grid_sum(acc, i & 1);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.hcol[i] = h;
 #pragma unroll
     for (int k = 0; k < RPT; ++k)
-      if (32 * k < lim) x[k] = fma(-h, stash[k * MGS_THREADS + threadIdx.x], x[k]);
+      if (32 * k < lim) x[k] = fma(-h, vp[32 * k], x[k]);
   }
   double nacc = 0.0;
 #pragma unroll
@@ -568,15 +545,10 @@ void Gmres::ensure(int64_t n_, int m_) {
       const int64_t need = (n_ + T - 1) / T;
       const int rpt = need <= 8 ? 8 : need <= 16 ? 16 : need <= 24 ? 24 : need <= 32 ? 32 : 0;
       int per = 0;
-      const size_t sm = (size_t)rpt * MGS_THREADS * sizeof(double);  // up to 160 KiB
-      const void* fn = rpt == 8 ? (const void*)mgs_coop_kernel<8>
-                       : rpt == 16 ? (const void*)mgs_coop_kernel<16>
-                       : rpt == 24 ? (const void*)mgs_coop_kernel<24>
-                                   : (const void*)mgs_coop_kernel<32>;
-      if (rpt > 0) {
-        CB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        CB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, MGS_THREADS, sm));
-      }
+      if (rpt == 8) CB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mgs_coop_kernel<8>, MGS_THREADS, 0));
+      if (rpt == 16) CB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mgs_coop_kernel<16>, MGS_THREADS, 0));
+      if (rpt == 24) CB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mgs_coop_kernel<24>, MGS_THREADS, 0));
+      if (rpt == 32) CB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mgs_coop_kernel<32>, MGS_THREADS, 0));
       if (rpt > 0 && per >= 1) {
         mgs_grid = sms;
         mgs_rpt = rpt;
@@ -698,8 +670,7 @@ int gmres_run(fem_problem* P, bddc_ctx* C, Gmres& G, const double* b, double* x,
                          : G.mgs_rpt == 16 ? (const void*)mgs_coop_kernel<16>
                          : G.mgs_rpt == 24 ? (const void*)mgs_coop_kernel<24>
                                            : (const void*)mgs_coop_kernel<32>;
-        CB_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G.mgs_grid), dim3(MGS_THREADS), args,
-                                            (size_t)G.mgs_rpt * MGS_THREADS * sizeof(double), s));
+        CB_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G.mgs_grid), dim3(MGS_THREADS), args, 0, s));
         CB_LAUNCH();
       } else {
         // classical Gram-Schmidt with a second pass only where the first
