@@ -396,6 +396,15 @@ TIMER_CLASSES = ("SWEEP_GEMM", "ELEMENT", "APPLY", "SPMV", "ORTH", "SETUP", "LEV
                  "COARSE_SETUP", "COARSE_APPLY", "SETUP_GEMM_F64")
 
 
+# DRAM traffic of one BDDC apply per byte of local_bytes, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum over the kernels of
+# an apply, lv_p2_small, the same generator and kernels at 194k DoFs).  The
+# apply streams every operator once, so its traffic grows with local_bytes,
+# and the ratio scales the capture to the full workload.  None: no capture
+# for that workload's current kernels.
+APPLY_TRAFFIC_PER_LOCAL_BYTE = {"lv_p2": 1.034}
+
+
 def _opts(pkg, prob, spec, precision, max_gmres):
     ml = {}
     if spec["levels"] == 3:
@@ -608,8 +617,13 @@ def run_ours(args, world, rank, local):
     gemm_step = gm["ms_per_step"] if gm else 0.0
     if apply_step >= gemm_step and ap:
         achieved = ap["GBps"]
+        ratio = APPLY_TRAFFIC_PER_LOCAL_BYTE.get(args.workload)
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": None,
+                    "frac": achieved / hbm,
+                    "traffic": ratio * ap["GB_per_launch"] * 1e9 if ratio else None,
+                    "traffic_source": ("ncu DRAM bytes of one apply on lv_p2_small, %.3f per byte of "
+                                       "local_bytes, scaled to this workload's local_bytes" % ratio)
+                    if ratio else None,
                     "kernel": "BDDC apply (its batched launches, level 2 and coarsest included)",
                     "bytes_per_launch": ap["GB_per_launch"] * 1e9, "ms_per_launch": ap["ms_per_launch"],
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",

@@ -53,7 +53,10 @@ __device__ inline float vdot2(float4 a, float4 b) { return a.x * b.x + a.y * b.y
 __device__ inline double vdot2(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
 
 // Dot products of two rows (16-byte aligned) with a shared-memory vector,
-// one warp: 2 x 4 streaming 16-byte loads in flight per lane, no barriers.
+// one warp: the rows go in chunks of 32 x U 16-byte vectors, and every lane
+// issues all its loads of a chunk (2 x U, predicated at the row's end)
+// before using them, so short rows (a few hundred entries) are one round of
+// loads; no barriers.
 template <typename T>
 __device__ __forceinline__ void warp_dot2(const T* __restrict__ ra, const T* __restrict__ rb, bool has_b,
                                           const T* __restrict__ xs, int n, int lane, T& oa, T& ob) {
@@ -65,26 +68,23 @@ __device__ __forceinline__ void warp_dot2(const T* __restrict__ ra, const T* __r
   const V* vb = reinterpret_cast<const V*>(rb);
   const V* xv = reinterpret_cast<const V*>(xs);
   T acc_a = T(0), acc_b = T(0);
-  int i = lane;
-  for (; i + 32 * (U - 1) < nv; i += 32 * U) {
+  for (int i0 = lane; i0 < nv; i0 += 32 * U) {
     V la[U], lb[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) la[u] = __ldcs(va + i + 32 * u);
-    if (has_b) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) lb[u] = __ldcs(vb + i + 32 * u);
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + 32 * u;
+      la[u] = i < nv ? __ldcs(va + i) : V{};
+      lb[u] = (has_b && i < nv) ? __ldcs(vb + i) : V{};
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const V x = xv[i + 32 * u];
-      acc_a += vdot2(la[u], x);
-      if (has_b) acc_b += vdot2(lb[u], x);
+      const int i = i0 + 32 * u;
+      if (i < nv) {
+        const V x = xv[i];
+        acc_a += vdot2(la[u], x);
+        if (has_b) acc_b += vdot2(lb[u], x);
+      }
     }
-  }
-  for (; i < nv; i += 32) {
-    const V x = xv[i];
-    acc_a += vdot2(__ldcs(va + i), x);
-    if (has_b) acc_b += vdot2(__ldcs(vb + i), x);
   }
   for (int c = nv * W + lane; c < n; c += 32) {
     acc_a += ra[c] * xs[c];
@@ -412,7 +412,7 @@ __global__ void coarse_assemble_kernel_d(const int* __restrict__ key, const int*
 }
 
 // ------------------------------------------------------------ apply kernels
-constexpr int AROWS = 32;  // rows per CTA in the batched GEMVs (8 warps x 4)
+constexpr int AROWS = 128;  // rows per CTA of the prolongation (8 warps x 4 rows, 4 passes)
 constexpr int PHIT_ROWS = 128;  // interface rows per CTA of the coarse restriction
 constexpr int NC_MAX = 512;  // primal constraints per subdomain
 
@@ -467,7 +467,7 @@ apply_interior_kernel(const int2* __restrict__ items, const int* __restrict__ nI
 // One lane per block row, all nine products in the operator precision.
 template <typename T> struct Q4;
 template <> struct Q4<float> { using type = float4; };
-template <> struct Q4<double> { using type = double4; };
+template <> struct Q4<double> { using type = double4_32a; };
 
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -602,19 +602,38 @@ apply_phit_kernel(const int2* __restrict__ items, const int* __restrict__ nG, co
     // products and the chunk's partial sums in the operator precision (FP64
     // issue is the scarce resource on this part); chunks are summed in FP64
     T acc[4] = {T(0), T(0), T(0), T(0)};
+    if (sizeof(T) == 4) {
+      // FP32: lane owns columns 4 lane .. 4 lane + 3 of the block, one
+      // 16-byte load per row (rows are 16-byte aligned and ld is a multiple
+      // of 4, so the load stays inside the row; columns past nc are padding
+      // whose sums are not stored)
+      const bool in = cb + 4 * lane < ld;
 #pragma unroll 4
-    for (int j = r0 + warp; j < r1; j += 8) {
-      const T gj = (T)gl[og + j];
-      const T* row = P0 + (int64_t)j * ld + cb;
+      for (int j = r0 + warp; j < r1; j += 8) {
+        const T gj = (T)gl[og + j];
+        if (in) {
+          const float4 v = __ldcs(reinterpret_cast<const float4*>(P0 + (int64_t)j * ld + cb) + lane);
+          acc[0] += (T)v.x * gj;
+          acc[1] += (T)v.y * gj;
+          acc[2] += (T)v.z * gj;
+          acc[3] += (T)v.w * gj;
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int j = r0 + warp; j < r1; j += 8) {
+        const T gj = (T)gl[og + j];
+        const T* row = P0 + (int64_t)j * ld + cb;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int c = lane + 32 * t;
-        if (cb + c < ncs) acc[t] += row[c] * gj;
+        for (int t = 0; t < 4; ++t) {
+          const int c = lane + 32 * t;
+          if (cb + c < ncs) acc[t] += row[c] * gj;
+        }
       }
     }
     __syncthreads();  // red is reused across column blocks
 #pragma unroll
-    for (int t = 0; t < 4; ++t) red[warp][lane + 32 * t] = (double)acc[t];
+    for (int t = 0; t < 4; ++t) red[warp][sizeof(T) == 4 ? 4 * lane + t : lane + 32 * t] = (double)acc[t];
     __syncthreads();
     for (int c = threadIdx.x; c < 128 && cb + c < ncs; c += blockDim.x) {
       double v = 0.0;
@@ -722,25 +741,30 @@ apply_prolong_kernel(const int2* __restrict__ items, const int* __restrict__ nG,
   for (int c = threadIdx.x; c < ncs; c += blockDim.x) ucl[c] = (T)uc[gprim[offC[s] + c]];
   __syncthreads();
   const int sub = threadIdx.x & 7, grp = threadIdx.x >> 3;  // 32 groups of 8 lanes
-  const int row = r0 + grp;
-  T acc = T(0);  // operator precision, as in the other local products
-  if (row < ng) {
-    // rows start 16-byte aligned (offsets and leading dimensions are
-    // multiples of 8 elements): 8 lanes read 8 consecutive 16-byte chunks
-    const T* pr = Phi + offPhi[s] + (int64_t)row * ldPhi[s];
-    const V* pv = reinterpret_cast<const V*>(pr);
-    const V* uv = reinterpret_cast<const V*>(ucl);
-    const int nv = ncs / W;
+  // the CTA's rows in passes of 32 (uniform trip count: the shuffles below
+  // need every lane of the warp)
+  for (int pass = 0; pass < AROWS / 32; ++pass) {
+    const int row = r0 + grp + 32 * pass;
+    T acc = T(0);  // operator precision, as in the other local products
+    if (row < ng) {
+      // rows start 16-byte aligned (block offsets are multiples of 64
+      // elements, leading dimensions of 4): 8 lanes read 8 consecutive
+      // 16-byte chunks
+      const T* pr = Phi + offPhi[s] + (int64_t)row * ldPhi[s];
+      const V* pv = reinterpret_cast<const V*>(pr);
+      const V* uv = reinterpret_cast<const V*>(ucl);
+      const int nv = ncs / W;
 #pragma unroll 2
-    for (int c = sub; c < nv; c += 8) acc += vdot2(__ldcs(pv + c), uv[c]);
-    for (int c = nv * W + sub; c < ncs; c += 8) acc += pr[c] * ucl[c];
-  }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  if (row < ng && sub == 0) {
-    const int64_t og = offGam[s];
-    yG[og + row] = Dg[og + row] * (wG[og + row] + (double)acc);
+      for (int c = sub; c < nv; c += 8) acc += vdot2(__ldcs(pv + c), uv[c]);
+      for (int c = nv * W + sub; c < ncs; c += 8) acc += pr[c] * ucl[c];
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (row < ng && sub == 0) {
+      const int64_t og = offGam[s];
+      yG[og + row] = Dg[og + row] * (wG[og + row] + (double)acc);
+    }
   }
 }
 
