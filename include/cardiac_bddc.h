@@ -459,12 +459,13 @@ enum {
    Gauss-Jordan sweep updates, else two (three products); bit 2 (4): the
    same for the other setup products; bit 3 (8): the other products on the
    CUDA cores; bit 4 (16): the sweep updates on the CUDA cores; bit 5 (32):
-   the tensor-core sweep updates sum four K-slices in FP32 instead of one
-   per 32-wide K block.  Bits above 5 are ignored.  Default 1 (tensor
-   cores, two parts, one slice per K block).  The enable bits are read at
-   every setup, the part counts when a context is created.  Returns the
-   previous mode.  Host-side state, not thread safe; a diagnostic and
-   comparison switch. */
+   the tensor-core sweep updates accumulate a whole 32-wide K block in each
+   TMEM slice instead of one K-step of 8; bit 6 (64): the other products
+   accumulate one K-step of 8 per slice instead of a 32-wide K block.
+   Bits above 6 are ignored.  Default 1
+   (tensor cores, two parts).  The enable bits are read at every setup,
+   the part counts when a context is created.  Returns the previous mode.
+   Host-side state, not thread safe; a diagnostic and comparison switch. */
 CBDDC_API int cbddc_set_tensor_cores(int mode);
 
 /* Starts recording CUDA events around every launch of the given class (and

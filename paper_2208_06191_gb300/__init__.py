@@ -222,7 +222,9 @@ def set_tensor_cores(mode):
     """FP32 setup GEMMs: mode bit 0 = tcgen05 tensor cores (else the FP32
     CUDA cores), bit 1 = three TF32 parts for the sweep updates, bit 2 =
     three parts for the other products, bits 3/4 = the other products / the
-    sweep updates on the CUDA cores, bit 5 = four K-slices per sweep tile
+    sweep updates on the CUDA cores, bit 5 = sweep updates with a 32-wide K
+    block per tensor-memory slice instead of one K-step, bit 6 = the other
+    products with one K-step per slice instead of a 32-wide block
     (True means the default, 1; False means 0).  Returns the previous
     mode."""
     if mode is True:

@@ -30,6 +30,7 @@ bool tensor_cores_for(bool sweep) {
   return (m & 1) && !(m & (sweep ? 16 : 8));
 }
 bool tc_sweep_ks1() { return (g_tensor_cores.load(std::memory_order_relaxed) & 32) == 0; }
+bool tc_other_ks1() { return (g_tensor_cores.load(std::memory_order_relaxed) & 64) != 0; }
 int tc_parts(bool sweep) { return (g_tensor_cores.load(std::memory_order_relaxed) & (sweep ? 2 : 4)) ? 3 : 2; }
 
 // Launch timer: event pairs recorded on the launching stream, one pool per
@@ -612,7 +613,7 @@ const char* cbddc_last_error(void) { return g_last_error.c_str(); }
 
 uint64_t cbddc_kernel_launches(void) { return g_launches.load(); }
 
-int cbddc_set_tensor_cores(int mode) { return g_tensor_cores.exchange(mode & 63); }
+int cbddc_set_tensor_cores(int mode) { return g_tensor_cores.exchange(mode & 127); }
 
 int cbddc_timer_start(int kernel_class) {
   return guard([&] {

@@ -37,6 +37,7 @@ struct GemmProb {
 bool tensor_cores_enabled();
 bool tensor_cores_for(bool sweep);  // per kind of list (sweep updates / other products)
 bool tc_sweep_ks1();                 // sweep updates accumulate one K-step per TMEM slice
+bool tc_other_ks1();                 // the other products too
 int tc_parts(bool sweep);
 
 template <typename T> struct GemmCfg;
@@ -441,7 +442,8 @@ void launch_tc(const GemmList& g, const float* A, const float* B, float* C, floa
   // operand stage and two C buffers; longer K: two stages and one C buffer
   // (three-part operands: one stage and two C buffers always)
   const int grid = tc::tc_grid(g.ntiles);
-  const bool ks1 = g.presplit && tc_sweep_ks1();  // sweep updates: one K-step per TMEM slice
+  // one K-step per TMEM slice (else a 32-wide K block per slice)
+  const bool ks1 = g.presplit ? tc_sweep_ks1() : tc_other_ks1();
 #define CB_TC_LAUNCH(NST, NCB, NP, KS)                                                              \
   tc::tc_gemm_kernel<NST, NCB, NP, KS><<<grid, tc::TC_THREADS, tc::TcSmem<NST, NCB, NP>::bytes, s>>>( \
       g.tiles.p, g.ntiles, g.tcp.p, g.maps, C, alpha, beta, g.tc_status)
@@ -452,7 +454,8 @@ void launch_tc(const GemmList& g, const float* A, const float* B, float* C, floa
     if (ks1) CB_TC_LAUNCH(1, 2, 2, 1);
     else CB_TC_LAUNCH(1, 2, 2, 4);
   } else {
-    CB_TC_LAUNCH(2, 1, 2, 4);
+    if (ks1) CB_TC_LAUNCH(2, 1, 2, 1);
+    else CB_TC_LAUNCH(2, 1, 2, 4);
   }
 #undef CB_TC_LAUNCH
   CB_LAUNCH();

@@ -581,6 +581,7 @@ inline void set_smem_attr() {
     set_smem_attr_one<1, 2, 2, 1>();
     set_smem_attr_one<1, 2, 2, 4>();
     set_smem_attr_one<2, 1, 2, 4>();
+    set_smem_attr_one<2, 1, 2, 1>();
     set_smem_attr_one<1, 2, 3, 1>();
     set_smem_attr_one<1, 2, 3, 4>();
     done = true;
