@@ -30,6 +30,7 @@
 #include "bddc.h"
 #include "fem.h"
 #include "rigid.h"
+#include "sell.h"
 
 namespace cbddc {
 
@@ -888,60 +889,6 @@ static void build_coarse_problem(bddc_ctx* C, fem_problem* CP) {
   CB_CUDA(cudaMemset(CP->status.p, 0, CP->status.bytes()));
   CP->has_tangent = true;
   C->d_cbase.upload(cbase);
-}
-
-// Sliced ELL layout (32 rows per slice) of a block matrix given as CSR over
-// node rows: rows sorted by decreasing length inside windows of 8 slices,
-// so that a slice's rows have similar lengths and neighbouring rows stay
-// together.
-struct SellHost {
-  std::vector<int> off, len, row, col, src;
-  int64_t steps = 0;
-};
-
-static SellHost build_sell(const std::vector<int>& ptr, const std::vector<int>& col,
-                           const std::vector<int>& src) {
-  const int nrows = (int)ptr.size() - 1;
-  std::vector<int> order(nrows);
-  for (int i = 0; i < nrows; ++i) order[i] = i;
-  for (int w0 = 0; w0 < nrows; w0 += 256) {
-    const int w1 = std::min(nrows, w0 + 256);
-    std::stable_sort(order.begin() + w0, order.begin() + w1,
-                     [&](int a, int b) { return ptr[a + 1] - ptr[a] > ptr[b + 1] - ptr[b]; });
-  }
-  const int nsl = (nrows + 31) / 32;
-  SellHost S;
-  S.off.assign(nsl + 1, 0);
-  S.len.assign(nsl, 0);
-  S.row.assign((size_t)nsl * 32, -1);
-  int64_t steps = 0;
-  for (int q = 0; q < nsl; ++q) {
-    int L = 0;
-    for (int l = 0; l < 32 && 32 * q + l < nrows; ++l) {
-      const int r = order[32 * q + l];
-      S.row[32 * q + l] = r;
-      L = std::max(L, ptr[r + 1] - ptr[r]);
-    }
-    CB_CHECK(steps < INT32_MAX, CBDDC_EINVAL, "coupling matrix too large");
-    S.off[q] = (int)steps;
-    S.len[q] = L;
-    steps += L;
-  }
-  S.off[nsl] = (int)steps;
-  S.steps = steps;
-  S.col.assign((size_t)steps * 32, 0);
-  S.src.assign((size_t)steps * 32, -1);
-  for (int q = 0; q < nsl; ++q)
-    for (int l = 0; l < 32; ++l) {
-      const int r = S.row[32 * q + l];
-      if (r < 0) continue;
-      for (int k = 0; k < ptr[r + 1] - ptr[r]; ++k) {
-        const size_t p = ((size_t)S.off[q] + k) * 32 + l;
-        S.col[p] = col[ptr[r] + k];
-        S.src[p] = src[ptr[r] + k];
-      }
-    }
-  return S;
 }
 
 void bddc_create(fem_problem* P, const bddc_options* opt, bddc_ctx* C) {
